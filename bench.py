@@ -1,0 +1,391 @@
+"""Benchmark of the GB300 pressure multigrid (arXiv 1410.8568, Sec. 2.3).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload drop_film_128|drop_film_512|sphere_32]
+
+Metric: Poisson multigrid solves per second to a relative residual of 1e-10,
+mixed precision (FP32 V(2,2) cycles inside FP64 iterative refinement) next to
+the plain FP64 path on the same inputs, with p50/p99 latency.
+
+One step = one pressure solve of a time step: the new density goes in
+(face coefficients of Eqs. 11-12, coarse-level coefficients, coarsest-grid
+inverse) and Eq. 9 is solved from a cold start to ||r|| <= 1e-10 ||b||.  Inputs
+are resident in HBM when the timed region starts; L2 is flushed (a 256 MB
+write) before every step, outside the step's events.  Each step is bracketed by
+CUDA events on the solver's stream; `value` = steps / summed step time.
+
+`e2e` repeats the step through mg_step_host with pinned host buffers (density
+and right-hand side copied in, pressure copied out, inside the timed region).
+
+`roofline` is for the dominant kernel (the finest-level red-black half-sweep,
+FP32): its launches are timed with CUDA events on the solver stream in a second
+pass of the same steps (host-driven loop, one event pair per launch).
+
+`cpu_baseline` / `--impl reference`: the FP64 CPU oracle (oracle/, plain C with
+OpenMP over z-planes) solving the same problem on the host cores.
+
+Multi-GPU: the solve does not shard here (replicas only): each rank solves its
+own copy; value = all ranks' solves / the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Poisson MG solves/s to 1e-10 rel. residual, mixed vs FP64 on GB300; p50/p99 ms"
+TOL = 1e-10
+L2_FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "drop_film_128": dict(kind="config2", n=128,
+                          desc="drop_film_128^3_1000to1: film depth 0.1 + drop R 0.125 at z 0.3, periodic x,y, Neumann z, Fourier-divergence RHS"),
+    "drop_film_512": dict(kind="config3", n=512,
+                          desc="drop_film_512^3_1000to1: film + drop + 0-4 droplets, periodic x,y, Neumann z, Fourier-divergence RHS"),
+    "sphere_32": dict(kind="config1", n=32,
+                      desc="sphere_32^3_1000to1: R 0.2 centred, Neumann walls, N(0,1) RHS"),
+}
+
+
+def make_problem(name):
+    from paper_1410_8568_gb300 import inputs as I
+    w = WORKLOADS[name]
+    if w["kind"] == "config1":
+        return I.config1(w["n"])
+    if w["kind"] == "config2":
+        return I.config2(w["n"])
+    return I.config3(w["n"])
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("mg_kernels.cu", "mg_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1410_8568_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    or None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "smooth_level0_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def count_launches(levels, iters, nu1=2, nu2=2):
+    """Kernels of one step: coefficient set-up + prologue + iters * body + final."""
+    setup = 1 + (levels - 1) + 1  # faces from density, coarsening per level, coarsest inverse
+    prologue = 6                  # begin, sum b, mean, residual, finalize, loop control
+    body = (levels - 1) * (2 * nu1 + 1 + 1 + 2 * nu2) + 1 + 1 + 1 + 1  # smooth/restrict/prolong, coarse, residual, finalize, control
+    return setup + prologue + iters * body + 1
+
+
+def cpu_oracle_solve(P, faces, tol=TOL):
+    import oracle
+    t = time.perf_counter()
+    r = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=tol, max_cycles=200)
+    return time.perf_counter() - t, r
+
+
+def run_reference(args, name):
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    import oracle
+    P = make_problem(name)
+    faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
+    cores = oracle.num_threads()
+    times = []
+    for s in range(args.warmup + args.steps):
+        dt, r = cpu_oracle_solve(P, faces)
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[name]["desc"], "grid": list(P.shape), "tol": TOL},
+        "p50_ms": 1000.0 * statistics.median(times), "p99_ms": 1000.0 * float(np.percentile(times, 99)),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d full FP64 oracle solves of the workload to 1e-10 (%d V(2,2) cycles each)" %
+                                   (len(times), r.cycles)},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="drop_film_128", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, args.workload)
+        return
+
+    import torch
+
+    from paper_1410_8568_gb300 import gbmg
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+
+    P = make_problem(args.workload)
+    N = P.cells
+    rho_h = torch.from_numpy(P.rho).pin_memory()
+    rhs_h = torch.from_numpy(P.rhs).pin_memory()
+    rho = rho_h.cuda()
+    rhs = rhs_h.cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def timed(solver, steps, host=False):
+        """Per-step device times (ms) and the last stats."""
+        p = torch.zeros_like(rhs)
+        ph = torch.zeros(P.rho.shape, dtype=torch.float64).pin_memory()
+        times, st = [], None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for s in range(steps):
+                flush.fill_(float(s))
+                ev[s][0].record(stream)
+                if host:
+                    ph.zero_()
+                    st = solver.step_host(rho_h.numpy(), rhs_h.numpy(), ph.numpy(), tol=TOL)
+                else:
+                    p.zero_()
+                    solver.set_density(rho)
+                    st = solver.solve(rhs, p, tol=TOL)
+                ev[s][1].record(stream)
+                if st.status != gbmg.OK:
+                    raise RuntimeError("solve failed: %s" % gbmg.strerror(st.status))
+            stream.synchronize()
+        times = [a.elapsed_time(b) for a, b in ev]
+        return times, st, p
+
+    results = {}
+    solvers = {}
+    for prec in (gbmg.MIXED, gbmg.FP64):
+        with torch.cuda.stream(stream):
+            solvers[prec] = gbmg.Solver(P.shape, P.bc, rho=rho, precision=prec, stream=stream)
+        S = solvers[prec]
+        timed(S, args.warmup)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local_rank) if prec == gbmg.MIXED else None
+        if clocks:
+            clocks.start()
+        t0 = time.perf_counter()
+        times, st, p = timed(S, args.steps)
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        if clocks:
+            results["clocks"] = clocks.stop()
+        tot = sum(times)
+        if dist is not None:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = t.item()
+        results[prec] = dict(ms=tot / args.steps, value=world * args.steps / (tot / 1000.0),
+                             p50=statistics.median(times), p99=float(np.percentile(times, 99)),
+                             iters=st.iters, gamma=st.gamma, rel_res=st.rel_res, wall=wall,
+                             levels=S.num_levels(), p=p)
+
+    # error of each result against the FP64 oracle's converged solution (small grids only)
+    errors = {}
+    if rank == 0 and N <= 128 ** 3:
+        import oracle
+        faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
+        pstar = oracle.solve_exact(P.shape, P.bc, faces, P.rhs).x
+        for prec in (gbmg.MIXED, gbmg.FP64):
+            x = results[prec]["p"].cpu().numpy()
+            errors[prec] = float(np.linalg.norm(x - pstar) / np.linalg.norm(pstar))
+
+    # end to end through the host entry point (pinned buffers, copies inside)
+    S = solvers[gbmg.MIXED]
+    timed(S, 2, host=True)
+    e2e_times, _, _ = timed(S, args.steps, host=True)
+    e2e_tot = sum(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = t.item()
+
+    # roofline of the dominant kernel: finest-level half-sweep, per-launch events
+    S.profile(True)
+    prof_steps = max(3, min(args.steps, 10))
+    timed(S, prof_steps)
+    n_l, ms_l = S.profile_read(gbmg.K_SMOOTH, 0)
+    n_r, ms_r = S.profile_read(gbmg.K_RESIDUAL, 0)
+    S.profile(False)
+    avg_s = ms_l / n_l / 1000.0
+    bytes_launch = 5 * 4 * N  # FP32 half-sweep: read x, b (own colour), 3 faces; write own colour
+    peak, peak_kind = read_peaks()
+    achieved = bytes_launch / avg_s / 1e9
+    traffic = profiled_traffic(args.workload)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
+        if N <= 128 ** 3:
+            dt, r = cpu_oracle_solve(P, faces)
+            cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": "1 full FP64 oracle solve of the workload to 1e-10 (%d V(2,2) cycles)" % r.cycles}
+        else:
+            # bounded sample: 2 oracle cycles, scaled by the GPU solve's cycle count
+            t = time.perf_counter()
+            r = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=2)
+            dt = (time.perf_counter() - t) * results[gbmg.FP64]["iters"] / 2.0
+            cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": "2 FP64 oracle V(2,2) cycles of the workload, scaled to %d cycles per solve" %
+                             results[gbmg.FP64]["iters"]}
+
+    if rank == 0:
+        m, f = results[gbmg.MIXED], results[gbmg.FP64]
+        launches = args.steps * count_launches(m["levels"], m["iters"])
+        line = {
+            "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "grid": list(P.shape),
+                       "bc": list(P.bc), "density_ratio": P.ratio, "tol": TOL,
+                       "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
+                       "step": "set density (faces, coarse faces, coarsest inverse) + cold-start solve",
+                       "l2": "flushed before every step (256 MB write, outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "p50_ms": m["p50"], "p99_ms": m["p99"],
+            "iters": m["iters"], "gamma": m["gamma"], "rel_res": m["rel_res"],
+            "err_vs_oracle": errors.get(gbmg.MIXED),
+            "fp64": {"value": f["value"], "unit": "solves/s", "ms_per_step": f["ms"], "p50_ms": f["p50"],
+                     "p99_ms": f["p99"], "iters": f["iters"], "gamma": f["gamma"], "rel_res": f["rel_res"],
+                     "err_vs_oracle": errors.get(gbmg.FP64)},
+            "mixed_over_fp64": m["value"] / f["value"],
+            "e2e": {"value": world * args.steps / (e2e_tot / 1000.0), "unit": "solves/s",
+                    "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_smooth<float> level 0 (one red or black half-sweep)",
+                         "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": n_l, "peak_source": peak_kind,
+                         "residual_fp64_avg_launch_us": 1000.0 * ms_r / max(1, n_r)},
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": results.get("clocks"),
+        }
+        print(json.dumps(line))
+    for S in solvers.values():
+        S.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

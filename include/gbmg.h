@@ -1,0 +1,293 @@
+/*
+ * gbmg.h -- C ABI of the GB300 multigrid solver for the variable-density
+ * pressure Poisson equation
+ *
+ *     div( (1/rho) grad p ) = S                                       (Eq. 9)
+ *
+ * of Shin, Chergui & Juric, "A solver for massively parallel direct numerical
+ * simulation of three-dimensional multiphase flows" (arXiv 1410.8568), Sec. 2.3,
+ * discretised with cell-centred second-order differences on a uniform
+ * staggered (MAC) grid (Eq. 10) with face coefficients alpha = 1/rho (harmonic
+ * averages, Eqs. 11-12), solved by V-cycle multigrid with red-black relaxation.
+ *
+ * One process, one GPU.  All compute runs in the CUDA kernels of libgbmg.so;
+ * there is no CPU fallback.  Every call returns an int status (MG_OK = 0).
+ *
+ * ---------------------------------------------------------------------------
+ * Layout.  A grid has nx*ny*nz cells; cell (i,j,k) is element i + nx*(j + ny*k)
+ * of every cell array (x fastest).  A face array ax (likewise ay, az) has one
+ * entry per cell: the coefficient alpha of that cell's LOW face along x, i.e.
+ * the face between cells (i-1,j,k) and (i,j,k).  On a Neumann (wall) axis the
+ * entries at i = 0 are the wall and are ignored (zero flux), and the high wall
+ * of the last cell carries no entry.  On a periodic axis the entry at i = 0 is
+ * the face shared with cell nx-1.  All arrays are FP64 unless stated.
+ *
+ * Operator.  (A p)_c = sum over the faces f of c of alpha_f / h_d^2 (p_nb - p_c)
+ * with h_d = l_d / n_d; A is symmetric negative semidefinite with A 1 = 0.
+ * Because every boundary is a wall or periodic, A p = b is solvable only for
+ * sum(b) = 0 and p is defined up to a constant: the library removes the mean of
+ * the right-hand side (reported in mg_stats.rhs_mean) and returns the solution
+ * with zero mean.
+ *
+ * Size rule.  Every axis is n = m * 2^k with m in {2, 3, 4} (2, 3, 4, 6, 8, 12,
+ * 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, ...).  All axes are
+ * coarsened together while every axis is even and larger than 4; the coarsest
+ * grid must have at most MG_MAX_COARSE cells (it is solved exactly).
+ *
+ * Ownership.  The caller owns every buffer it passes.  Device pointers are
+ * device memory of the current CUDA device.  A handle owns its hierarchy (all
+ * levels, FP32 copies, the coarsest-grid inverse, reduction scratch) until
+ * mg_destroy.  No host<->device copy happens inside the device-pointer calls
+ * except the small statistics record.  The *_host calls take host pointers and
+ * do their own copies on the handle's stream.
+ *
+ * Errors.  MG_EINVAL for bad arguments (unsupported size, null pointer,
+ * non-positive or non-finite coefficients or density, bad parameters);
+ * MG_ENOMEM when device memory cannot be allocated; MG_ECUDA for a CUDA error;
+ * MG_ENOTCONV when max_iters cycles did not reach the tolerance (p holds the
+ * last iterate); MG_EDIVERGED when the residual became NaN/Inf; MG_ESINGULAR
+ * when the coarsest-grid matrix could not be inverted (a grid cut into pieces
+ * by zero coefficients); MG_EBUSY, MG_EAGAIN, MG_EBUDGET, MG_ENOTFOUND for the
+ * serving calls; MG_ETIMEOUT when a bounded device wait expired.
+ */
+#ifndef GBMG_H
+#define GBMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_OK 0
+#define MG_EINVAL 1
+#define MG_ENOMEM 2
+#define MG_ECUDA 3
+#define MG_ENOTCONV 4
+#define MG_EDIVERGED 5
+#define MG_ETIMEOUT 6
+#define MG_EBUSY 7
+#define MG_EAGAIN 8
+#define MG_EBUDGET 9
+#define MG_ESINGULAR 10
+#define MG_ENOTFOUND 11
+
+#define MG_BC_NEUMANN 0  /* walls at both ends of the axis: zero normal flux */
+#define MG_BC_PERIODIC 1 /* the axis wraps around */
+
+#define MG_PREC_FP64 0  /* every level in FP64 */
+#define MG_PREC_MIXED 1 /* FP32 V-cycles inside FP64 iterative refinement */
+
+#define MG_FACE_HARMONIC 0   /* Eqs. 11-12: 2 a_L a_R / (a_L + a_R), a = 1/rho */
+#define MG_FACE_ARITHMETIC 1 /* (a_L + a_R) / 2 */
+
+#define MG_MAX_COARSE 512 /* most cells allowed on the coarsest grid */
+#define MG_MAX_LEVELS 16
+
+typedef struct {
+    int nx, ny, nz;     /* cells per axis */
+    double lx, ly, lz;  /* domain lengths (h_d = l_d / n_d) */
+    int bc[3];          /* MG_BC_NEUMANN or MG_BC_PERIODIC, per axis x, y, z */
+} mg_grid;
+
+typedef struct {
+    int nu1, nu2;      /* pre- and post-relaxation sweeps (one sweep = red then black) */
+    double omega;      /* SOR factor of the red-black relaxation, 0 < omega < 2 */
+    int max_iters;     /* most V-cycles per solve */
+    int precision;     /* MG_PREC_FP64 or MG_PREC_MIXED */
+    int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
+} mg_params;
+
+typedef struct {
+    int iters;          /* V-cycles performed (nc of Eq. 15) */
+    int status;         /* MG_OK, MG_ENOTCONV or MG_EDIVERGED */
+    double rel_res;     /* ||b - A p||_2 / ||b||_2 at exit (b with its mean removed) */
+    double res0;        /* R_0: ||b - A p0||_2 for the starting iterate */
+    double res;         /* R_nc: final ||b - A p||_2 */
+    double gamma;       /* average reduction rate (R_nc / R_0)^(1/nc), Eq. 15 */
+    double bnorm;       /* ||b - mean(b)||_2 */
+    double rhs_mean;    /* mean of the right-hand side that was removed */
+    double ms;          /* device time of the solve (stream events), milliseconds */
+} mg_stats;
+
+typedef struct mg_handle mg_handle;
+typedef struct mg_batch mg_batch;
+typedef struct mg_server mg_server;
+typedef int64_t mg_ticket;
+
+/* Error text of a status code (static string). */
+const char *mg_strerror(int status);
+
+/* cudaError_t value of the most recent CUDA failure seen by this thread
+ * (0 if none); explains an MG_ECUDA return. */
+int mg_last_cuda_error(void);
+
+/* Default parameters: V(2,2), omega = 1 (Gauss-Seidel), 100 cycles, mixed
+ * precision, CUDA graph on. */
+int mg_params_default(mg_params *params);
+
+/* Face coefficients alpha = 1/rho of Eqs. 11-12 (mode MG_FACE_HARMONIC) or the
+ * arithmetic mean of 1/rho (MG_FACE_ARITHMETIC) from the cell density rho
+ * (DEVICE, nx*ny*nz, rho > 0), written to ax, ay, az (DEVICE, nx*ny*nz each,
+ * the layout above; Neumann wall entries are written as 0).  Asynchronous on
+ * `stream` (a cudaStream_t, NULL = the legacy default stream). */
+int mg_faces_from_density(const mg_grid *grid, const double *rho, int mode,
+                          double *ax, double *ay, double *az, void *stream);
+
+/* Build a solver for `grid` with face coefficients ax, ay, az (DEVICE, the
+ * layout above, alpha > 0 and finite off the walls).  The coefficients are
+ * copied (scaled by 1/h^2, coarsened level by level as the mean of the 4 fine
+ * faces tiling each coarse face, and the coarsest grid's inverse is formed),
+ * so the caller may free them afterwards.  `params` may be NULL (defaults).
+ * `stream` is the cudaStream_t all work of the handle runs on (NULL = the
+ * legacy default stream).  Steps 1 (operator), 2 (Eqs. 11-12 input), 6
+ * (coarsest grid) of Sec. 2.3. */
+int mg_create(const mg_grid *grid, const double *ax, const double *ay, const double *az,
+              const mg_params *params, void *stream, mg_handle **out);
+
+/* Replace the face coefficients of an existing handle (same grid): the new
+ * density of the next time step.  DEVICE pointers, same rules as mg_create.
+ * Asynchronous on the handle's stream. */
+int mg_set_faces(mg_handle *h, const double *ax, const double *ay, const double *az);
+
+/* mg_faces_from_density followed by mg_set_faces, using the handle's own face
+ * storage (no caller buffers besides rho, DEVICE).  Asynchronous. */
+int mg_set_density(mg_handle *h, const double *rho, int mode);
+
+/* Solve A p = rhs to ||rhs - A p|| <= tol ||rhs|| (after removing the mean of
+ * rhs).  rhs and p are DEVICE arrays of nx*ny*nz doubles; p is the starting
+ * iterate on entry (warm start; zeros for a cold start) and the zero-mean
+ * solution on exit.  rhs is not modified.  Synchronous: returns when the solve
+ * has finished on the handle's stream.  `st` may be NULL.  Returns MG_OK,
+ * MG_ENOTCONV or MG_EDIVERGED (p then holds the last iterate) or an error. */
+int mg_solve(mg_handle *h, const double *rhs, double *p, double tol, mg_stats *st);
+
+/* Same as mg_solve with HOST arrays (pinned or pageable): copies rhs and the
+ * warm start p to the device, solves, copies p back. */
+int mg_solve_host(mg_handle *h, const double *rhs_host, double *p_host, double tol, mg_stats *st);
+
+/* mg_set_density + mg_solve_host with HOST rho: one time step's pressure solve
+ * from host data (density and right-hand side in, pressure out). */
+int mg_step_host(mg_handle *h, const double *rho_host, int mode, const double *rhs_host,
+                 double *p_host, double tol, mg_stats *st);
+
+/* Release the handle and its device memory. */
+int mg_destroy(mg_handle *h);
+
+/* ---------------------------------------------------------------------------
+ * Batched solves: many independent grids of uneven sizes advanced together,
+ * one kernel launch per V-cycle stage for the whole batch, the whole solve one
+ * CUDA-graph launch.  Each grid's arithmetic is independent of the others, so
+ * its result is bitwise the same alone and in any batch.
+ * --------------------------------------------------------------------------- */
+
+/* Group `count` handles (all with the same precision and stream) into a batch.
+ * The batch does not own the handles; destroy the batch before them. */
+int mg_batch_create(mg_handle *const *handles, int count, mg_batch **out);
+
+/* Solve every grid of the batch: rhs[g], p[g] DEVICE arrays as in mg_solve,
+ * tol per grid; st (may be NULL) receives `count` records.  Returns MG_OK if
+ * every grid converged, else the first failing status. */
+int mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *p, const double *tol,
+                   mg_stats *st);
+
+int mg_batch_destroy(mg_batch *b);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop on a host thread that admits queued solves as slots
+ * and device memory (an HBM budget) allow, keeps hierarchies of finished
+ * requests for reuse by later requests of the same size, and advances all
+ * admitted requests together one V-cycle at a time (continuous batching):
+ * requests join and leave between cycles.
+ * --------------------------------------------------------------------------- */
+
+/* hbm_budget_bytes: most device memory the server's hierarchies may hold;
+ * max_slots: most requests on the GPU at once; params: precision etc. (NULL =
+ * defaults); stream: cudaStream_t of the server's work (NULL = its own). */
+int mg_server_create(size_t hbm_budget_bytes, int max_slots, const mg_params *params,
+                     void *stream, mg_server **out);
+
+/* Queue a solve.  grid, the face coefficients ax/ay/az, rhs and p are as in
+ * mg_create/mg_solve (DEVICE); they must stay valid and unmodified until
+ * mg_poll reports the ticket finished.  Returns MG_EBUDGET if the request can
+ * never fit in the budget. */
+int mg_submit(mg_server *s, const mg_grid *grid, const double *ax, const double *ay,
+              const double *az, const double *rhs, double *p, double tol, mg_ticket *out);
+
+/* MG_EAGAIN while the ticket is queued or running; otherwise the solve's final
+ * status (MG_OK, MG_ENOTCONV, ...) and its statistics, after which the ticket
+ * is forgotten (MG_ENOTFOUND on a second poll).  st may be NULL; st->ms is the
+ * latency from submission to completion. */
+int mg_poll(mg_server *s, mg_ticket t, mg_stats *st);
+
+/* Block until every submitted ticket has finished. */
+int mg_server_drain(mg_server *s);
+
+/* Statistics of the server: completed requests, bytes of hierarchies held,
+ * peak bytes, most requests in flight at once. */
+int mg_server_info(mg_server *s, int64_t *completed, size_t *bytes_in_use, size_t *peak_bytes,
+                   int *max_in_flight);
+
+/* Stops the loop; returns MG_EBUSY (and does nothing) if tickets are pending. */
+int mg_server_destroy(mg_server *s);
+
+/* ---------------------------------------------------------------------------
+ * Single steps of the V-cycle, for unit checks of each kernel.  `level` 0 is
+ * the finest grid.  Vectors are DEVICE arrays of the level's cell count, in
+ * FP64 when prec = MG_PREC_FP64 and FP32 when prec = MG_PREC_MIXED (the
+ * precision the V-cycle of a mixed handle runs in).  Synchronous.
+ * --------------------------------------------------------------------------- */
+
+int mg_num_levels(const mg_handle *h, int *levels);
+int mg_level_shape(const mg_handle *h, int level, int *nx, int *ny, int *nz);
+
+/* Scaled coefficients w_d = alpha_d / h_d^2 of `level` (FP64, DEVICE out). */
+int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double *wz);
+
+/* y = A_level x (Eq. 10 / h^2 on that level). */
+int mg_apply(mg_handle *h, int level, int prec, const void *x, void *y);
+
+/* `half_sweeps` red-black half-sweeps on x (red = (i+j+k) even first, then
+ * alternating), relaxation factor of the handle (Sec. 2.3 item 5). */
+int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int half_sweeps);
+
+/* coarse_b = mean over the 8 children of (b - A x) on `level` (item 3). */
+int mg_restrict_residual(mg_handle *h, int level, int prec, const void *b, const void *x,
+                         void *coarse_b);
+
+/* x += trilinear prolongation of the coarse error e of level+1 (item 4). */
+int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x);
+
+/* e = zero-mean solution of A e = r - mean(r) on the coarsest level (item 6). */
+int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e);
+
+/* ---------------------------------------------------------------------------
+ * Timing of individual kernels.  While enabled, every kernel launch of the
+ * handle is bracketed by CUDA events on its stream (solves then run as a
+ * host-driven loop, not a graph).  mg_profile_read returns, for kernel class
+ * `kind` (see below) on `level`, the number of launches and their summed
+ * duration in ms since the last reset.
+ * --------------------------------------------------------------------------- */
+#define MG_K_SMOOTH 0
+#define MG_K_RESTRICT 1
+#define MG_K_PROLONG 2
+#define MG_K_COARSE 3
+#define MG_K_RESIDUAL 4 /* the FP64 outer update + residual + norms */
+#define MG_K_OTHER 5
+#define MG_K_KINDS 6
+
+int mg_profile_enable(mg_handle *h, int enable);
+int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double *total_ms);
+
+/* Bytes of device memory the handle holds. */
+int mg_memory_bytes(const mg_handle *h, size_t *bytes);
+
+/* Bytes of device memory a handle for `grid` with `params` would hold. */
+int mg_memory_estimate(const mg_grid *grid, const mg_params *params, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBMG_H */

@@ -1,0 +1,1130 @@
+// mg_api.cu -- C ABI of the GB300 pressure multigrid (include/gbmg.h).
+//
+// A handle owns the hierarchy of one grid; a Plan holds the launch tables of
+// one or more handles (a single solve is a plan of one grid, a batch a plan of
+// many) and runs the FP64 outer iteration of Sec. 2.3 of arXiv 1410.8568 with
+// the V-cycle either as a host-driven loop or as one CUDA-graph launch whose
+// loop is a device-side conditional `while` node.
+#include "gbmg.h"
+#include "mg_api_internal.h"
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+using namespace gbmg;
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            gbmg::note_cuda_error(e_);                \
+            return MG_ECUDA;                          \
+        }                                             \
+    } while (0)
+
+namespace gbmg {
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+void note_cuda_error(cudaError_t e) { g_last_cuda = e; }
+cudaError_t last_cuda_error() { return g_last_cuda; }
+
+size_t Carve::take(size_t bytes)
+{
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+}
+
+int make_levels(const mg_grid &g, int n[][3], int *L)
+{
+    n[0][0] = g.nx;
+    n[0][1] = g.ny;
+    n[0][2] = g.nz;
+    int l = 1;
+    while (l < MG_MAX_LEVELS) {
+        const int *p = n[l - 1];
+        bool ok = true;
+        for (int d = 0; d < 3; d++)
+            if (p[d] % 2 != 0 || p[d] <= 4) ok = false;
+        if (!ok) break;
+        for (int d = 0; d < 3; d++) n[l][d] = p[d] / 2;
+        l++;
+    }
+    *L = l;
+    const long long nc = (long long)n[l - 1][0] * n[l - 1][1] * n[l - 1][2];
+    return nc <= kMaxCoarse ? MG_OK : MG_EINVAL;
+}
+
+int check_grid(const mg_grid *g)
+{
+    if (!g) return MG_EINVAL;
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const double l[3] = {g->lx, g->ly, g->lz};
+    for (int d = 0; d < 3; d++) {
+        if (n[d] < 2 || n[d] > (1 << 16)) return MG_EINVAL;
+        if (!(l[d] > 0.0) || !isfinite(l[d])) return MG_EINVAL;
+        if (g->bc[d] != MG_BC_NEUMANN && g->bc[d] != MG_BC_PERIODIC) return MG_EINVAL;
+    }
+    if ((long long)n[0] * n[1] * n[2] > (1LL << 34)) return MG_EINVAL;
+    int lv[MG_MAX_LEVELS][3], L;
+    return make_levels(*g, lv, &L);
+}
+
+int check_params(const mg_params *p)
+{
+    if (p->nu1 < 1 || p->nu1 > 16 || p->nu2 < 0 || p->nu2 > 16) return MG_EINVAL;
+    if (!(p->omega > 0.0 && p->omega < 2.0)) return MG_EINVAL;
+    if (p->max_iters < 1 || p->max_iters > 100000) return MG_EINVAL;
+    if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) return MG_EINVAL;
+    return MG_OK;
+}
+
+// Byte layout of a handle's device slab (also used for the memory estimate).
+struct Layout {
+    int L;
+    int n[MG_MAX_LEVELS][3];
+    size_t w64[MG_MAX_LEVELS][3], w32[MG_MAX_LEVELS][3], x[MG_MAX_LEVELS], b[MG_MAX_LEVELS];
+    size_t G, xbuf, part, err, state, dstate, dview, dstart, dcview, total;
+    int nblk0;
+};
+
+static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
+{
+    int rc = make_levels(g, lay.n, &lay.L);
+    if (rc) return rc;
+    const bool mixed = p.precision == MG_PREC_MIXED;
+    const size_t vs = mixed ? 4 : 8;
+    Carve c;
+    for (int l = 0; l < lay.L; l++) {
+        const size_t N = (size_t)lay.n[l][0] * lay.n[l][1] * lay.n[l][2];
+        for (int d = 0; d < 3; d++) lay.w64[l][d] = c.take(N * 8);
+        for (int d = 0; d < 3; d++) lay.w32[l][d] = mixed ? c.take(N * 4) : 0;
+        lay.x[l] = c.take(N * vs);
+        lay.b[l] = c.take(N * vs);
+    }
+    const int *nc = lay.n[lay.L - 1];
+    const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
+    lay.G = c.take(ncells * ncells * 8);
+    const size_t N0 = (size_t)g.nx * g.ny * g.nz;
+    lay.xbuf = c.take(N0 * 8);
+    const int n0[3] = {g.nx, g.ny, g.nz};
+    lay.nblk0 = fine_blocks(n0);
+    lay.part = c.take((size_t)lay.nblk0 * kPart * 8);
+    lay.err = c.take(16 * sizeof(int));
+    lay.state = c.take(sizeof(GridState));
+    lay.dstate = c.take(sizeof(GridState));
+    lay.dview = c.take(sizeof(LevelView));
+    lay.dstart = c.take(2 * sizeof(int));
+    lay.dcview = c.take(sizeof(CoarseView));
+    lay.total = c.off;
+    return MG_OK;
+}
+
+}  // namespace gbmg
+
+// ---------------------------------------------------------------------------
+// Plan: launch tables over one or more handles
+// ---------------------------------------------------------------------------
+
+namespace gbmg {
+
+static int per_bits(const mg_grid &g)
+{
+    return (g.bc[0] == MG_BC_PERIODIC ? 1 : 0) | (g.bc[1] == MG_BC_PERIODIC ? 2 : 0) |
+           (g.bc[2] == MG_BC_PERIODIC ? 4 : 0);
+}
+
+void Plan::release()
+{
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+    if (mem) cudaFree(mem);
+    mem = nullptr;
+    if (ov_h) cudaFreeHost(ov_h);
+    if (st_h) cudaFreeHost(st_h);
+    ov_h = nullptr;
+    st_h = nullptr;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    e0 = e1 = nullptr;
+}
+
+int Plan::build(mg_handle *const *handles, int count)
+{
+    hs.assign(handles, handles + count);
+    G = count;
+    mixed = hs[0]->mixed;
+    stream = hs[0]->stream;
+    prm = hs[0]->prm;
+    Lmax = 0;
+    for (auto *h : hs) Lmax = std::max(Lmax, h->L);
+    // host copies of the tables
+    std::vector<LevelView> lv;
+    std::vector<int> starts;
+    struct Range { int lv0, count, sf, sc, bf, bc; };
+    std::vector<Range> ranges(Lmax);
+    for (int l = 0; l + 1 < Lmax; l++) {
+        Range r{(int)lv.size(), 0, 0, 0, 0, 0};
+        std::vector<int> sf{0}, sc{0};
+        for (int g = 0; g < G; g++) {
+            mg_handle *h = hs[g];
+            if (l + 1 >= h->L) continue;
+            const HLevel &F = h->lev[l], &C = h->lev[l + 1];
+            LevelView v;
+            memset(&v, 0, sizeof(v));
+            for (int d = 0; d < 3; d++) {
+                v.n[d] = F.n[d];
+                v.nc[d] = C.n[d];
+                v.w[d] = mixed ? (void *)F.w32[d] : (void *)F.w64[d];
+            }
+            v.per = h->per;
+            v.x = F.x;
+            v.b = F.b;
+            v.xc = C.x;
+            v.bc = C.b;
+            v.st = h->state;
+            lv.push_back(v);
+            sf.push_back(sf.back() + fine_blocks(F.n));
+            sc.push_back(sc.back() + coarse_blocks(C.n));
+            r.count++;
+        }
+        r.sf = (int)starts.size();
+        starts.insert(starts.end(), sf.begin(), sf.end());
+        r.sc = (int)starts.size();
+        starts.insert(starts.end(), sc.begin(), sc.end());
+        r.bf = sf.back();
+        r.bc = sc.back();
+        ranges[l] = r;
+    }
+    std::vector<int> so{0};
+    for (int g = 0; g < G; g++) so.push_back(so.back() + hs[g]->nblk0);
+    const int so_off = (int)starts.size();
+    starts.insert(starts.end(), so.begin(), so.end());
+
+    Carve c;
+    const size_t o_lv = c.take(std::max<size_t>(1, lv.size()) * sizeof(LevelView));
+    const size_t o_st = c.take(starts.size() * sizeof(int));
+    const size_t o_cv = c.take(G * sizeof(CoarseView));
+    const size_t o_ov = c.take(G * sizeof(OuterView));
+    const size_t o_gs = c.take(G * sizeof(GridState));
+    CK(cudaMalloc((void **)&mem, c.off));
+    LevelView *d_lv = (LevelView *)(mem + o_lv);
+    int *d_starts = (int *)(mem + o_st);
+    cv = (CoarseView *)(mem + o_cv);
+    ov = (OuterView *)(mem + o_ov);
+    st = (GridState *)(mem + o_gs);
+    for (int l = 0; l < MG_MAX_LEVELS; l++) {
+        down[l] = Table{d_lv, d_starts, 0, 0};
+        rest[l] = down[l];
+    }
+    for (int l = 0; l + 1 < Lmax; l++) {
+        const Range &r = ranges[l];
+        down[l] = Table{d_lv + r.lv0, d_starts + r.sf, r.count, r.bf};
+        rest[l] = Table{d_lv + r.lv0, d_starts + r.sc, r.count, r.bc};
+    }
+    ot = OuterTable{ov, d_starts + so_off, G, so.back()};
+    std::vector<CoarseView> cvh(G);
+    for (int g = 0; g < G; g++) {
+        mg_handle *h = hs[g];
+        const HLevel &Cl = h->lev[h->L - 1];
+        CoarseView &v = cvh[g];
+        memset(&v, 0, sizeof(v));
+        for (int d = 0; d < 3; d++) {
+            v.n[d] = Cl.n[d];
+            v.w[d] = Cl.w64[d];
+        }
+        v.per = h->per;
+        v.nc = (int)Cl.N;
+        v.G = h->G;
+        v.x = Cl.x;
+        v.b = Cl.b;
+        v.st = h->state;
+        v.err = h->err + 1;
+    }
+    CK(cudaMallocHost((void **)&ov_h, G * sizeof(OuterView)));
+    CK(cudaMallocHost((void **)&st_h, G * sizeof(GridState)));
+    for (int g = 0; g < G; g++) {
+        mg_handle *h = hs[g];
+        OuterView &v = ov_h[g];
+        memset(&v, 0, sizeof(v));
+        for (int d = 0; d < 3; d++) {
+            v.n[d] = h->lev[0].n[d];
+            v.w[d] = h->lev[0].w64[d];
+        }
+        v.per = h->per;
+        v.xbuf = h->xbuf;
+        v.e = h->lev[0].x;
+        v.r = h->lev[0].b;
+        v.part = h->part;
+        v.nblk = h->nblk0;
+        v.st = h->state;
+        v.tol = 1e-10;
+        v.max_iters = h->prm.max_iters;
+    }
+    if (!lv.empty()) CK(cudaMemcpy(d_lv, lv.data(), lv.size() * sizeof(LevelView), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_starts, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(cv, cvh.data(), G * sizeof(CoarseView), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ov, ov_h, G * sizeof(OuterView), cudaMemcpyHostToDevice));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    return MG_OK;
+}
+
+// ---- profiling: events around launches -------------------------------------
+
+void Prof::begin(cudaStream_t s, int kind, int level)
+{
+    if (!on) return;
+    if (used + 2 > pool.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        pool.push_back(a);
+        pool.push_back(b);
+    }
+    cur_kind = kind;
+    cur_level = std::min(level, MG_MAX_LEVELS - 1);
+    cudaEventRecord(pool[used], s);
+}
+
+void Prof::end(cudaStream_t s)
+{
+    if (!on) return;
+    cudaEventRecord(pool[used + 1], s);
+    pending.push_back({cur_kind, cur_level, (int)used});
+    used += 2;
+}
+
+void Prof::collect()
+{
+    for (auto &p : pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pool[p.ev], pool[p.ev + 1]) == cudaSuccess) {
+            total_ms[p.kind][p.level] += ms;
+            launches[p.kind][p.level] += 1;
+        }
+    }
+    pending.clear();
+    used = 0;
+}
+
+void Prof::reset()
+{
+    memset(total_ms, 0, sizeof(total_ms));
+    memset(launches, 0, sizeof(launches));
+}
+
+Prof::~Prof()
+{
+    for (auto e : pool) cudaEventDestroy(e);
+}
+
+// ---- the V-cycle and the outer iteration -----------------------------------
+
+template <class T>
+static void vcycle(Plan &P, Prof &pf)
+{
+    const cudaStream_t s = P.stream;
+    const mg_params &q = P.prm;
+    for (int l = 0; l + 1 < P.Lmax; l++) {
+        const Table &D = P.down[l];
+        if (D.count == 0) continue;
+        for (int it = 0; it < q.nu1; it++) {
+            pf.begin(s, MG_K_SMOOTH, l);
+            launch_smooth<T>(D, 0, q.omega, it == 0, s);
+            pf.end(s);
+            pf.begin(s, MG_K_SMOOTH, l);
+            launch_smooth<T>(D, 1, q.omega, 0, s);
+            pf.end(s);
+        }
+        pf.begin(s, MG_K_RESTRICT, l);
+        launch_restrict<T>(P.rest[l], s);
+        pf.end(s);
+    }
+    pf.begin(s, MG_K_COARSE, P.Lmax - 1);
+    launch_coarse_solve<T>(P.cv, P.G, s);
+    pf.end(s);
+    for (int l = P.Lmax - 2; l >= 0; l--) {
+        const Table &D = P.down[l];
+        if (D.count == 0) continue;
+        pf.begin(s, MG_K_PROLONG, l);
+        launch_prolong<T>(D, s);
+        pf.end(s);
+        for (int it = 0; it < q.nu2; it++) {
+            pf.begin(s, MG_K_SMOOTH, l);
+            launch_smooth<T>(D, 0, q.omega, 0, s);
+            pf.end(s);
+            pf.begin(s, MG_K_SMOOTH, l);
+            launch_smooth<T>(D, 1, q.omega, 0, s);
+            pf.end(s);
+        }
+    }
+}
+
+template <class T>
+static void prologue(Plan &P, Prof &pf)
+{
+    const cudaStream_t s = P.stream;
+    pf.begin(s, MG_K_OTHER, 0);
+    launch_begin(P.ov, P.G, s);
+    launch_bsum(P.ot, s);
+    launch_finalize(P.ot, 0, s);
+    pf.end(s);
+    pf.begin(s, MG_K_RESIDUAL, 0);
+    launch_residual<T>(P.ot, 0, s);
+    pf.end(s);
+    pf.begin(s, MG_K_OTHER, 0);
+    launch_finalize(P.ot, 1, s);
+    pf.end(s);
+}
+
+template <class T>
+static void body(Plan &P, Prof &pf)
+{
+    const cudaStream_t s = P.stream;
+    vcycle<T>(P, pf);
+    pf.begin(s, MG_K_RESIDUAL, 0);
+    launch_residual<T>(P.ot, 1, s);
+    pf.end(s);
+    pf.begin(s, MG_K_OTHER, 0);
+    launch_finalize(P.ot, 2, s);
+    pf.end(s);
+}
+
+template <class T>
+static int build_graph(Plan &P)
+{
+    Prof off;  // no events inside graphs
+    cudaStream_t cs = P.capture_stream;
+    if (!cs) {
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        P.capture_stream = cs;
+    }
+    Plan Q = P;  // same tables, launches go to the capture stream
+    Q.stream = cs;
+    Q.mem = nullptr;
+    Q.ov_h = nullptr;
+    Q.st_h = nullptr;
+    Q.e0 = Q.e1 = nullptr;
+    Q.graph = nullptr;
+    Q.gexec = nullptr;
+    cudaGraph_t main_g = nullptr, pro_g = nullptr, body_g = nullptr, epi_g = nullptr;
+    CK(cudaGraphCreate(&main_g, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, main_g, 0, cudaGraphCondAssignDefault));
+    // prologue
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    prologue<T>(Q, off);
+    launch_loop_ctl(cond, Q.ot, cs);
+    CK(cudaStreamEndCapture(cs, &pro_g));
+    // loop body
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    body<T>(Q, off);
+    launch_loop_ctl(cond, Q.ot, cs);
+    CK(cudaStreamEndCapture(cs, &body_g));
+    // epilogue
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    launch_final(Q.ot, cs);
+    CK(cudaStreamEndCapture(cs, &epi_g));
+    cudaGraphNode_t n_pro, n_loop, n_epi, n_inner;
+    CK(cudaGraphAddChildGraphNode(&n_pro, main_g, nullptr, 0, pro_g));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CK(cudaGraphAddNode(&n_loop, main_g, &n_pro, nullptr, 1, &cp));
+    cudaGraph_t loop_body = cp.conditional.phGraph_out[0];
+    CK(cudaGraphAddChildGraphNode(&n_inner, loop_body, nullptr, 0, body_g));
+    CK(cudaGraphAddChildGraphNode(&n_epi, main_g, &n_loop, 1, epi_g));
+    cudaGraphDestroy(pro_g);
+    cudaGraphDestroy(body_g);
+    cudaGraphDestroy(epi_g);
+    CK(cudaGraphInstantiate(&P.gexec, main_g, 0));
+    P.graph = main_g;
+    return MG_OK;
+}
+
+template <class T>
+static int run_plan_t(Plan &P, Prof &pf, bool use_graph)
+{
+    const cudaStream_t s = P.stream;
+    CK(cudaMemcpyAsync(P.ov, P.ov_h, P.G * sizeof(OuterView), cudaMemcpyHostToDevice, s));
+    if (use_graph && !pf.on) {
+        if (!P.gexec) {
+            int rc = build_graph<T>(P);
+            if (rc) return rc;
+        }
+        CK(cudaEventRecord(P.e0, s));
+        CK(cudaGraphLaunch(P.gexec, s));
+        CK(cudaEventRecord(P.e1, s));
+    } else {
+        CK(cudaEventRecord(P.e0, s));
+        prologue<T>(P, pf);
+        int max_it = 0;
+        for (auto *h : P.hs) max_it = std::max(max_it, h->prm.max_iters);
+        for (int it = 0; it <= max_it; it++) {
+            launch_gather_states(P.ot, P.st, s);
+            CK(cudaMemcpyAsync(P.st_h, P.st, P.G * sizeof(GridState), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            bool any = false;
+            for (int g = 0; g < P.G; g++) any |= P.st_h[g].active != 0;
+            if (!any) break;
+            body<T>(P, pf);
+        }
+        pf.begin(s, MG_K_OTHER, 0);
+        launch_final(P.ot, s);
+        pf.end(s);
+        CK(cudaEventRecord(P.e1, s));
+    }
+    CK(cudaGetLastError());
+    launch_gather_states(P.ot, P.st, s);
+    CK(cudaMemcpyAsync(P.st_h, P.st, P.G * sizeof(GridState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    pf.collect();
+    return MG_OK;
+}
+
+void plan_bind(Plan &P, int g, const double *rhs, double *p, double tol, int max_iters)
+{
+    P.ov_h[g].b = rhs;
+    P.ov_h[g].p = p;
+    P.ov_h[g].tol = tol;
+    P.ov_h[g].max_iters = max_iters;
+}
+
+int plan_upload(Plan &P)
+{
+    CK(cudaMemcpyAsync(P.ov, P.ov_h, P.G * sizeof(OuterView), cudaMemcpyHostToDevice, P.stream));
+    return MG_OK;
+}
+
+static Prof g_no_prof;
+
+int plan_prologue(Plan &P)
+{
+    if (P.mixed) prologue<float>(P, g_no_prof);
+    else prologue<double>(P, g_no_prof);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+int plan_body(Plan &P)
+{
+    if (P.mixed) body<float>(P, g_no_prof);
+    else body<double>(P, g_no_prof);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+int plan_final(Plan &P)
+{
+    launch_final(P.ot, P.stream);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+int plan_sync_states(Plan &P)
+{
+    launch_gather_states(P.ot, P.st, P.stream);
+    CK(cudaMemcpyAsync(P.st_h, P.st, P.G * sizeof(GridState), cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    return MG_OK;
+}
+
+void fill_stats(const GridState &s, const int herr[2], double ms, mg_stats *o, int *status_out)
+{
+    int status = s.status;
+    if (herr[0]) status = MG_EINVAL;
+    else if (herr[1]) status = MG_ESINGULAR;
+    if (o) {
+        o->iters = s.iters;
+        o->status = status;
+        o->res0 = s.r0;
+        o->res = s.rnorm;
+        o->bnorm = s.bnorm;
+        o->rel_res = s.bnorm > 0.0 ? s.rnorm / s.bnorm : 0.0;
+        o->gamma = (s.iters > 0 && s.r0 > 0.0) ? pow(s.rnorm / s.r0, 1.0 / s.iters) : 0.0;
+        o->rhs_mean = s.bmean;
+        o->ms = ms;
+    }
+    *status_out = status;
+}
+
+int run_plan(Plan &P, Prof &pf, const double *const *rhs, double *const *p, const double *tol,
+             mg_stats *out)
+{
+    for (int g = 0; g < P.G; g++) {
+        if (!rhs[g] || !p[g] || !(tol[g] >= 0.0)) return MG_EINVAL;
+        P.ov_h[g].b = rhs[g];
+        P.ov_h[g].p = p[g];
+        P.ov_h[g].tol = tol[g];
+        P.ov_h[g].max_iters = P.hs[g]->prm.max_iters;
+    }
+    const bool use_graph = P.prm.use_graph != 0;
+    int rc = P.mixed ? run_plan_t<float>(P, pf, use_graph) : run_plan_t<double>(P, pf, use_graph);
+    if (rc) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P.e0, P.e1);
+    int first_bad = MG_OK;
+    for (int g = 0; g < P.G; g++) {
+        // coefficient problems found on the device by mg_set_faces / mg_set_density
+        int herr[2] = {0, 0};
+        cudaMemcpy(herr, P.hs[g]->err, sizeof(herr), cudaMemcpyDeviceToHost);
+        int status;
+        fill_stats(P.st_h[g], herr, ms, out ? &out[g] : nullptr, &status);
+        if (status != MG_OK && first_bad == MG_OK) first_bad = status;
+    }
+    return first_bad;
+}
+
+}  // namespace gbmg
+
+// ---------------------------------------------------------------------------
+// handle life cycle
+// ---------------------------------------------------------------------------
+
+static int upload_faces(mg_handle *h)
+{
+    // coarse levels: mean of the 4 fine faces tiling each coarse face
+    for (int l = 1; l < h->L; l++) {
+        CoarsenArgs a;
+        memset(&a, 0, sizeof(a));
+        for (int d = 0; d < 3; d++) {
+            a.nf[d] = h->lev[l - 1].n[d];
+            a.nc[d] = h->lev[l].n[d];
+            a.wf[d] = h->lev[l - 1].w64[d];
+            a.wc[d] = h->lev[l].w64[d];
+            a.wc32[d] = h->mixed ? h->lev[l].w32[d] : nullptr;
+        }
+        launch_coarsen_faces(a, h->stream);
+    }
+    launch_coarse_setup(h->plan->cv, 1, h->stream);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+int gbmg::set_faces_impl(mg_handle *h, const double *ax, const double *ay, const double *az)
+{
+    if (!ax || !ay || !az) return MG_EINVAL;
+    CK(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
+    FaceArgs a;
+    memset(&a, 0, sizeof(a));
+    const double *in[3] = {ax, ay, az};
+    for (int d = 0; d < 3; d++) {
+        a.n[d] = h->lev[0].n[d];
+        a.in[d] = in[d];
+        a.scale[d] = 1.0 / (h->lev[0].h[d] * h->lev[0].h[d]);
+        a.out64[d] = h->lev[0].w64[d];
+        a.out32[d] = h->mixed ? h->lev[0].w32[d] : nullptr;
+    }
+    a.per = h->per;
+    a.err = h->err;
+    launch_scale_faces(a, h->stream);
+    return upload_faces(h);
+}
+
+static int set_density_impl(mg_handle *h, const double *rho, int mode)
+{
+    if (!rho || (mode != MG_FACE_HARMONIC && mode != MG_FACE_ARITHMETIC)) return MG_EINVAL;
+    CK(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
+    FaceArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int d = 0; d < 3; d++) {
+        a.n[d] = h->lev[0].n[d];
+        a.scale[d] = 1.0 / (h->lev[0].h[d] * h->lev[0].h[d]);
+        a.out64[d] = h->lev[0].w64[d];
+        a.out32[d] = h->mixed ? h->lev[0].w32[d] : nullptr;
+    }
+    a.per = h->per;
+    a.mode = mode;
+    a.rho = rho;
+    a.err = h->err;
+    launch_faces_from_density(a, h->stream);
+    return upload_faces(h);
+}
+
+int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *stream, mg_handle **out)
+{
+    if (!out) return MG_EINVAL;
+    *out = nullptr;
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    mg_params prm;
+    mg_params_default(&prm);
+    if (params) prm = *params;
+    rc = check_params(&prm);
+    if (rc) return rc;
+    Layout lay;
+    rc = plan_layout(*grid, prm, lay);
+    if (rc) return rc;
+    mg_handle *h = new (std::nothrow) mg_handle();
+    if (!h) return MG_ENOMEM;
+    h->g = *grid;
+    h->prm = prm;
+    h->stream = (cudaStream_t)stream;
+    h->per = per_bits(*grid);
+    h->mixed = prm.precision == MG_PREC_MIXED;
+    CK(cudaGetDevice(&h->device));
+    cudaError_t e = cudaMalloc((void **)&h->slab, lay.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MG_ENOMEM;
+    }
+    h->bytes = lay.total;
+    h->L = lay.L;
+    const double len[3] = {grid->lx, grid->ly, grid->lz};
+    for (int l = 0; l < lay.L; l++) {
+        HLevel &L = h->lev[l];
+        for (int d = 0; d < 3; d++) {
+            L.n[d] = lay.n[l][d];
+            L.h[d] = len[d] / lay.n[l][d];
+            L.w64[d] = (double *)(h->slab + lay.w64[l][d]);
+            L.w32[d] = h->mixed ? (float *)(h->slab + lay.w32[l][d]) : nullptr;
+        }
+        L.N = (long long)L.n[0] * L.n[1] * L.n[2];
+        L.x = h->slab + lay.x[l];
+        L.b = h->slab + lay.b[l];
+    }
+    h->G = (double *)(h->slab + lay.G);
+    h->xbuf = (double *)(h->slab + lay.xbuf);
+    h->part = (double *)(h->slab + lay.part);
+    h->nblk0 = lay.nblk0;
+    h->err = (int *)(h->slab + lay.err);
+    h->state = (GridState *)(h->slab + lay.state);
+    h->dstate = (GridState *)(h->slab + lay.dstate);
+    h->dview = (LevelView *)(h->slab + lay.dview);
+    h->dstart = (int *)(h->slab + lay.dstart);
+    h->dcview = (CoarseView *)(h->slab + lay.dcview);
+    GridState ds;
+    memset(&ds, 0, sizeof(ds));
+    ds.active = 1;
+    CK(cudaMemcpy(h->dstate, &ds, sizeof(ds), cudaMemcpyHostToDevice));
+    CK(cudaMemset(h->state, 0, sizeof(GridState)));
+    CK(cudaMemset(h->err, 0, 16 * sizeof(int)));
+    h->plan = new (std::nothrow) Plan();
+    if (!h->plan) {
+        mg_destroy(h);
+        return MG_ENOMEM;
+    }
+    rc = h->plan->build(&h, 1);
+    if (rc) {
+        mg_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return MG_OK;
+}
+
+extern "C" {
+
+const char *mg_strerror(int s)
+{
+    switch (s) {
+    case MG_OK: return "ok";
+    case MG_EINVAL: return "invalid argument";
+    case MG_ENOMEM: return "out of device memory";
+    case MG_ECUDA: return "CUDA error";
+    case MG_ENOTCONV: return "not converged within max_iters";
+    case MG_EDIVERGED: return "residual became NaN or Inf";
+    case MG_ETIMEOUT: return "bounded device wait expired";
+    case MG_EBUSY: return "busy: requests outstanding";
+    case MG_EAGAIN: return "pending";
+    case MG_EBUDGET: return "request exceeds the device-memory budget";
+    case MG_ESINGULAR: return "coarsest-grid matrix is singular (grid cut by zero coefficients)";
+    case MG_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+    }
+}
+
+int mg_last_cuda_error(void) { return (int)gbmg::last_cuda_error(); }
+
+int mg_params_default(mg_params *p)
+{
+    if (!p) return MG_EINVAL;
+    p->nu1 = 2;
+    p->nu2 = 2;
+    p->omega = 1.0;
+    p->max_iters = 100;
+    p->precision = MG_PREC_MIXED;
+    p->use_graph = 1;
+    return MG_OK;
+}
+
+int mg_faces_from_density(const mg_grid *grid, const double *rho, int mode, double *ax, double *ay,
+                          double *az, void *stream)
+{
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    if (!rho || !ax || !ay || !az) return MG_EINVAL;
+    if (mode != MG_FACE_HARMONIC && mode != MG_FACE_ARITHMETIC) return MG_EINVAL;
+    FaceArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n[0] = grid->nx;
+    a.n[1] = grid->ny;
+    a.n[2] = grid->nz;
+    a.per = per_bits(*grid);
+    a.mode = mode;
+    a.rho = rho;
+    a.scale[0] = a.scale[1] = a.scale[2] = 1.0;
+    a.out64[0] = ax;
+    a.out64[1] = ay;
+    a.out64[2] = az;
+    launch_faces_from_density(a, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+int mg_create(const mg_grid *grid, const double *ax, const double *ay, const double *az,
+              const mg_params *params, void *stream, mg_handle **out)
+{
+    if (!ax || !ay || !az) return MG_EINVAL;
+    mg_handle *h = nullptr;
+    int rc = handle_alloc(grid, params, stream, &h);
+    if (rc) return rc;
+    rc = set_faces_impl(h, ax, ay, az);
+    if (rc == MG_OK) {
+        int herr[2] = {0, 0};
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            note_cuda_error(e);
+            rc = MG_ECUDA;
+        } else if (herr[0]) {
+            rc = MG_EINVAL;
+        } else if (herr[1]) {
+            rc = MG_ESINGULAR;
+        }
+    }
+    if (rc) {
+        mg_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return MG_OK;
+}
+
+int mg_set_faces(mg_handle *h, const double *ax, const double *ay, const double *az)
+{
+    if (!h) return MG_EINVAL;
+    return set_faces_impl(h, ax, ay, az);
+}
+
+int mg_set_density(mg_handle *h, const double *rho, int mode)
+{
+    if (!h) return MG_EINVAL;
+    return set_density_impl(h, rho, mode);
+}
+
+int mg_solve(mg_handle *h, const double *rhs, double *p, double tol, mg_stats *st)
+{
+    if (!h || !rhs || !p) return MG_EINVAL;
+    mg_stats tmp;
+    return run_plan(*h->plan, h->prof, &rhs, &p, &tol, st ? st : &tmp);
+}
+
+static int ensure_host_buffers(mg_handle *h, bool rho)
+{
+    const size_t n = (size_t)h->lev[0].N * sizeof(double);
+    if (!h->io_rhs) CK(cudaMalloc((void **)&h->io_rhs, n));
+    if (!h->io_p) CK(cudaMalloc((void **)&h->io_p, n));
+    if (rho && !h->io_rho) CK(cudaMalloc((void **)&h->io_rho, n));
+    return MG_OK;
+}
+
+int mg_solve_host(mg_handle *h, const double *rhs_host, double *p_host, double tol, mg_stats *st)
+{
+    if (!h || !rhs_host || !p_host) return MG_EINVAL;
+    int rc = ensure_host_buffers(h, false);
+    if (rc) return rc;
+    const size_t n = (size_t)h->lev[0].N * sizeof(double);
+    CK(cudaMemcpyAsync(h->io_rhs, rhs_host, n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->io_p, p_host, n, cudaMemcpyHostToDevice, h->stream));
+    rc = mg_solve(h, h->io_rhs, h->io_p, tol, st);
+    if (rc != MG_OK && rc != MG_ENOTCONV && rc != MG_EDIVERGED) return rc;
+    CK(cudaMemcpyAsync(p_host, h->io_p, n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int mg_step_host(mg_handle *h, const double *rho_host, int mode, const double *rhs_host,
+                 double *p_host, double tol, mg_stats *st)
+{
+    if (!h || !rho_host) return MG_EINVAL;
+    int rc = ensure_host_buffers(h, true);
+    if (rc) return rc;
+    const size_t n = (size_t)h->lev[0].N * sizeof(double);
+    CK(cudaMemcpyAsync(h->io_rho, rho_host, n, cudaMemcpyHostToDevice, h->stream));
+    rc = set_density_impl(h, h->io_rho, mode);
+    if (rc) return rc;
+    return mg_solve_host(h, rhs_host, p_host, tol, st);
+}
+
+int mg_destroy(mg_handle *h)
+{
+    if (!h) return MG_EINVAL;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->plan) {
+        if (h->plan->capture_stream) cudaStreamDestroy(h->plan->capture_stream);
+        h->plan->release();
+        delete h->plan;
+    }
+    if (h->io_rhs) cudaFree(h->io_rhs);
+    if (h->io_p) cudaFree(h->io_p);
+    if (h->io_rho) cudaFree(h->io_rho);
+    if (h->slab) cudaFree(h->slab);
+    delete h;
+    return MG_OK;
+}
+
+// ---- batches ----------------------------------------------------------------
+
+struct mg_batch {
+    Plan plan;
+    Prof prof;
+};
+
+int mg_batch_create(mg_handle *const *handles, int count, mg_batch **out)
+{
+    if (!handles || count < 1 || !out) return MG_EINVAL;
+    for (int g = 0; g < count; g++) {
+        if (!handles[g]) return MG_EINVAL;
+        if (handles[g]->mixed != handles[0]->mixed || handles[g]->stream != handles[0]->stream)
+            return MG_EINVAL;
+        if (handles[g]->prm.nu1 != handles[0]->prm.nu1 || handles[g]->prm.nu2 != handles[0]->prm.nu2 ||
+            handles[g]->prm.omega != handles[0]->prm.omega)
+            return MG_EINVAL;
+        for (int q = 0; q < g; q++)
+            if (handles[q] == handles[g]) return MG_EINVAL;
+    }
+    mg_batch *b = new (std::nothrow) mg_batch();
+    if (!b) return MG_ENOMEM;
+    int rc = b->plan.build(handles, count);
+    if (rc) {
+        b->plan.release();
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return MG_OK;
+}
+
+int mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *p, const double *tol,
+                   mg_stats *st)
+{
+    if (!b || !rhs || !p || !tol) return MG_EINVAL;
+    std::vector<mg_stats> tmp;
+    if (!st) {
+        tmp.resize(b->plan.G);
+        st = tmp.data();
+    }
+    return run_plan(b->plan, b->prof, rhs, p, tol, st);
+}
+
+int mg_batch_destroy(mg_batch *b)
+{
+    if (!b) return MG_EINVAL;
+    if (b->plan.stream) cudaStreamSynchronize(b->plan.stream);
+    if (b->plan.capture_stream) cudaStreamDestroy(b->plan.capture_stream);
+    b->plan.release();
+    delete b;
+    return MG_OK;
+}
+
+// ---- single steps -------------------------------------------------------------
+
+int mg_num_levels(const mg_handle *h, int *levels)
+{
+    if (!h || !levels) return MG_EINVAL;
+    *levels = h->L;
+    return MG_OK;
+}
+
+int mg_level_shape(const mg_handle *h, int level, int *nx, int *ny, int *nz)
+{
+    if (!h || level < 0 || level >= h->L || !nx || !ny || !nz) return MG_EINVAL;
+    *nx = h->lev[level].n[0];
+    *ny = h->lev[level].n[1];
+    *nz = h->lev[level].n[2];
+    return MG_OK;
+}
+
+int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double *wz)
+{
+    if (!h || level < 0 || level >= h->L || !wx || !wy || !wz) return MG_EINVAL;
+    const size_t n = (size_t)h->lev[level].N * sizeof(double);
+    double *o[3] = {wx, wy, wz};
+    for (int d = 0; d < 3; d++)
+        CK(cudaMemcpyAsync(o[d], h->lev[level].w64[d], n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b, const void *xc,
+                     void *bc, Table *tb, bool coarse_tiles)
+{
+    if (!h || level < 0 || level >= h->L) return MG_EINVAL;
+    if (prec != MG_PREC_FP64 && prec != MG_PREC_MIXED) return MG_EINVAL;
+    if (prec == MG_PREC_MIXED && !h->mixed) return MG_EINVAL;
+    LevelView v;
+    memset(&v, 0, sizeof(v));
+    const HLevel &L = h->lev[level];
+    for (int d = 0; d < 3; d++) {
+        v.n[d] = L.n[d];
+        v.w[d] = prec == MG_PREC_MIXED ? (void *)L.w32[d] : (void *)L.w64[d];
+        v.nc[d] = level + 1 < h->L ? h->lev[level + 1].n[d] : 0;
+    }
+    v.per = h->per;
+    v.x = (void *)x;
+    v.b = b;
+    v.xc = (void *)xc;
+    v.bc = bc;
+    v.st = h->dstate;
+    const int blocks = coarse_tiles ? coarse_blocks(v.nc) : fine_blocks(v.n);
+    const int starts[2] = {0, blocks};
+    CK(cudaMemcpyAsync(h->dview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, h->stream));
+    *tb = Table{h->dview, h->dstart, 1, blocks};
+    return MG_OK;
+}
+
+int mg_apply(mg_handle *h, int level, int prec, const void *x, void *y)
+{
+    if (!x || !y) return MG_EINVAL;
+    Table tb;
+    int rc = unit_view(h, level, prec, x, y, nullptr, nullptr, &tb, false);
+    if (rc) return rc;
+    if (prec == MG_PREC_MIXED) launch_apply<float>(tb, h->stream);
+    else launch_apply<double>(tb, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int half_sweeps)
+{
+    if (!x || !b || half_sweeps < 0) return MG_EINVAL;
+    if (h && level == h->L - 1 && h->L > 1) {
+        // the coarsest level is never relaxed; odd periodic sizes are allowed there
+    }
+    Table tb;
+    int rc = unit_view(h, level, prec, x, (void *)b, nullptr, nullptr, &tb, false);
+    if (rc) return rc;
+    for (int s = 0; s < half_sweeps; s++) {
+        if (prec == MG_PREC_MIXED) launch_smooth<float>(tb, s & 1, h->prm.omega, 0, h->stream);
+        else launch_smooth<double>(tb, s & 1, h->prm.omega, 0, h->stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_restrict_residual(mg_handle *h, int level, int prec, const void *b, const void *x,
+                         void *coarse_b)
+{
+    if (!x || !b || !coarse_b || !h || level + 1 >= h->L) return MG_EINVAL;
+    Table tb;
+    int rc = unit_view(h, level, prec, x, (void *)b, nullptr, coarse_b, &tb, true);
+    if (rc) return rc;
+    if (prec == MG_PREC_MIXED) launch_restrict<float>(tb, h->stream);
+    else launch_restrict<double>(tb, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x)
+{
+    if (!x || !coarse_e || !h || level + 1 >= h->L) return MG_EINVAL;
+    Table tb;
+    int rc = unit_view(h, level, prec, x, nullptr, coarse_e, nullptr, &tb, false);
+    if (rc) return rc;
+    if (prec == MG_PREC_MIXED) launch_prolong<float>(tb, h->stream);
+    else launch_prolong<double>(tb, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e)
+{
+    if (!h || !r || !e) return MG_EINVAL;
+    if (prec != MG_PREC_FP64 && prec != MG_PREC_MIXED) return MG_EINVAL;
+    if (prec == MG_PREC_MIXED && !h->mixed) return MG_EINVAL;
+    const HLevel &C = h->lev[h->L - 1];
+    CoarseView v;
+    memset(&v, 0, sizeof(v));
+    for (int d = 0; d < 3; d++) {
+        v.n[d] = C.n[d];
+        v.w[d] = C.w64[d];
+    }
+    v.per = h->per;
+    v.nc = (int)C.N;
+    v.G = h->G;
+    v.x = e;
+    v.b = r;
+    v.st = h->dstate;
+    v.err = h->err + 1;
+    CK(cudaMemcpyAsync(h->dcview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+    if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, h->stream);
+    else launch_coarse_solve<double>(h->dcview, 1, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+// ---- profiling / memory ---------------------------------------------------------
+
+int mg_profile_enable(mg_handle *h, int enable)
+{
+    if (!h) return MG_EINVAL;
+    h->prof.on = enable != 0;
+    h->prof.reset();
+    return MG_OK;
+}
+
+int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double *total_ms)
+{
+    if (!h || kind < 0 || kind >= MG_K_KINDS || level < 0 || level >= MG_MAX_LEVELS) return MG_EINVAL;
+    if (launches) *launches = h->prof.launches[kind][level];
+    if (total_ms) *total_ms = h->prof.total_ms[kind][level];
+    return MG_OK;
+}
+
+int mg_memory_bytes(const mg_handle *h, size_t *bytes)
+{
+    if (!h || !bytes) return MG_EINVAL;
+    *bytes = h->bytes;
+    return MG_OK;
+}
+
+int mg_memory_estimate(const mg_grid *grid, const mg_params *params, size_t *bytes)
+{
+    if (!bytes) return MG_EINVAL;
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    mg_params prm;
+    mg_params_default(&prm);
+    if (params) prm = *params;
+    rc = check_params(&prm);
+    if (rc) return rc;
+    Layout lay;
+    rc = plan_layout(*grid, prm, lay);
+    if (rc) return rc;
+    *bytes = lay.total;
+    return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// mg_api_internal.h -- host-side structures of the multigrid library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "gbmg.h"
+#include "mg_kernels.h"
+
+namespace gbmg {
+
+void note_cuda_error(cudaError_t e);
+cudaError_t last_cuda_error();
+
+// Bump allocator of offsets inside one device slab (256-byte aligned pieces).
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes);
+};
+
+int make_levels(const mg_grid &g, int n[][3], int *L);
+int check_grid(const mg_grid *g);
+int check_params(const mg_params *p);
+
+// One level of a handle's hierarchy.
+struct HLevel {
+    int n[3];
+    long long N;
+    double h[3];
+    double *w64[3];  // alpha / h^2, FP64
+    float *w32[3];   // FP32 copy (mixed precision only)
+    void *x;         // V-cycle iterate / correction (V-cycle precision)
+    void *b;         // V-cycle right-hand side (V-cycle precision)
+};
+
+// CUDA-event timing of kernel classes (host-driven solves only).
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    int cur_kind = 0, cur_level = 0;
+    struct Pending {
+        int kind, level, ev;
+    };
+    std::vector<Pending> pending;
+    double total_ms[MG_K_KINDS][MG_MAX_LEVELS] = {};
+    int64_t launches[MG_K_KINDS][MG_MAX_LEVELS] = {};
+    void begin(cudaStream_t s, int kind, int level);
+    void end(cudaStream_t s);
+    void collect();
+    void reset();
+    ~Prof();
+};
+
+struct Plan;
+
+}  // namespace gbmg
+
+struct mg_handle {
+    mg_grid g;
+    mg_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int per = 0;
+    bool mixed = true;
+    int L = 0;
+    gbmg::HLevel lev[MG_MAX_LEVELS];
+    double *G = nullptr;       // coarsest-grid inverse
+    double *xbuf = nullptr;    // FP64 ping-pong iterate
+    double *part = nullptr;    // reduction partials of the outer launches
+    int nblk0 = 0;
+    int *err = nullptr;        // [0] bad coefficient, [1] singular coarsest grid
+    gbmg::GridState *state = nullptr;    // solve state of this grid (kept across plans)
+    gbmg::GridState *dstate = nullptr;   // always-active state of the unit calls
+    gbmg::LevelView *dview = nullptr;    // view slot of the unit calls
+    int *dstart = nullptr;
+    gbmg::CoarseView *dcview = nullptr;
+    char *slab = nullptr;
+    size_t bytes = 0;
+    gbmg::Plan *plan = nullptr;          // single-grid launch plan
+    gbmg::Prof prof;
+    double *io_rhs = nullptr, *io_p = nullptr, *io_rho = nullptr;  // host-call staging
+};
+
+namespace gbmg {
+
+// Launch tables over one or more handles plus the per-solve state.
+struct Plan {
+    std::vector<mg_handle *> hs;
+    int G = 0;
+    int Lmax = 0;
+    bool mixed = true;
+    mg_params prm;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    char *mem = nullptr;
+    Table down[MG_MAX_LEVELS];  // smoothing / prolongation (fine tiles of level l)
+    Table rest[MG_MAX_LEVELS];  // restriction (coarse tiles of level l+1)
+    CoarseView *cv = nullptr;
+    OuterView *ov = nullptr;
+    OuterTable ot;
+    GridState *st = nullptr;    // gathered copy of the grids' states (device)
+    OuterView *ov_h = nullptr;  // pinned host mirror of ov
+    GridState *st_h = nullptr;  // pinned host mirror of st
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int build(mg_handle *const *handles, int count);
+    void release();
+};
+
+int run_plan(Plan &P, Prof &pf, const double *const *rhs, double *const *p, const double *tol,
+             mg_stats *out);
+
+// Pieces of a solve, for the serving loop (host-driven, no graph):
+// set the caller pointers of grid g of the plan (host mirror only)
+void plan_bind(Plan &P, int g, const double *rhs, double *p, double tol, int max_iters);
+// upload the host mirror of the outer views
+int plan_upload(Plan &P);
+// start of a solve for every grid of the plan (state reset, mean of b, R_0)
+int plan_prologue(Plan &P);
+// one V-cycle + FP64 update for every active grid of the plan
+int plan_body(Plan &P);
+// p = x - mean(x) for every grid of the plan
+int plan_final(Plan &P);
+// states of all grids of the plan into P.st_h (synchronises the stream)
+int plan_sync_states(Plan &P);
+// allocate a handle (no coefficients yet) / set its coefficients (async)
+int handle_alloc(const mg_grid *grid, const mg_params *params, void *stream, mg_handle **out);
+int set_faces_impl(mg_handle *h, const double *ax, const double *ay, const double *az);
+void fill_stats(const GridState &s, const int herr[2], double ms, mg_stats *o, int *status);
+
+}  // namespace gbmg

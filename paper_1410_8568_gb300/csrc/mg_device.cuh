@@ -1,0 +1,95 @@
+// mg_device.cuh -- data structures shared by the host driver and the kernels of
+// the variable-density pressure multigrid (arXiv 1410.8568, Sec. 2.3).
+//
+// Every V-cycle kernel works on a TABLE of level views: one entry per grid of
+// a batch.  A launch covers the blocks of all entries back to back; a block
+// finds its entry by binary search in the prefix array `start`.  A single
+// solve is a table of one entry, so a grid's arithmetic does not depend on
+// what else is in the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbmg {
+
+constexpr int kThreads = 256;     // threads per block of every cell kernel
+constexpr int kRowsPerBlock = 8;  // one grid row (fixed j, k) per warp
+constexpr int kSeg = 64;          // x extent of a warp's row segment (2 cells per lane)
+constexpr int kCSeg = 32;         // x extent of a warp's coarse row segment (restriction)
+constexpr int kMaxCoarse = 512;   // most cells of the coarsest grid (dense inverse)
+constexpr int kPart = 4;          // doubles of reduction partials per block
+
+// Per-grid solve state, in device memory, written only by kernels.
+struct GridState {
+    double tol;
+    double bmean;   // mean of the right-hand side (removed)
+    double bnorm;   // ||b - bmean||_2
+    double r0;      // R_0 of Eq. 15
+    double rnorm;   // current ||r||_2
+    double xmean;   // mean of the current iterate
+    int max_iters;
+    int iters;      // completed cycles; parity tells which buffer holds x
+    int status;     // gbmg status code
+    int active;     // 1 while the grid is being iterated
+};
+
+// One level of one grid as seen by the V-cycle kernels (precision T is fixed
+// by the kernel instantiation; pointers are typeless here).
+struct LevelView {
+    int n[3];
+    int per;        // bit d set: axis d periodic
+    void *w[3];     // scaled face coefficients alpha / h^2 (low face of each cell)
+    void *x;        // iterate / correction
+    void *b;        // right-hand side
+    void *xc;       // next coarser level: iterate (null at the coarsest)
+    void *bc;       // next coarser level: right-hand side
+    int nc[3];
+    const GridState *st;
+};
+
+// The finest level of one grid for the FP64 outer iteration.
+struct OuterView {
+    int n[3];
+    int per;
+    const double *w[3];  // FP64 scaled faces of level 0
+    const double *b;     // caller's right-hand side
+    double *p;           // caller's iterate / solution
+    double *xbuf;        // second FP64 iterate buffer (ping-pong with p)
+    void *e;             // level-0 correction of the V-cycle (V-cycle precision)
+    void *r;             // level-0 right-hand side of the V-cycle (V-cycle precision)
+    double *part;        // kPart doubles per block of this grid's outer launches
+    int nblk;            // blocks of this grid in an outer launch
+    GridState *st;
+    double tol;
+    int max_iters;
+};
+
+// The coarsest level of one grid.
+struct CoarseView {
+    int n[3];
+    int per;
+    int nc;              // cells
+    double *G;           // nc x nc inverse of (-A + c 1 1^T), FP64
+    const double *w[3];  // FP64 scaled faces of the coarsest level (set-up only)
+    void *x;             // solution (V-cycle precision)
+    const void *b;       // right-hand side (V-cycle precision)
+    const GridState *st;
+    int *err;            // set-up error flag (non-positive pivot)
+};
+
+// Blocks of a launch over the cells of an n[0] x n[1] x n[2] level: a block is
+// 8 rows, each row split in segments of 64 cells along x.
+__host__ __device__ inline int fine_xtiles(int nx) { return (nx + kSeg - 1) / kSeg; }
+__host__ __device__ inline int fine_blocks(const int n[3])
+{
+    return fine_xtiles(n[0]) * ((n[1] * n[2] + kRowsPerBlock - 1) / kRowsPerBlock);
+}
+// Blocks of a launch over the cells of a coarse level (32 coarse cells per warp row).
+__host__ __device__ inline int coarse_xtiles(int nx) { return (nx + kCSeg - 1) / kCSeg; }
+__host__ __device__ inline int coarse_blocks(const int n[3])
+{
+    return coarse_xtiles(n[0]) * ((n[1] * n[2] + kRowsPerBlock - 1) / kRowsPerBlock);
+}
+
+}  // namespace gbmg

@@ -1,0 +1,62 @@
+// mg_kernels.h -- host-side launchers of the multigrid kernels (mg_kernels.cu).
+#pragma once
+
+#include "mg_device.cuh"
+
+namespace gbmg {
+
+// A launch table: `count` views in device memory and the prefix `start`
+// (count + 1 entries) of their block ranges; `blocks` = start[count].
+struct Table {
+    const LevelView *lv;
+    const int *start;
+    int count;
+    int blocks;
+};
+
+struct OuterTable {
+    const OuterView *ov;
+    const int *start;
+    int count;
+    int blocks;
+};
+
+// density -> faces, or caller faces -> scaled faces: out_d = scale_d * face_d
+struct FaceArgs {
+    int n[3];
+    int per;
+    int mode;                // 0 harmonic (Eqs. 11-12), 1 arithmetic
+    const double *rho;       // density (faces_from_density)
+    const double *in[3];     // caller faces (scale_faces)
+    double scale[3];         // 1 for raw alpha, 1/h_d^2 for level-0 coefficients
+    double *out64[3];
+    float *out32[3];         // optional FP32 copy
+    int *err;                // set to 1 on a non-positive / non-finite value
+};
+
+struct CoarsenArgs {
+    int nf[3];
+    int nc[3];
+    const double *wf[3];
+    double *wc[3];
+    float *wc32[3];
+};
+
+template <class T> void launch_smooth(const Table &, int colour, double omega, int zero_guess, cudaStream_t);
+template <class T> void launch_restrict(const Table &, cudaStream_t);
+template <class T> void launch_prolong(const Table &, cudaStream_t);
+template <class T> void launch_apply(const Table &, cudaStream_t);
+template <class T> void launch_coarse_solve(const CoarseView *, int count, cudaStream_t);
+void launch_coarse_setup(const CoarseView *, int count, cudaStream_t);
+void launch_faces_from_density(const FaceArgs &, cudaStream_t);
+void launch_scale_faces(const FaceArgs &, cudaStream_t);
+void launch_coarsen_faces(const CoarsenArgs &, cudaStream_t);
+void launch_begin(const OuterView *, int count, cudaStream_t);
+void launch_bsum(const OuterTable &, cudaStream_t);
+template <class Te> void launch_residual(const OuterTable &, int update, cudaStream_t);
+void launch_finalize(const OuterTable &, int mode, cudaStream_t);
+void launch_final(const OuterTable &, cudaStream_t);
+void launch_gather_states(const OuterTable &, GridState *out, cudaStream_t);
+void launch_loop_ctl(cudaGraphConditionalHandle, const OuterTable &, cudaStream_t);
+
+}  // namespace gbmg

@@ -1,0 +1,420 @@
+"""ctypes binding of libgbmg.so (C ABI in include/gbmg.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of
+the library.  Device arrays are torch CUDA tensors (float64 unless a call says
+otherwise), shape (nz, ny, nx) or flat, contiguous; the binding passes their
+data pointers and the current torch stream.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+
+Shin, Chergui & Juric, arXiv 1410.8568, Sec. 2.3 (pressure equation Eq. 9,
+discretisation Eqs. 10-12, V-cycle multigrid, reduction rate Eq. 15).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgbmg.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EDIVERGED, ETIMEOUT, EBUSY, EAGAIN, EBUDGET, ESINGULAR, ENOTFOUND = range(12)
+NEUMANN, PERIODIC = 0, 1
+FP64, MIXED = 0, 1
+HARMONIC, ARITHMETIC = 0, 1
+K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER = range(6)
+
+
+class MGError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (status %d, cuda error %d)" % (what, strerror(code), code, last_cuda_error()))
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("bc", ctypes.c_int * 3)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("res0", ctypes.c_double), ("res", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("bnorm", ctypes.c_double), ("rhs_mean", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_V = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_P = ctypes.POINTER
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgbmg.so is not built (run python -m paper_1410_8568_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "mg_strerror": (ctypes.c_char_p, [_I]),
+            "mg_last_cuda_error": (_I, []),
+            "mg_params_default": (_I, [_P(Params)]),
+            "mg_faces_from_density": (_I, [_P(Grid), _V, _I, _V, _V, _V, _V]),
+            "mg_create": (_I, [_P(Grid), _V, _V, _V, _P(Params), _V, _P(_V)]),
+            "mg_set_faces": (_I, [_V, _V, _V, _V]),
+            "mg_set_density": (_I, [_V, _V, _I]),
+            "mg_solve": (_I, [_V, _V, _V, _D, _P(Stats)]),
+            "mg_solve_host": (_I, [_V, _V, _V, _D, _P(Stats)]),
+            "mg_step_host": (_I, [_V, _V, _I, _V, _V, _D, _P(Stats)]),
+            "mg_destroy": (_I, [_V]),
+            "mg_batch_create": (_I, [_P(_V), _I, _P(_V)]),
+            "mg_batch_solve": (_I, [_V, _P(_V), _P(_V), _P(_D), _P(Stats)]),
+            "mg_batch_destroy": (_I, [_V]),
+            "mg_server_create": (_I, [ctypes.c_size_t, _I, _P(Params), _V, _P(_V)]),
+            "mg_submit": (_I, [_V, _P(Grid), _V, _V, _V, _V, _V, _D, _P(ctypes.c_int64)]),
+            "mg_poll": (_I, [_V, ctypes.c_int64, _P(Stats)]),
+            "mg_server_drain": (_I, [_V]),
+            "mg_server_info": (_I, [_V, _P(ctypes.c_int64), _P(ctypes.c_size_t), _P(ctypes.c_size_t), _P(_I)]),
+            "mg_server_destroy": (_I, [_V]),
+            "mg_num_levels": (_I, [_V, _P(_I)]),
+            "mg_level_shape": (_I, [_V, _I, _P(_I), _P(_I), _P(_I)]),
+            "mg_level_faces": (_I, [_V, _I, _V, _V, _V]),
+            "mg_apply": (_I, [_V, _I, _I, _V, _V]),
+            "mg_smooth": (_I, [_V, _I, _I, _V, _V, _I]),
+            "mg_restrict_residual": (_I, [_V, _I, _I, _V, _V, _V]),
+            "mg_prolong": (_I, [_V, _I, _I, _V, _V]),
+            "mg_coarse_solve": (_I, [_V, _I, _V, _V]),
+            "mg_profile_enable": (_I, [_V, _I]),
+            "mg_profile_read": (_I, [_V, _I, _I, _P(ctypes.c_int64), _P(_D)]),
+            "mg_memory_bytes": (_I, [_V, _P(ctypes.c_size_t)]),
+            "mg_memory_estimate": (_I, [_P(Grid), _P(Params), _P(ctypes.c_size_t)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().mg_strerror(code).decode()
+
+
+def last_cuda_error() -> int:
+    return lib().mg_last_cuda_error()
+
+
+def check(rc: int, what: str = "gbmg") -> int:
+    if rc != OK:
+        raise MGError(rc, what)
+    return rc
+
+
+def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
+    g = Grid()
+    g.nx, g.ny, g.nz = (int(v) for v in shape)
+    g.lx, g.ly, g.lz = (float(v) for v in length)
+    for d in range(3):
+        g.bc[d] = int(bc[d])
+    return g
+
+
+def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True) -> Params:
+    p = Params()
+    lib().mg_params_default(ctypes.byref(p))
+    p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
+    p.max_iters = int(max_iters)
+    p.precision = int(precision)
+    p.use_graph = 1 if use_graph else 0
+    return p
+
+
+def _ptr(t, cells=None, dtype=None):
+    """Data pointer of a contiguous CUDA tensor (checked)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("expected %s, got %s" % (dtype, t.dtype))
+    if cells is not None and t.numel() != cells:
+        raise ValueError("expected %d elements, got %d" % (cells, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray, cells: int):
+    if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != cells:
+        raise ValueError("host arrays must be contiguous float64 with %d elements" % cells)
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def faces_from_density(shape, bc, rho, ax, ay, az, mode=HARMONIC, length=(1.0, 1.0, 1.0), stream=None):
+    """Face coefficients of Eqs. 11-12 from cell density (device tensors)."""
+    import torch
+
+    g = make_grid(shape, bc, length)
+    n = int(np.prod(shape))
+    d = torch.float64
+    check(lib().mg_faces_from_density(ctypes.byref(g), _ptr(rho, n, d), int(mode), _ptr(ax, n, d),
+                                      _ptr(ay, n, d), _ptr(az, n, d), _stream(stream)),
+          "mg_faces_from_density")
+
+
+class Solver:
+    """One grid's hierarchy (mg_create ... mg_destroy)."""
+
+    def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
+                 precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None):
+        import torch
+
+        self.shape = tuple(int(v) for v in shape)
+        self.bc = tuple(int(v) for v in bc)
+        self.length = tuple(float(v) for v in length)
+        self.cells = int(np.prod(self.shape))
+        self.precision = precision
+        self.grid = make_grid(self.shape, self.bc, self.length)
+        self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph)
+        self._h = ctypes.c_void_p()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        if faces is None:
+            if rho is None:
+                raise ValueError("give face coefficients or a density")
+            nz, ny, nx = self.shape[2], self.shape[1], self.shape[0]
+            faces = [torch.empty((nz, ny, nx), dtype=torch.float64, device=rho.device) for _ in range(3)]
+            faces_from_density(self.shape, self.bc, rho, *faces, mode=face_mode, length=self.length,
+                               stream=self.stream)
+        ax, ay, az = (_ptr(f, self.cells, torch.float64) for f in faces)
+        check(lib().mg_create(ctypes.byref(self.grid), ax, ay, az, ctypes.byref(self.params),
+                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h)), "mg_create")
+
+    # -- life cycle --------------------------------------------------------
+    def close(self):
+        if self._h:
+            lib().mg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- coefficients ------------------------------------------------------
+    def set_faces(self, ax, ay, az):
+        import torch
+
+        d = torch.float64
+        check(lib().mg_set_faces(self._h, _ptr(ax, self.cells, d), _ptr(ay, self.cells, d),
+                                 _ptr(az, self.cells, d)), "mg_set_faces")
+
+    def set_density(self, rho, mode=HARMONIC):
+        import torch
+
+        check(lib().mg_set_density(self._h, _ptr(rho, self.cells, torch.float64), int(mode)), "mg_set_density")
+
+    # -- solves -----------------------------------------------------------
+    def solve(self, rhs, p, tol=1e-10, raise_on_error=True) -> Stats:
+        """Solve in place into p (warm start).  Returns the statistics."""
+        import torch
+
+        st = Stats()
+        rc = lib().mg_solve(self._h, _ptr(rhs, self.cells, torch.float64), _ptr(p, self.cells, torch.float64),
+                            float(tol), ctypes.byref(st))
+        if raise_on_error and rc not in (OK, ENOTCONV, EDIVERGED):
+            check(rc, "mg_solve")
+        st.status = rc if rc not in (OK, ENOTCONV, EDIVERGED) else st.status
+        return st
+
+    def solve_host(self, rhs: np.ndarray, p: np.ndarray, tol=1e-10) -> Stats:
+        st = Stats()
+        rc = lib().mg_solve_host(self._h, _hptr(rhs, self.cells), _hptr(p, self.cells), float(tol),
+                                 ctypes.byref(st))
+        if rc not in (OK, ENOTCONV, EDIVERGED):
+            check(rc, "mg_solve_host")
+        return st
+
+    def step_host(self, rho: np.ndarray, rhs: np.ndarray, p: np.ndarray, tol=1e-10, mode=HARMONIC) -> Stats:
+        st = Stats()
+        rc = lib().mg_step_host(self._h, _hptr(rho, self.cells), int(mode), _hptr(rhs, self.cells),
+                                _hptr(p, self.cells), float(tol), ctypes.byref(st))
+        if rc not in (OK, ENOTCONV, EDIVERGED):
+            check(rc, "mg_step_host")
+        return st
+
+    # -- single steps (unit checks) ----------------------------------------
+    def num_levels(self) -> int:
+        v = ctypes.c_int()
+        check(lib().mg_num_levels(self._h, ctypes.byref(v)))
+        return v.value
+
+    def level_shape(self, level):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().mg_level_shape(self._h, int(level), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return (a.value, b.value, c.value)
+
+    def level_faces(self, level):
+        import torch
+
+        nx, ny, nz = self.level_shape(level)
+        out = [torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+        check(lib().mg_level_faces(self._h, int(level), *[_ptr(o) for o in out]), "mg_level_faces")
+        return out
+
+    def apply(self, level, x, y, prec=FP64):
+        check(lib().mg_apply(self._h, int(level), int(prec), _ptr(x), _ptr(y)), "mg_apply")
+
+    def smooth(self, level, b, x, half_sweeps, prec=FP64):
+        check(lib().mg_smooth(self._h, int(level), int(prec), _ptr(b), _ptr(x), int(half_sweeps)), "mg_smooth")
+
+    def restrict_residual(self, level, b, x, coarse_b, prec=FP64):
+        check(lib().mg_restrict_residual(self._h, int(level), int(prec), _ptr(b), _ptr(x), _ptr(coarse_b)),
+              "mg_restrict_residual")
+
+    def prolong(self, level, coarse_e, x, prec=FP64):
+        check(lib().mg_prolong(self._h, int(level), int(prec), _ptr(coarse_e), _ptr(x)), "mg_prolong")
+
+    def coarse_solve(self, r, e, prec=FP64):
+        check(lib().mg_coarse_solve(self._h, int(prec), _ptr(r), _ptr(e)), "mg_coarse_solve")
+
+    # -- profiling / memory --------------------------------------------------
+    def profile(self, enable=True):
+        check(lib().mg_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self, kind, level):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        check(lib().mg_profile_read(self._h, int(kind), int(level), ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def memory_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        check(lib().mg_memory_bytes(self._h, ctypes.byref(v)))
+        return v.value
+
+
+def memory_estimate(shape, bc, precision=MIXED, length=(1.0, 1.0, 1.0)) -> int:
+    g = make_grid(shape, bc, length)
+    p = make_params(precision)
+    v = ctypes.c_size_t()
+    check(lib().mg_memory_estimate(ctypes.byref(g), ctypes.byref(p), ctypes.byref(v)), "mg_memory_estimate")
+    return v.value
+
+
+class Batch:
+    """Several solvers advanced together (mg_batch_*)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.handle.value for s in self.solvers])
+        self._b = ctypes.c_void_p()
+        check(lib().mg_batch_create(arr, len(self.solvers), ctypes.byref(self._b)), "mg_batch_create")
+
+    def solve(self, rhs_list, p_list, tol=1e-10):
+        import torch
+
+        G = len(self.solvers)
+        tols = list(tol) if hasattr(tol, "__len__") else [tol] * G
+        r = (ctypes.c_void_p * G)(*[_ptr(t, s.cells, torch.float64).value for t, s in zip(rhs_list, self.solvers)])
+        p = (ctypes.c_void_p * G)(*[_ptr(t, s.cells, torch.float64).value for t, s in zip(p_list, self.solvers)])
+        tl = (ctypes.c_double * G)(*[float(v) for v in tols])
+        st = (Stats * G)()
+        rc = lib().mg_batch_solve(self._b, r, p, tl, st)
+        if rc not in (OK, ENOTCONV, EDIVERGED):
+            check(rc, "mg_batch_solve")
+        return list(st)
+
+    def close(self):
+        if self._b:
+            lib().mg_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (mg_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=16, precision=MIXED, max_iters=100, stream=None):
+        self.params = make_params(precision, max_iters=max_iters)
+        self._s = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
+        check(lib().mg_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(self.params), st,
+                                     ctypes.byref(self._s)), "mg_server_create")
+        self._keep = {}
+
+    def submit(self, shape, bc, faces, rhs, p, tol=1e-10, length=(1.0, 1.0, 1.0)) -> int:
+        g = make_grid(shape, bc, length)
+        t = ctypes.c_int64()
+        check(lib().mg_submit(self._s, ctypes.byref(g), *[_ptr(f) for f in faces], _ptr(rhs), _ptr(p),
+                              float(tol), ctypes.byref(t)), "mg_submit")
+        self._keep[t.value] = (faces, rhs, p)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (status, Stats)."""
+        st = Stats()
+        rc = lib().mg_poll(self._s, int(ticket), ctypes.byref(st))
+        if rc == EAGAIN:
+            return None
+        if rc == ENOTFOUND:
+            raise MGError(rc, "mg_poll")
+        self._keep.pop(int(ticket), None)
+        return rc, st
+
+    def drain(self):
+        return lib().mg_server_drain(self._s)
+
+    def info(self):
+        c, b, pk, m = ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+        check(lib().mg_server_info(self._s, ctypes.byref(c), ctypes.byref(b), ctypes.byref(pk), ctypes.byref(m)))
+        return {"completed": c.value, "bytes_in_use": b.value, "peak_bytes": pk.value, "max_in_flight": m.value}
+
+    def close(self):
+        if self._s:
+            rc = lib().mg_server_destroy(self._s)
+            if rc == OK:
+                self._s = ctypes.c_void_p()
+            return rc
+        return OK
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

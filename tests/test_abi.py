@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads and exports every entry point of include/gbmg.h.
+
+No compute call is made here (no GPU in the build container)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1410_8568_gb300 import build as B
+from paper_1410_8568_gb300 import gbmg
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gbmg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(mg_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    assert os.path.exists(path)
+    L = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 30, names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    gbmg.lib()
+    import inspect
+    src = inspect.getsource(gbmg)
+    missing = [n for n in declared_functions() if '"%s"' % n not in src]
+    assert not missing, missing
+
+
+def test_host_only_calls():
+    """Calls that need no device: messages, defaults, size rules, estimates."""
+    L = gbmg.lib()
+    assert gbmg.strerror(gbmg.ENOTCONV).startswith("not converged")
+    p = gbmg.Params()
+    assert L.mg_params_default(ctypes.byref(p)) == 0
+    assert (p.nu1, p.nu2, p.omega, p.precision, p.use_graph) == (2, 2, 1.0, gbmg.MIXED, 1)
+    est = gbmg.memory_estimate((64, 64, 64), (1, 1, 0))
+    assert 64 ** 3 * 52 < est < 64 ** 3 * 70
+    # coarsest grid too large: 4 x 4 x 64 cannot be coarsened to <= 512 cells
+    with pytest.raises(gbmg.MGError) as e:
+        gbmg.memory_estimate((4, 4, 64), (0, 0, 0))
+    assert e.value.code == gbmg.EINVAL
+    with pytest.raises(gbmg.MGError):
+        gbmg.memory_estimate((1, 8, 8), (0, 0, 0))
+
+
+def test_no_gpu_fails_loudly():
+    """Without a usable GPU the product path raises instead of computing on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(Exception):
+        gbmg.Solver((8, 8, 8), (0, 0, 0), faces=[torch.ones(512, dtype=torch.float64)] * 3)
