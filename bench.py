@@ -159,12 +159,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def count_launches(levels, iters, nu1=2, nu2=2):
-    """Kernels of one step: coefficient set-up + prologue + iters * body + final."""
-    setup = 1 + (levels - 1) + 1  # faces from density, coarsening per level, coarsest inverse
-    prologue = 6                  # begin, sum b, mean, residual, finalize, loop control
-    body = (levels - 1) * (2 * nu1 + 1 + 1 + 2 * nu2) + 1 + 1 + 1 + 1  # smooth/restrict/prolong, coarse, residual, finalize, control
-    return setup + prologue + iters * body + 1
+def count_launches(levels, iters, nu1=2, nu2=2, inner=2):
+    """Kernels of one step: coefficient set-up, prologue, refinement steps, epilogue."""
+    setup = 1 + (levels - 1) + 1       # faces from density, coarsening per level, coarsest inverse
+    prologue = 6                       # begin, sum b, mean, residual, finalize, loop control
+    cycle = (levels - 1) * (2 * nu1 + 1 + 1 + 2 * nu2) + 1  # half-sweeps, restriction, prolongation; coarsest
+    step = inner * cycle + 3           # + residual, finalize, loop control
+    epilogue = 3                       # sum p, mean, p - mean
+    return setup + prologue + (iters // inner) * step + epilogue
 
 
 def cpu_oracle_solve(P, faces, tol=TOL):
@@ -324,7 +326,9 @@ def main():
     n_r, ms_r = S.profile_read(gbmg.K_RESIDUAL, 0)
     S.profile(False)
     avg_s = ms_l / n_l / 1000.0
-    bytes_launch = 5 * 4 * N  # FP32 half-sweep: read x, b (own colour), 3 faces; write own colour
+    # FP32 half-sweep, algorithmic: read x (all cells), b of the colour (half),
+    # the 3 face arrays (every face borders one cell of each colour), write the colour (half)
+    bytes_launch = (4 + 2 + 12 + 2) * N
     peak, peak_kind = read_peaks()
     achieved = bytes_launch / avg_s / 1e9
     traffic = profiled_traffic(args.workload)
@@ -371,7 +375,7 @@ def main():
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_smooth<float> level 0 (one red or black half-sweep)",
+                         "kernel": "k_half<float> level 0 (one red or black half-sweep)",
                          "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
                          "launches_timed": n_l, "peak_source": peak_kind,
                          "residual_fp64_avg_launch_us": 1000.0 * ms_r / max(1, n_r)},

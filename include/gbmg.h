@@ -92,11 +92,12 @@ typedef struct {
 } mg_grid;
 
 typedef struct {
-    int nu1, nu2;      /* pre- and post-relaxation sweeps (one sweep = red then black) */
+    int nu1, nu2;      /* pre- and post-relaxation sweeps (one sweep = red then black), nu1 >= 1 */
     double omega;      /* SOR factor of the red-black relaxation, 0 < omega < 2 */
     int max_iters;     /* most V-cycles per solve */
     int precision;     /* MG_PREC_FP64 or MG_PREC_MIXED */
     int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
+    int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1 */
 } mg_params;
 
 typedef struct {
@@ -124,7 +125,7 @@ const char *mg_strerror(int status);
 int mg_last_cuda_error(void);
 
 /* Default parameters: V(2,2), omega = 1 (Gauss-Seidel), 100 cycles, mixed
- * precision, CUDA graph on. */
+ * precision, CUDA graph on, 2 V-cycles per refinement step. */
 int mg_params_default(mg_params *params);
 
 /* Face coefficients alpha = 1/rho of Eqs. 11-12 (mode MG_FACE_HARMONIC) or the
@@ -156,7 +157,8 @@ int mg_set_faces(mg_handle *h, const double *ax, const double *ay, const double 
 int mg_set_density(mg_handle *h, const double *rho, int mode);
 
 /* Solve A p = rhs to ||rhs - A p|| <= tol ||rhs|| (after removing the mean of
- * rhs).  rhs and p are DEVICE arrays of nx*ny*nz doubles; p is the starting
+ * rhs).  rhs and p are DEVICE arrays of nx*ny*nz doubles (p 16-byte aligned,
+ * as every cudaMalloc/torch allocation is); p is the starting
  * iterate on entry (warm start; zeros for a cold start) and the zero-mean
  * solution on exit.  rhs is not modified.  Synchronous: returns when the solve
  * has finished on the handle's stream.  `st` may be NULL.  Returns MG_OK,
@@ -248,9 +250,9 @@ int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double
 /* y = A_level x (Eq. 10 / h^2 on that level). */
 int mg_apply(mg_handle *h, int level, int prec, const void *x, void *y);
 
-/* `half_sweeps` red-black half-sweeps on x (red = (i+j+k) even first, then
- * alternating), relaxation factor of the handle (Sec. 2.3 item 5). */
-int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int half_sweeps);
+/* `sweeps` red-black sweeps on x (each: red = (i+j+k) even cells, then black),
+ * relaxation factor of the handle (Sec. 2.3 item 5). */
+int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int sweeps);
 
 /* coarse_b = mean over the 8 children of (b - A x) on `level` (item 3). */
 int mg_restrict_residual(mg_handle *h, int level, int prec, const void *b, const void *x,

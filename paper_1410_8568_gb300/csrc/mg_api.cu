@@ -84,6 +84,7 @@ int check_params(const mg_params *p)
     if (!(p->omega > 0.0 && p->omega < 2.0)) return MG_EINVAL;
     if (p->max_iters < 1 || p->max_iters > 100000) return MG_EINVAL;
     if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) return MG_EINVAL;
+    if (p->inner_cycles < 1 || p->inner_cycles > 16) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -92,7 +93,7 @@ struct Layout {
     int L;
     int n[MG_MAX_LEVELS][3];
     size_t w64[MG_MAX_LEVELS][3], w32[MG_MAX_LEVELS][3], x[MG_MAX_LEVELS], b[MG_MAX_LEVELS];
-    size_t G, xbuf, part, err, state, dstate, dview, dstart, dcview, total;
+    size_t G, b0, part, err, state, dstate, dview, dstart, dcview, total;
     int nblk0;
 };
 
@@ -114,9 +115,9 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
     const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
     lay.G = c.take(ncells * ncells * 8);
     const size_t N0 = (size_t)g.nx * g.ny * g.nz;
-    lay.xbuf = c.take(N0 * 8);
+    lay.b0 = c.take(N0 * 8);
     const int n0[3] = {g.nx, g.ny, g.nz};
-    lay.nblk0 = fine_blocks(n0);
+    lay.nblk0 = outer_blocks(n0);
     lay.part = c.take((size_t)lay.nblk0 * kPart * 8);
     lay.err = c.take(16 * sizeof(int));
     lay.state = c.take(sizeof(GridState));
@@ -171,11 +172,11 @@ int Plan::build(mg_handle *const *handles, int count)
     // host copies of the tables
     std::vector<LevelView> lv;
     std::vector<int> starts;
-    struct Range { int lv0, count, sf, sc, bf, bc; };
+    struct Range { int lv0, count, sf, sc, sh, bf, bc, bh; };
     std::vector<Range> ranges(Lmax);
     for (int l = 0; l + 1 < Lmax; l++) {
-        Range r{(int)lv.size(), 0, 0, 0, 0, 0};
-        std::vector<int> sf{0}, sc{0};
+        Range r{(int)lv.size(), 0, 0, 0, 0, 0, 0, 0};
+        std::vector<int> sf{0}, sc{0}, sh{0};
         for (int g = 0; g < G; g++) {
             mg_handle *h = hs[g];
             if (l + 1 >= h->L) continue;
@@ -192,18 +193,23 @@ int Plan::build(mg_handle *const *handles, int count)
             v.b = F.b;
             v.xc = C.x;
             v.bc = C.b;
+            v.g = g;
             v.st = h->state;
             lv.push_back(v);
-            sf.push_back(sf.back() + fine_blocks(F.n));
-            sc.push_back(sc.back() + coarse_blocks(C.n));
+            sf.push_back(sf.back() + prolong_blocks(F.n));
+            sc.push_back(sc.back() + restrict_blocks(F.n, C.n));
+            sh.push_back(sh.back() + half_sweep_blocks(F.n));
             r.count++;
         }
         r.sf = (int)starts.size();
         starts.insert(starts.end(), sf.begin(), sf.end());
         r.sc = (int)starts.size();
         starts.insert(starts.end(), sc.begin(), sc.end());
+        r.sh = (int)starts.size();
+        starts.insert(starts.end(), sh.begin(), sh.end());
         r.bf = sf.back();
         r.bc = sc.back();
+        r.bh = sh.back();
         ranges[l] = r;
     }
     std::vector<int> so{0};
@@ -226,11 +232,13 @@ int Plan::build(mg_handle *const *handles, int count)
     for (int l = 0; l < MG_MAX_LEVELS; l++) {
         down[l] = Table{d_lv, d_starts, 0, 0};
         rest[l] = down[l];
+        half[l] = down[l];
     }
     for (int l = 0; l + 1 < Lmax; l++) {
         const Range &r = ranges[l];
         down[l] = Table{d_lv + r.lv0, d_starts + r.sf, r.count, r.bf};
         rest[l] = Table{d_lv + r.lv0, d_starts + r.sc, r.count, r.bc};
+        half[l] = Table{d_lv + r.lv0, d_starts + r.sh, r.count, r.bh};
     }
     ot = OuterTable{ov, d_starts + so_off, G, so.back()};
     std::vector<CoarseView> cvh(G);
@@ -250,6 +258,8 @@ int Plan::build(mg_handle *const *handles, int count)
         v.b = Cl.b;
         v.st = h->state;
         v.err = h->err + 1;
+        v.g = g;
+        v.outer = h->L == 1 ? 1 : 0;
     }
     CK(cudaMallocHost((void **)&ov_h, G * sizeof(OuterView)));
     CK(cudaMallocHost((void **)&st_h, G * sizeof(GridState)));
@@ -262,14 +272,14 @@ int Plan::build(mg_handle *const *handles, int count)
             v.w[d] = h->lev[0].w64[d];
         }
         v.per = h->per;
-        v.xbuf = h->xbuf;
-        v.e = h->lev[0].x;
+        v.b0 = h->b0;
         v.r = h->lev[0].b;
         v.part = h->part;
         v.nblk = h->nblk0;
         v.st = h->state;
         v.tol = 1e-10;
         v.max_iters = h->prm.max_iters;
+        v.inner = prm.inner_cycles;
     }
     if (!lv.empty()) CK(cudaMemcpy(d_lv, lv.data(), lv.size() * sizeof(LevelView), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_starts, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -331,20 +341,27 @@ Prof::~Prof()
 
 // ---- the V-cycle and the outer iteration -----------------------------------
 
+// One V(nu1, nu2) cycle over every grid of the plan, red-black half-sweeps in
+// place.  Coarse levels start every cycle from a zero correction (the first
+// red half-sweep takes x = 0).  The finest level starts from zero in the first
+// cycle of a refinement step and from the previous cycle's correction in the
+// next ones.  The last red and black half-sweeps on the finest level in the
+// last cycle of the step add the correction to the FP64 iterate.
 template <class T>
-static void vcycle(Plan &P, Prof &pf)
+static void vcycle(Plan &P, Prof &pf, int cycle_in_step, bool last_of_step)
 {
     const cudaStream_t s = P.stream;
     const mg_params &q = P.prm;
     for (int l = 0; l + 1 < P.Lmax; l++) {
-        const Table &D = P.down[l];
-        if (D.count == 0) continue;
+        const Table &H = P.half[l];
+        if (H.count == 0) continue;
+        const bool zero = !(l == 0 && cycle_in_step > 0);
         for (int it = 0; it < q.nu1; it++) {
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_smooth<T>(D, 0, q.omega, it == 0, s);
+            launch_half<T>(H, 0, q.omega, (it == 0 && zero) ? kHalfZero : 0, P.ov, s);
             pf.end(s);
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_smooth<T>(D, 1, q.omega, 0, s);
+            launch_half<T>(H, 1, q.omega, 0, P.ov, s);
             pf.end(s);
         }
         pf.begin(s, MG_K_RESTRICT, l);
@@ -352,20 +369,22 @@ static void vcycle(Plan &P, Prof &pf)
         pf.end(s);
     }
     pf.begin(s, MG_K_COARSE, P.Lmax - 1);
-    launch_coarse_solve<T>(P.cv, P.G, s);
+    launch_coarse_solve<T>(P.cv, P.G, last_of_step ? P.ov : nullptr, s);
     pf.end(s);
     for (int l = P.Lmax - 2; l >= 0; l--) {
-        const Table &D = P.down[l];
-        if (D.count == 0) continue;
+        const Table &H = P.half[l];
+        if (H.count == 0) continue;
+        const bool outer = l == 0 && last_of_step;
         pf.begin(s, MG_K_PROLONG, l);
-        launch_prolong<T>(D, s);
+        launch_prolong<T>(P.down[l], P.ov, (outer && q.nu2 == 0) ? 1 : 0, s);
         pf.end(s);
         for (int it = 0; it < q.nu2; it++) {
+            const int fl = (outer && it == q.nu2 - 1) ? kHalfOuter : 0;
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_smooth<T>(D, 0, q.omega, 0, s);
+            launch_half<T>(H, 0, q.omega, fl, P.ov, s);
             pf.end(s);
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_smooth<T>(D, 1, q.omega, 0, s);
+            launch_half<T>(H, 1, q.omega, fl, P.ov, s);
             pf.end(s);
         }
     }
@@ -377,27 +396,40 @@ static void prologue(Plan &P, Prof &pf)
     const cudaStream_t s = P.stream;
     pf.begin(s, MG_K_OTHER, 0);
     launch_begin(P.ov, P.G, s);
-    launch_bsum(P.ot, s);
+    launch_sum(P.ot, 0, s);
     launch_finalize(P.ot, 0, s);
     pf.end(s);
     pf.begin(s, MG_K_RESIDUAL, 0);
-    launch_residual<T>(P.ot, 0, s);
+    launch_residual<T>(P.ot, 1, s);
     pf.end(s);
     pf.begin(s, MG_K_OTHER, 0);
     launch_finalize(P.ot, 1, s);
     pf.end(s);
 }
 
+// One refinement step: inner_cycles V-cycles on A e = r (the first from e = 0,
+// the next ones continuing from the current e), the last one adding e to the
+// FP64 iterate, then the FP64 residual and the stopping test.
 template <class T>
 static void body(Plan &P, Prof &pf)
 {
     const cudaStream_t s = P.stream;
-    vcycle<T>(P, pf);
+    for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c, c == P.prm.inner_cycles - 1);
     pf.begin(s, MG_K_RESIDUAL, 0);
-    launch_residual<T>(P.ot, 1, s);
+    launch_residual<T>(P.ot, 0, s);
     pf.end(s);
     pf.begin(s, MG_K_OTHER, 0);
     launch_finalize(P.ot, 2, s);
+    pf.end(s);
+}
+
+static void epilogue(Plan &P, Prof &pf)
+{
+    const cudaStream_t s = P.stream;
+    pf.begin(s, MG_K_OTHER, 0);
+    launch_sum(P.ot, 1, s);
+    launch_finalize(P.ot, 3, s);
+    launch_final(P.ot, s);
     pf.end(s);
 }
 
@@ -434,7 +466,7 @@ static int build_graph(Plan &P)
     CK(cudaStreamEndCapture(cs, &body_g));
     // epilogue
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    launch_final(Q.ot, cs);
+    epilogue(Q, off);
     CK(cudaStreamEndCapture(cs, &epi_g));
     cudaGraphNode_t n_pro, n_loop, n_epi, n_inner;
     CK(cudaGraphAddChildGraphNode(&n_pro, main_g, nullptr, 0, pro_g));
@@ -482,9 +514,7 @@ static int run_plan_t(Plan &P, Prof &pf, bool use_graph)
             if (!any) break;
             body<T>(P, pf);
         }
-        pf.begin(s, MG_K_OTHER, 0);
-        launch_final(P.ot, s);
-        pf.end(s);
+        epilogue(P, pf);
         CK(cudaEventRecord(P.e1, s));
     }
     CK(cudaGetLastError());
@@ -529,7 +559,7 @@ int plan_body(Plan &P)
 
 int plan_final(Plan &P)
 {
-    launch_final(P.ot, P.stream);
+    epilogue(P, g_no_prof);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -566,6 +596,7 @@ int run_plan(Plan &P, Prof &pf, const double *const *rhs, double *const *p, cons
 {
     for (int g = 0; g < P.G; g++) {
         if (!rhs[g] || !p[g] || !(tol[g] >= 0.0)) return MG_EINVAL;
+        if (((uintptr_t)p[g] & 15) != 0) return MG_EINVAL;  // p is staged in 16-byte pieces
         P.ov_h[g].b = rhs[g];
         P.ov_h[g].p = p[g];
         P.ov_h[g].tol = tol[g];
@@ -698,7 +729,7 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
         L.b = h->slab + lay.b[l];
     }
     h->G = (double *)(h->slab + lay.G);
-    h->xbuf = (double *)(h->slab + lay.xbuf);
+    h->b0 = (double *)(h->slab + lay.b0);
     h->part = (double *)(h->slab + lay.part);
     h->nblk0 = lay.nblk0;
     h->err = (int *)(h->slab + lay.err);
@@ -759,6 +790,7 @@ int mg_params_default(mg_params *p)
     p->max_iters = 100;
     p->precision = MG_PREC_MIXED;
     p->use_graph = 1;
+    p->inner_cycles = 2;
     return MG_OK;
 }
 
@@ -972,8 +1004,10 @@ int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double
     return MG_OK;
 }
 
-static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b, const void *xc,
-                     void *bc, Table *tb, bool coarse_tiles)
+enum UnitTiles { kFineTiles, kCoarseTiles, kHalfTiles, kProlongTiles };
+
+static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b,
+                     const void *xc, void *bc, Table *tb, UnitTiles tiles)
 {
     if (!h || level < 0 || level >= h->L) return MG_EINVAL;
     if (prec != MG_PREC_FP64 && prec != MG_PREC_MIXED) return MG_EINVAL;
@@ -992,7 +1026,9 @@ static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b, 
     v.xc = (void *)xc;
     v.bc = bc;
     v.st = h->dstate;
-    const int blocks = coarse_tiles ? coarse_blocks(v.nc) : fine_blocks(v.n);
+    const int blocks = tiles == kCoarseTiles ? restrict_blocks(v.n, v.nc)
+                       : tiles == kHalfTiles ? half_sweep_blocks(v.n)
+                       : tiles == kProlongTiles ? prolong_blocks(v.n) : fine_blocks(v.n);
     const int starts[2] = {0, blocks};
     CK(cudaMemcpyAsync(h->dview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, h->stream));
@@ -1004,7 +1040,7 @@ int mg_apply(mg_handle *h, int level, int prec, const void *x, void *y)
 {
     if (!x || !y) return MG_EINVAL;
     Table tb;
-    int rc = unit_view(h, level, prec, x, y, nullptr, nullptr, &tb, false);
+    int rc = unit_view(h, level, prec, x, y, nullptr, nullptr, &tb, kFineTiles);
     if (rc) return rc;
     if (prec == MG_PREC_MIXED) launch_apply<float>(tb, h->stream);
     else launch_apply<double>(tb, h->stream);
@@ -1013,18 +1049,17 @@ int mg_apply(mg_handle *h, int level, int prec, const void *x, void *y)
     return MG_OK;
 }
 
-int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int half_sweeps)
+int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int sweeps)
 {
-    if (!x || !b || half_sweeps < 0) return MG_EINVAL;
-    if (h && level == h->L - 1 && h->L > 1) {
-        // the coarsest level is never relaxed; odd periodic sizes are allowed there
-    }
+    if (!h || !x || !b || sweeps < 0) return MG_EINVAL;
     Table tb;
-    int rc = unit_view(h, level, prec, x, (void *)b, nullptr, nullptr, &tb, false);
+    int rc = unit_view(h, level, prec, x, (void *)b, nullptr, nullptr, &tb, kHalfTiles);
     if (rc) return rc;
-    for (int s = 0; s < half_sweeps; s++) {
-        if (prec == MG_PREC_MIXED) launch_smooth<float>(tb, s & 1, h->prm.omega, 0, h->stream);
-        else launch_smooth<double>(tb, s & 1, h->prm.omega, 0, h->stream);
+    for (int s = 0; s < sweeps; s++) {
+        for (int colour = 0; colour < 2; colour++) {
+            if (prec == MG_PREC_MIXED) launch_half<float>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
+            else launch_half<double>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
+        }
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
@@ -1036,7 +1071,7 @@ int mg_restrict_residual(mg_handle *h, int level, int prec, const void *b, const
 {
     if (!x || !b || !coarse_b || !h || level + 1 >= h->L) return MG_EINVAL;
     Table tb;
-    int rc = unit_view(h, level, prec, x, (void *)b, nullptr, coarse_b, &tb, true);
+    int rc = unit_view(h, level, prec, x, (void *)b, nullptr, coarse_b, &tb, kCoarseTiles);
     if (rc) return rc;
     if (prec == MG_PREC_MIXED) launch_restrict<float>(tb, h->stream);
     else launch_restrict<double>(tb, h->stream);
@@ -1049,10 +1084,10 @@ int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x)
 {
     if (!x || !coarse_e || !h || level + 1 >= h->L) return MG_EINVAL;
     Table tb;
-    int rc = unit_view(h, level, prec, x, nullptr, coarse_e, nullptr, &tb, false);
+    int rc = unit_view(h, level, prec, x, nullptr, coarse_e, nullptr, &tb, kProlongTiles);
     if (rc) return rc;
-    if (prec == MG_PREC_MIXED) launch_prolong<float>(tb, h->stream);
-    else launch_prolong<double>(tb, h->stream);
+    if (prec == MG_PREC_MIXED) launch_prolong<float>(tb, nullptr, 0, h->stream);
+    else launch_prolong<double>(tb, nullptr, 0, h->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return MG_OK;
@@ -1078,8 +1113,8 @@ int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e)
     v.st = h->dstate;
     v.err = h->err + 1;
     CK(cudaMemcpyAsync(h->dcview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
-    if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, h->stream);
-    else launch_coarse_solve<double>(h->dcview, 1, h->stream);
+    if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, nullptr, h->stream);
+    else launch_coarse_solve<double>(h->dcview, 1, nullptr, h->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return MG_OK;

@@ -68,7 +68,7 @@ struct mg_handle {
     int L = 0;
     gbmg::HLevel lev[MG_MAX_LEVELS];
     double *G = nullptr;       // coarsest-grid inverse
-    double *xbuf = nullptr;    // FP64 ping-pong iterate
+    double *b0 = nullptr;      // right-hand side minus its mean (FP64)
     double *part = nullptr;    // reduction partials of the outer launches
     int nblk0 = 0;
     int *err = nullptr;        // [0] bad coefficient, [1] singular coarsest grid
@@ -96,8 +96,9 @@ struct Plan {
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
     char *mem = nullptr;
-    Table down[MG_MAX_LEVELS];  // smoothing / prolongation (fine tiles of level l)
+    Table down[MG_MAX_LEVELS];  // prolongation (fine tiles of level l)
     Table rest[MG_MAX_LEVELS];  // restriction (coarse tiles of level l+1)
+    Table half[MG_MAX_LEVELS];  // red-black half-sweeps of level l
     CoarseView *cv = nullptr;
     OuterView *ov = nullptr;
     OuterTable ot;

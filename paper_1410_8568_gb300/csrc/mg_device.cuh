@@ -19,6 +19,8 @@ constexpr int kSeg = 64;          // x extent of a warp's row segment (2 cells p
 constexpr int kCSeg = 32;         // x extent of a warp's coarse row segment (restriction)
 constexpr int kMaxCoarse = 512;   // most cells of the coarsest grid (dense inverse)
 constexpr int kPart = 4;          // doubles of reduction partials per block
+constexpr int kOuterCap = 608;    // most blocks of one grid in an outer (FP64) launch: 4 per SM
+
 
 // Per-grid solve state, in device memory, written only by kernels.
 struct GridState {
@@ -29,7 +31,7 @@ struct GridState {
     double rnorm;   // current ||r||_2
     double xmean;   // mean of the current iterate
     int max_iters;
-    int iters;      // completed cycles; parity tells which buffer holds x
+    int iters;      // completed V-cycles
     int status;     // gbmg status code
     int active;     // 1 while the grid is being iterated
 };
@@ -42,9 +44,10 @@ struct LevelView {
     void *w[3];     // scaled face coefficients alpha / h^2 (low face of each cell)
     void *x;        // iterate / correction
     void *b;        // right-hand side
-    void *xc;       // next coarser level: iterate (null at the coarsest)
+    void *xc;       // next coarser level: its final correction (null at the coarsest)
     void *bc;       // next coarser level: right-hand side
     int nc[3];
+    int g;          // index of the grid in its plan (selects its OuterView)
     const GridState *st;
 };
 
@@ -55,14 +58,14 @@ struct OuterView {
     const double *w[3];  // FP64 scaled faces of level 0
     const double *b;     // caller's right-hand side
     double *p;           // caller's iterate / solution
-    double *xbuf;        // second FP64 iterate buffer (ping-pong with p)
-    void *e;             // level-0 correction of the V-cycle (V-cycle precision)
+    double *b0;          // right-hand side minus its mean, FP64 (library buffer)
     void *r;             // level-0 right-hand side of the V-cycle (V-cycle precision)
     double *part;        // kPart doubles per block of this grid's outer launches
     int nblk;            // blocks of this grid in an outer launch
     GridState *st;
     double tol;
     int max_iters;
+    int inner;           // V-cycles per refinement step
 };
 
 // The coarsest level of one grid.
@@ -76,6 +79,8 @@ struct CoarseView {
     const void *b;       // right-hand side (V-cycle precision)
     const GridState *st;
     int *err;            // set-up error flag (non-positive pivot)
+    int g;               // index of the grid in its plan
+    int outer;           // 1 if this is also the finest level (x += e happens here)
 };
 
 // Blocks of a launch over the cells of an n[0] x n[1] x n[2] level: a block is
@@ -84,6 +89,12 @@ __host__ __device__ inline int fine_xtiles(int nx) { return (nx + kSeg - 1) / kS
 __host__ __device__ inline int fine_blocks(const int n[3])
 {
     return fine_xtiles(n[0]) * ((n[1] * n[2] + kRowsPerBlock - 1) / kRowsPerBlock);
+}
+// Outer (FP64) launches: at most kOuterCap blocks per grid, grid-stride over tiles.
+__host__ __device__ inline int outer_blocks(const int n[3])
+{
+    const int t = fine_blocks(n);
+    return t < kOuterCap ? t : kOuterCap;
 }
 // Blocks of a launch over the cells of a coarse level (32 coarse cells per warp row).
 __host__ __device__ inline int coarse_xtiles(int nx) { return (nx + kCSeg - 1) / kCSeg; }

@@ -120,13 +120,6 @@ struct LoadPlain {
     __device__ __forceinline__ T operator()(long long q) const { return x[q]; }
 };
 
-template <class Te>
-struct LoadSum {  // FP64 iterate plus the V-cycle correction
-    const double *x;
-    const Te *e;
-    __device__ __forceinline__ double operator()(long long q) const { return x[q] + (double)e[q]; }
-};
-
 // Deterministic block sum of up to 4 doubles; result valid in thread 0.
 __device__ __forceinline__ void block_sum4(double v[4], double *out)
 {
@@ -169,52 +162,283 @@ __device__ __forceinline__ Tile fine_tile(const int n[3], int lb)
 }
 
 // ---------------------------------------------------------------------------
-// (5) red-black relaxation: one half-sweep over the cells of one colour
+// (5) red-black relaxation, one colour per launch
 // ---------------------------------------------------------------------------
-
-// zero_guess: x is taken as 0 on entry (first pre-smoothing half-sweep of a
-// level): the relaxed colour gets omega * (-b / diag), the other colour 0, so
-// no separate clearing pass is needed.
+//
+// Cells of one colour only read cells of the other colour, so updating them in
+// place equals the textbook half-sweep whatever the order of the threads.  When
+// the row length is a multiple of 4 a thread owns an aligned quad of 4 cells of
+// a row (one 16-byte vector per operand for FP32, two for FP64), relaxes the 2
+// cells of the launch's colour and writes the other two back unchanged;
+// otherwise (small coarse levels) one cell per thread.  The FP32 cycle uses the
+// 2-ulp division (__fdividef): the inner cycle is a preconditioner and only
+// steers convergence; the FP64 path divides exactly.
+//
+// flags: kZeroGuess  (red launch) the iterate is zero on entry: red cells get
+//                    omega * (-b / d), black cells 0, so no clearing pass;
+//        kOuter      the relaxed cells' final values are also added to the FP64
+//                    iterate (last red and last black half-sweep of a
+//                    refinement step on the finest level).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_smooth(const LevelView *__restrict__ lv,
-                                                     const int *__restrict__ start, int count,
-                                                     int colour, T omega, int zero_guess)
+struct Quad {
+    T v[4];
+};
+
+template <class T>
+__device__ __forceinline__ Quad<T> ldq(const T *__restrict__ p)
+{
+    Quad<T> q;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        q.v[0] = a.x;
+        q.v[1] = a.y;
+        q.v[2] = a.z;
+        q.v[3] = a.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        q.v[0] = a.x;
+        q.v[1] = a.y;
+        q.v[2] = b.x;
+        q.v[3] = b.y;
+    }
+    return q;
+}
+
+template <class T>
+__device__ __forceinline__ void stq(T *p, const Quad<T> &q)
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(q.v[0], q.v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(q.v[2], q.v[3]);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T relax_div(T num, T den)
+{
+    if constexpr (sizeof(T) == 4) return __fdividef(num, den);  // inner cycle: 2-ulp division
+    else return num / den;
+}
+
+// outer_update / zero flags
+constexpr int kZeroGuess = 1, kOuter = 4;
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
+                                                   const int *__restrict__ start, int count,
+                                                   int colour, T omega, int flags,
+                                                   const OuterView *__restrict__ ov)
 {
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
     if (!L.st->active) return;
-    const Tile t = fine_tile(L.n, blockIdx.x - start[e]);
-    if (!t.ok) return;
-    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int i0 = t.xbase + ((threadIdx.x & 31) << 1);
-    if (i0 >= nx) return;
-    const int par = (colour + t.j + t.k) & 1;
-    const int i = i0 + par;
-    T *x = (T *)L.x;
-    const T *b = (const T *)L.b;
-    const T *wx = (const T *)L.w[0], *wy = (const T *)L.w[1], *wz = (const T *)L.w[2];
-    const long long rowoff = (long long)nx * t.row;
-    if (i < nx) {
-        const long long c = rowoff + i;
-        if (zero_guess) {
-            const T d = diag_of(wx, wy, wz, nx, ny, nz, L.per, i, t.j, t.k, c);
-            x[c] = d > T(0) ? omega * (-b[c] / d) : T(0);
-        } else {
-            const T xc = x[c];
-            T d, f;
-            stencil(wx, wy, wz, LoadPlain<T>{x}, nx, ny, nz, L.per, i, t.j, t.k, c, xc, d, f);
-            if (d > T(0)) x[c] = xc + omega * ((f - b[c]) / d);
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2], per = L.per;
+    T *__restrict__ x = (T *)L.x;
+    const T *__restrict__ b = (const T *)L.b;
+    const T *__restrict__ wx = (const T *)L.w[0];
+    const T *__restrict__ wy = (const T *)L.w[1];
+    const T *__restrict__ wz = (const T *)L.w[2];
+    const bool zero = flags & kZeroGuess;
+    double *__restrict__ pout = (flags & kOuter) ? ov[L.g].p : nullptr;
+    const long long sy = nx, sz = (long long)nx * ny;
+    const int lb = blockIdx.x - start[e];
+
+    if ((nx & 3) != 0) {
+        // one cell per thread (row tiles of 64 cells per warp, 2 per lane)
+        const Tile t = fine_tile(L.n, lb);
+        if (!t.ok) return;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+            if (i >= nx || ((i + t.j + t.k) & 1) != colour) {
+                if (zero && i < nx) x[(long long)nx * t.row + i] = T(0);
+                continue;
+            }
+            const long long c = (long long)nx * t.row + i;
+            T v;
+            if (zero) {
+                const T d = diag_of(wx, wy, wz, nx, ny, nz, per, i, t.j, t.k, c);
+                v = d > T(0) ? omega * relax_div(-b[c], d) : T(0);
+            } else {
+                const T xc = x[c];
+                T d, f;
+                stencil(wx, wy, wz, LoadPlain<T>{x}, nx, ny, nz, per, i, t.j, t.k, c, xc, d, f);
+                v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
+            }
+            x[c] = v;
+            if (pout) pout[c] += (double)v;
         }
+        return;
     }
-    if (zero_guess) {
-        const int io = i0 + 1 - par;
-        if (io < nx) x[rowoff + io] = T(0);
+
+    // an aligned quad of 4 cells per thread: a warp covers 32 quads of one row,
+    // a block 8 rows
+    const int nq = nx >> 2;
+    const int xt_n = (nq + 31) >> 5;
+    const int tq = lb % xt_n, rb = lb / xt_n;
+    const int row = rb * kRowsPerBlock + (threadIdx.x >> 5);
+    if (row >= ny * nz) return;
+    const int qx = (tq << 5) + (threadIdx.x & 31);
+    if (qx >= nq) return;
+    const int j = row % ny, k = row / ny;
+    const int i0 = qx << 2;
+    const long long c = (long long)row * nx + i0;
+    const int par = (colour + j + k) & 1;  // first cell of the colour in the quad
+    const Quad<T> Z{{T(0), T(0), T(0), T(0)}};
+    const bool has_w = i0 > 0 || (per & 1), has_e = i0 + 4 < nx || (per & 1);
+    const long long cw = i0 > 0 ? c - 1 : c + nx - 1;
+    const long long ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
+    const bool has_s = j > 0 || (per & 2), has_n = j + 1 < ny || (per & 2);
+    const long long cs = j > 0 ? c - sy : c + sy * (ny - 1);
+    const long long cn = j + 1 < ny ? c + sy : c - sy * (ny - 1);
+    const bool has_b = k > 0 || (per & 4), has_t = k + 1 < nz || (per & 4);
+    const long long cb = k > 0 ? c - sz : c + sz * (nz - 1);
+    const long long ct = k + 1 < nz ? c + sz : c - sz * (nz - 1);
+    const Quad<T> bq = ldq(b + c);
+    const Quad<T> fx = ldq(wx + c);
+    const T fxe = has_e ? wx[ce] : T(0);  // high x face of the last cell
+    const Quad<T> fy = ldq(wy + c);
+    const Quad<T> fyn = has_n ? ldq(wy + cn) : Z;
+    const Quad<T> fz = ldq(wz + c);
+    const Quad<T> fzt = has_t ? ldq(wz + ct) : Z;
+    Quad<T> xq = Z, xs = Z, xn = Z, xb = Z, xt = Z;
+    T xw = T(0), xe = T(0);
+    if (!zero) {
+        xq = ldq(x + c);
+        if (has_s) xs = ldq(x + cs);
+        if (has_n) xn = ldq(x + cn);
+        if (has_b) xb = ldq(x + cb);
+        if (has_t) xt = ldq(x + ct);
+        if (has_w) xw = x[cw];
+        if (has_e) xe = x[ce];
     }
+    Quad<T> out = xq;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        if ((u & 1) != par) continue;  // static indices; par is uniform over a warp (one row)
+        const T xc = xq.v[u];
+        const T xl = u > 0 ? xq.v[u - 1] : xw;
+        const T xr = u < 3 ? xq.v[u + 1] : xe;
+        T a, d, f;
+        a = fx.v[u];
+        d = a;
+        f = a * (xl - xc);
+        a = u < 3 ? fx.v[u + 1] : fxe;
+        d += a;
+        f += a * (xr - xc);
+        a = fy.v[u];
+        d += a;
+        f += a * (xs.v[u] - xc);
+        a = fyn.v[u];
+        d += a;
+        f += a * (xn.v[u] - xc);
+        a = fz.v[u];
+        d += a;
+        f += a * (xb.v[u] - xc);
+        a = fzt.v[u];
+        d += a;
+        f += a * (xt.v[u] - xc);
+        const T v = d > T(0) ? xc + omega * relax_div(f - bq.v[u], d) : xc;
+        out.v[u] = v;
+        if (pout) pout[c + u] += (double)v;
+    }
+    stq(x + c, out);
+}
+
+// Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64
+// cells) per warp, 8 rows per block.
+__host__ __device__ inline int half_blocks(const int n[3])
+{
+    if ((n[0] & 3) != 0) return fine_blocks(n);
+    const int nq = n[0] >> 2;
+    return ((nq + 31) >> 5) * ((n[1] * n[2] + kRowsPerBlock - 1) / kRowsPerBlock);
+}
+int half_sweep_blocks(const int n[3]) { return half_blocks(n); }
+int prolong_blocks(const int n[3]) { return half_blocks(n); }
+
+__device__ __forceinline__ int partner(int i, int nc, int periodic)
+{
+    const int I = i >> 1;
+    int J = (i & 1) ? I + 1 : I - 1;
+    if (J < 0 || J >= nc) J = periodic ? (J + nc) % nc : I;  // wrap, or mirror at a wall
+    return J;
+}
+
+// (4) trilinear prolongation at fine cell (i,j,k): weights 3/4 on the coarse
+// cell containing the fine centre and 1/4 on its partner, per axis.
+template <class T>
+__device__ __forceinline__ T prolong_at(const T *__restrict__ ec, const int nc[3], int per, int i,
+                                        int j, int k)
+{
+    const int I0 = i >> 1, I1 = partner(i, nc[0], per & 1);
+    const int J0 = j >> 1, J1 = partner(j, nc[1], per & 2);
+    const int K0 = k >> 1, K1 = partner(k, nc[2], per & 4);
+    const long long r00 = (long long)nc[0] * (J0 + (long long)nc[1] * K0);
+    const long long r10 = (long long)nc[0] * (J1 + (long long)nc[1] * K0);
+    const long long r01 = (long long)nc[0] * (J0 + (long long)nc[1] * K1);
+    const long long r11 = (long long)nc[0] * (J1 + (long long)nc[1] * K1);
+    const T w0 = T(0.75), w1 = T(0.25);
+    // order: z outer, y, x inner; weight product (wx * wy) * wz
+    T s = T(0);
+    s += w0 * w0 * w0 * ec[r00 + I0];
+    s += w1 * w0 * w0 * ec[r00 + I1];
+    s += w0 * w1 * w0 * ec[r10 + I0];
+    s += w1 * w1 * w0 * ec[r10 + I1];
+    s += w0 * w0 * w1 * ec[r01 + I0];
+    s += w1 * w0 * w1 * ec[r01 + I1];
+    s += w0 * w1 * w1 * ec[r11 + I0];
+    s += w1 * w1 * w1 * ec[r11 + I1];
+    return s;
 }
 
 // ---------------------------------------------------------------------------
 // (3) residual and restriction: coarse b = mean of (b - A x) over 8 children
 // ---------------------------------------------------------------------------
+
+// Residual of the 4 cells of the quad at (i0, j, k): b - A x, faces in the
+// order of stencil() (x-, x+, y-, y+, z-, z+).
+template <class T>
+__device__ __forceinline__ Quad<T> residual_quad(const T *__restrict__ x, const T *__restrict__ b,
+                                                 const T *__restrict__ wx, const T *__restrict__ wy,
+                                                 const T *__restrict__ wz, int nx, int ny, int nz,
+                                                 int per, int i0, int j, int k)
+{
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long c = i0 + sy * j + sz * k;
+    const Quad<T> Z{{T(0), T(0), T(0), T(0)}};
+    const bool has_w = i0 > 0 || (per & 1), has_e = i0 + 4 < nx || (per & 1);
+    const long long cw = i0 > 0 ? c - 1 : c + nx - 1;
+    const long long ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
+    const bool has_s = j > 0 || (per & 2), has_n = j + 1 < ny || (per & 2);
+    const long long cs = j > 0 ? c - sy : c + sy * (ny - 1);
+    const long long cn = j + 1 < ny ? c + sy : c - sy * (ny - 1);
+    const bool has_b = k > 0 || (per & 4), has_t = k + 1 < nz || (per & 4);
+    const long long cb = k > 0 ? c - sz : c + sz * (nz - 1);
+    const long long ct = k + 1 < nz ? c + sz : c - sz * (nz - 1);
+    const Quad<T> xq = ldq(x + c), bq = ldq(b + c);
+    const Quad<T> fx = ldq(wx + c), fy = ldq(wy + c), fz = ldq(wz + c);
+    const Quad<T> fyn = has_n ? ldq(wy + cn) : Z, fzt = has_t ? ldq(wz + ct) : Z;
+    const Quad<T> xs = has_s ? ldq(x + cs) : Z, xn = has_n ? ldq(x + cn) : Z;
+    const Quad<T> xb = has_b ? ldq(x + cb) : Z, xt = has_t ? ldq(x + ct) : Z;
+    const T xw = has_w ? x[cw] : T(0), xe = has_e ? x[ce] : T(0);
+    const T fxe = has_e ? wx[ce] : T(0);
+    Quad<T> r;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const T xc = xq.v[u];
+        T f = fx.v[u] * ((u > 0 ? xq.v[u - 1] : xw) - xc);
+        f += (u < 3 ? fx.v[u + 1] : fxe) * ((u < 3 ? xq.v[u + 1] : xe) - xc);
+        f += fy.v[u] * (xs.v[u] - xc);
+        f += fyn.v[u] * (xn.v[u] - xc);
+        f += fz.v[u] * (xb.v[u] - xc);
+        f += fzt.v[u] * (xt.v[u] - xc);
+        r.v[u] = bq.v[u] - f;
+    }
+    return r;
+}
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restrict__ lv,
@@ -224,7 +448,39 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
     const LevelView L = lv[e];
     if (!L.st->active) return;
     const int ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2];
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int lb = blockIdx.x - start[e];
+    const T *x = (const T *)L.x;
+    const T *b = (const T *)L.b;
+    const T *wx = (const T *)L.w[0], *wy = (const T *)L.w[1], *wz = (const T *)L.w[2];
+    if ((nx & 3) == 0) {
+        // a thread owns the coarse pair (2P, 2P+1) of a coarse row: one fine quad
+        // in each of the 2 x 2 fine rows below it
+        const int np = ncx >> 1;
+        const int xt_n = (np + 31) >> 5;
+        const int xt = lb % xt_n, rb = lb / xt_n;
+        const int crow = rb * kRowsPerBlock + (threadIdx.x >> 5);
+        if (crow >= ncy * ncz) return;
+        const int P = (xt << 5) + (threadIdx.x & 31);
+        if (P >= np) return;
+        const int J = crow % ncy, K = crow / ncy;
+        T s0 = T(0), s1 = T(0);
+#pragma unroll
+        for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++) {
+                const Quad<T> r = residual_quad(x, b, wx, wy, wz, nx, ny, nz, L.per, 4 * P, 2 * J + dy,
+                                                2 * K + dz);
+                s0 += r.v[0];
+                s0 += r.v[1];
+                s1 += r.v[2];
+                s1 += r.v[3];
+            }
+        T *bc = (T *)L.bc + (long long)ncx * crow + 2 * P;
+        bc[0] = s0 * T(0.125);
+        bc[1] = s1 * T(0.125);
+        return;
+    }
     const int xt_n = coarse_xtiles(ncx);
     const int xt = lb % xt_n, rb = lb / xt_n;
     const int crow = rb * kRowsPerBlock + (threadIdx.x >> 5);
@@ -232,10 +488,6 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
     const int I = xt * kCSeg + (threadIdx.x & 31);
     if (I >= ncx) return;
     const int J = crow % ncy, K = crow / ncy;
-    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const T *x = (const T *)L.x;
-    const T *b = (const T *)L.b;
-    const T *wx = (const T *)L.w[0], *wy = (const T *)L.w[1], *wz = (const T *)L.w[2];
     T s = T(0);
 #pragma unroll
     for (int dz = 0; dz < 2; dz++)
@@ -252,59 +504,67 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
     ((T *)L.bc)[I + (long long)ncx * crow] = s * T(0.125);
 }
 
-// ---------------------------------------------------------------------------
-// (4) prolongation and correction: x += trilinear(e_coarse)
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ int partner(int i, int nc, int periodic)
+// Blocks of a restriction launch over the coarse level of `n`.
+int restrict_blocks(const int n[3], const int nc[3])
 {
-    const int I = i >> 1;
-    int J = (i & 1) ? I + 1 : I - 1;
-    if (J < 0 || J >= nc) J = periodic ? (J + nc) % nc : I;  // wrap, or mirror at a wall
-    return J;
+    if ((n[0] & 3) != 0) return coarse_blocks(nc);
+    const int np = nc[0] >> 1;
+    return ((np + 31) >> 5) * ((nc[1] * nc[2] + kRowsPerBlock - 1) / kRowsPerBlock);
 }
+
+// ---------------------------------------------------------------------------
+// (4) prolongation and correction: x += P e_c.  outer_update: finest level with
+// no post-smoothing, the refinement step ends here, so p += (double) x too.
+// ---------------------------------------------------------------------------
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
-                                                      const int *__restrict__ start, int count)
+                                                      const int *__restrict__ start, int count,
+                                                      const OuterView *__restrict__ ov,
+                                                      int outer_update)
 {
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
     if (!L.st->active) return;
-    const Tile t = fine_tile(L.n, blockIdx.x - start[e]);
-    if (!t.ok) return;
-    const int nx = L.n[0];
-    const int ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2];
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const T *ec = (const T *)L.xc;
     T *x = (T *)L.x;
-    const int J0 = t.j >> 1, J1 = partner(t.j, ncy, L.per & 2);
-    const int K0 = t.k >> 1, K1 = partner(t.k, ncz, L.per & 4);
-    const long long r00 = (long long)ncx * (J0 + (long long)ncy * K0);
-    const long long r10 = (long long)ncx * (J1 + (long long)ncy * K0);
-    const long long r01 = (long long)ncx * (J0 + (long long)ncy * K1);
-    const long long r11 = (long long)ncx * (J1 + (long long)ncy * K1);
-    const T w0 = T(0.75), w1 = T(0.25);
+    const int lb = blockIdx.x - start[e];
+    double *pout = outer_update ? ov[L.g].p : nullptr;
+    if ((nx & 3) == 0) {
+        const int nq = nx >> 2;
+        const int xt_n = (nq + 31) >> 5;
+        const int xt = lb % xt_n, rb = lb / xt_n;
+        const int row = rb * kRowsPerBlock + (threadIdx.x >> 5);
+        if (row >= ny * nz) return;
+        const int qx = (xt << 5) + (threadIdx.x & 31);
+        if (qx >= nq) return;
+        const int j = row % ny, k = row / ny;
+        const long long c = (long long)row * nx + 4 * qx;
+        Quad<T> xq = ldq(x + c);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            xq.v[u] += prolong_at(ec, L.nc, L.per, 4 * qx + u, j, k);
+            if (pout) pout[c + u] += (double)xq.v[u];
+        }
+        stq(x + c, xq);
+        return;
+    }
+    const Tile t = fine_tile(L.n, lb);
+    if (!t.ok) return;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
         if (i >= nx) continue;
-        const int I0 = i >> 1, I1 = partner(i, ncx, L.per & 1);
-        // order: z outer, y, x inner; weight product (wx * wy) * wz
-        T s = T(0);
-        s += w0 * w0 * w0 * ec[r00 + I0];
-        s += w1 * w0 * w0 * ec[r00 + I1];
-        s += w0 * w1 * w0 * ec[r10 + I0];
-        s += w1 * w1 * w0 * ec[r10 + I1];
-        s += w0 * w0 * w1 * ec[r01 + I0];
-        s += w1 * w0 * w1 * ec[r01 + I1];
-        s += w0 * w1 * w1 * ec[r11 + I0];
-        s += w1 * w1 * w1 * ec[r11 + I1];
-        x[(long long)nx * t.row + i] += s;
+        const long long c = (long long)nx * t.row + i;
+        const T xn = x[c] + prolong_at(ec, L.nc, L.per, i, t.j, t.k);
+        x[c] = xn;
+        if (pout) pout[c] += (double)xn;
     }
 }
 
 // ---------------------------------------------------------------------------
-// y = A x on one level (unit checks)
+// y = A x on one level (unit checks): x in x, y in b
 // ---------------------------------------------------------------------------
 
 template <class T>
@@ -312,7 +572,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const LevelView *__restrict_
                                                     const int *__restrict__ start, int count)
 {
     const int e = find_entry(start, count);
-    const LevelView L = lv[e];
+    const LevelView &L = lv[e];
     const Tile t = fine_tile(L.n, blockIdx.x - start[e]);
     if (!t.ok) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
@@ -336,9 +596,13 @@ __global__ void __launch_bounds__(kThreads) k_apply(const LevelView *__restrict_
 
 // For sum(b) = 0 this is the zero-mean solution of A e = b; for sum(b) != 0 it
 // solves A e = b - mean(b) and adds a constant, which the cycle ignores
-// (A 1 = 0) and the final mean removal takes out.
+// (A 1 = 0) and the final mean removal takes out.  One warp per row of G
+// (rows are contiguous, G is symmetric), lanes split the dot product, fixed
+// shuffle tree.  A grid whose finest level is its coarsest (C.outer) also
+// gets p += (double) e.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__restrict__ cv)
+__global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__restrict__ cv,
+                                                           const OuterView *__restrict__ ov)
 {
     const CoarseView &C = cv[blockIdx.x];
     if (!C.st->active) return;
@@ -348,10 +612,18 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__r
     for (int t = threadIdx.x; t < n; t += blockDim.x) rb[t] = (double)b[t];
     __syncthreads();
     T *x = (T *)C.x;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    double *pout = (ov != nullptr && C.outer) ? ov[C.g].p : nullptr;
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int t = threadIdx.x >> 5; t < n; t += warps) {
+        const double *Gt = C.G + (long long)t * n;
         double s = 0.0;
-        for (int u = 0; u < n; u++) s += C.G[(long long)u * n + t] * rb[u];
-        x[t] = (T)(-s);
+        for (int u = lane; u < n; u += 32) s += Gt[u] * rb[u];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const T xn = (T)(-s);
+            x[t] = xn;
+            if (pout) pout[t] += (double)xn;
+        }
     }
 }
 
@@ -552,95 +824,120 @@ __global__ void k_begin(const OuterView *__restrict__ ov)
     s->xmean = 0.0;
 }
 
-// Partial sums of the right-hand side (slot 3 of each block's partials).
-__global__ void __launch_bounds__(kThreads) k_bsum(const OuterView *__restrict__ ov,
-                                                   const int *__restrict__ start, int count)
+// Partial sums of the caller's right-hand side (which = 0, partial slot 3) or
+// of the iterate p (which = 1, slot 1), FP64.
+__global__ void __launch_bounds__(kThreads) k_sum(const OuterView *__restrict__ ov,
+                                                  const int *__restrict__ start, int count, int which)
 {
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const int lb = blockIdx.x - start[e];
-    const Tile t = fine_tile(O.n, lb);
+    const int ntiles = fine_blocks(O.n);
+    const double *src = which == 0 ? O.b : O.p;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (t.ok) {
+    for (int tile = lb; tile < ntiles; tile += O.nblk) {
+        const Tile t = fine_tile(O.n, tile);
+        if (!t.ok) continue;
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {
             const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
-            if (i < O.n[0]) v[3] += O.b[rowoff + i];
+            if (i < O.n[0]) v[0] += src[rowoff + i];
         }
     }
     double out[4];
     block_sum4(v, out);
-    if (threadIdx.x == 0) O.part[kPart * lb + 3] = out[3];
+    if (threadIdx.x == 0) O.part[kPart * lb + (which == 0 ? 3 : 1)] = out[0];
 }
 
-// Residual of the outer iteration.  update = 0: r = (b - bmean) - A x for the
-// starting iterate x = p.  update = 1: x' = x + e (x in the buffer selected by
-// the iteration parity, x' written to the other one) and r = (b - bmean) - A x'.
-// r is handed to the V-cycle in its precision Te; ||r||^2, sum x', and (first
-// call) ||b - bmean||^2 go to the block partials.  All arithmetic FP64, with the
-// face differences taken before the products for accuracy near convergence.
+// Sum over the 6 faces of w_f (x_nb - x_c), FP64: the face difference is taken
+// before the product, which keeps the residual accurate to rounding of the
+// differences when x is smooth or carries a large constant.
+__device__ __forceinline__ double flux64(const OuterView &O, const double *__restrict__ x, int i,
+                                         int j, int k, long long c)
+{
+    const int nx = O.n[0], ny = O.n[1], nz = O.n[2], per = O.per;
+    const double *__restrict__ wx = O.w[0];
+    const double *__restrict__ wy = O.w[1];
+    const double *__restrict__ wz = O.w[2];
+    const long long sy = nx, sz = (long long)nx * ny;
+    const double xc = x[c];
+    double f = wx[c] * (x[i > 0 ? c - 1 : ((per & 1) ? c + (nx - 1) : c)] - xc);
+    if (i + 1 < nx) f += wx[c + 1] * (x[c + 1] - xc);
+    else if (per & 1) f += wx[c + 1 - nx] * (x[c + 1 - nx] - xc);
+    f += wy[c] * (x[j > 0 ? c - sy : ((per & 2) ? c + sy * (ny - 1) : c)] - xc);
+    if (j + 1 < ny) f += wy[c + sy] * (x[c + sy] - xc);
+    else if (per & 2) f += wy[c - sy * (ny - 1)] * (x[c - sy * (ny - 1)] - xc);
+    f += wz[c] * (x[k > 0 ? c - sz : ((per & 4) ? c + sz * (nz - 1) : c)] - xc);
+    if (k + 1 < nz) f += wz[c + sz] * (x[c + sz] - xc);
+    else if (per & 4) f += wz[c - sz * (nz - 1)] * (x[c - sz * (nz - 1)] - xc);
+    return f;
+}
+
+// Outer residual r = (b - mean b) - A p in FP64, handed to the V-cycle in its
+// precision Te.  init = 1 (start of a solve): also stores b0 = b - mean(b) and
+// the partial sums of ||b0||^2 (slot 2), all FP64.  ||r||^2 goes to slot 0; in
+// the refinement steps it is accumulated from the rounded r handed to the
+// cycle (a norm only steers the stopping test, so its own rounding at 1e-7
+// relative is immaterial).
 template <class Te>
 __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restrict__ ov,
                                                        const int *__restrict__ start, int count,
-                                                       int update)
+                                                       int init)
 {
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const GridState *s = O.st;
     if (!s->active) return;
     const int lb = blockIdx.x - start[e];
-    const Tile t = fine_tile(O.n, lb);
-    const int nx = O.n[0], ny = O.n[1], nz = O.n[2];
-    const bool odd = s->iters & 1;
-    const double *xin = odd ? O.xbuf : O.p;
-    double *xout = odd ? O.p : O.xbuf;
-    const Te *ec = (const Te *)O.e;
+    const int ntiles = fine_blocks(O.n);
+    const int nx = O.n[0];
     Te *r = (Te *)O.r;
     const double m = s->bmean;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (t.ok) {
+    Te racc = Te(0);
+    for (int tile = lb; tile < ntiles; tile += O.nblk) {
+        const Tile t = fine_tile(O.n, tile);
+        if (!t.ok) continue;
         const long long rowoff = (long long)nx * t.row;
         for (int h = 0; h < 2; h++) {
             const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
             if (i >= nx) continue;
             const long long c = rowoff + i;
-            double d, f, xc;
-            if (update) {
-                xc = xin[c] + (double)ec[c];
-                stencil(O.w[0], O.w[1], O.w[2], LoadSum<Te>{xin, ec}, nx, ny, nz, O.per, i, t.j,
-                        t.k, c, xc, d, f);
-                xout[c] = xc;
+            const double f = flux64(O, O.p, i, t.j, t.k, c);
+            double bc;
+            if (init) {
+                bc = O.b[c] - m;
+                O.b0[c] = bc;
+                v[2] += bc * bc;
             } else {
-                xc = xin[c];
-                stencil(O.w[0], O.w[1], O.w[2], LoadPlain<double>{xin}, nx, ny, nz, O.per, i, t.j,
-                        t.k, c, xc, d, f);
+                bc = O.b0[c];
             }
-            const double bc = O.b[c] - m;
             const double rc = bc - f;
-            r[c] = (Te)rc;
-            v[0] += rc * rc;
-            v[1] += xc;
-            v[2] += bc * bc;
+            const Te rt = (Te)rc;
+            r[c] = rt;
+            if (init) v[0] += rc * rc;
+            else racc += rt * rt;
         }
     }
+    if (!init) v[0] = (double)racc;
     double out[4];
     block_sum4(v, out);
     if (threadIdx.x == 0) {
         O.part[kPart * lb + 0] = out[0];
-        O.part[kPart * lb + 1] = out[1];
-        O.part[kPart * lb + 2] = out[2];
+        if (init) O.part[kPart * lb + 2] = out[2];
     }
 }
 
 // One block per grid: sum the block partials in a fixed order and update the
 // state.  mode 0: mean of b.  mode 1: after the starting residual.  mode 2:
-// after a cycle (counts it).  Stopping test: ||r|| <= tol ||b||; NaN/Inf
-// residual = diverged; max_iters reached = not converged.
+// after a cycle (counts it).  mode 3: mean of the final iterate.  Stopping
+// test: ||r|| <= tol ||b||; NaN/Inf residual = diverged; max_iters reached =
+// not converged.
 __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restrict__ ov, int mode)
 {
     const OuterView &O = ov[blockIdx.x];
     GridState *s = O.st;
-    if (!s->active) return;
+    if (mode != 3 && !s->active) return;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int q = threadIdx.x; q < O.nblk; q += blockDim.x)
         for (int f = 0; f < 4; f++) v[f] += O.part[kPart * q + f];
@@ -652,15 +949,18 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
         s->bmean = out[3] / N;
         return;
     }
+    if (mode == 3) {
+        s->xmean = out[1] / N;
+        return;
+    }
     const double rn = sqrt(out[0]);
     if (mode == 1) {
         s->bnorm = sqrt(out[2]);
         s->r0 = rn;
     } else {
-        s->iters += 1;
+        s->iters += O.inner;
     }
     s->rnorm = rn;
-    s->xmean = out[1] / N;
     if (!isfinite(rn)) {
         s->status = 5;  // MG_EDIVERGED
         s->active = 0;
@@ -673,23 +973,25 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
     }
 }
 
-// End of a solve: p = x - mean(x) from whichever buffer holds the iterate (a
-// zero right-hand side gives p = 0).
+// End of a solve: p = p - mean(p) (a zero right-hand side gives p = 0).
 __global__ void __launch_bounds__(kThreads) k_final(const OuterView *__restrict__ ov,
                                                     const int *__restrict__ start, int count)
 {
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const GridState *s = O.st;
-    const Tile t = fine_tile(O.n, blockIdx.x - start[e]);
-    if (!t.ok) return;
-    const double *x = (s->iters & 1) ? O.xbuf : O.p;
+    const int lb = blockIdx.x - start[e];
+    const int ntiles = fine_blocks(O.n);
     const double m = s->xmean;
     const bool zero = s->bnorm == 0.0;
-    const long long rowoff = (long long)O.n[0] * t.row;
-    for (int h = 0; h < 2; h++) {
-        const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
-        if (i < O.n[0]) O.p[rowoff + i] = zero ? 0.0 : x[rowoff + i] - m;
+    for (int tile = lb; tile < ntiles; tile += O.nblk) {
+        const Tile t = fine_tile(O.n, tile);
+        if (!t.ok) continue;
+        const long long rowoff = (long long)O.n[0] * t.row;
+        for (int h = 0; h < 2; h++) {
+            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+            if (i < O.n[0]) O.p[rowoff + i] = zero ? 0.0 : O.p[rowoff + i] - m;
+        }
     }
 }
 
@@ -726,10 +1028,9 @@ void launch_loop_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStr
 }
 
 template <class T>
-void launch_smooth(const Table &tb, int colour, double omega, int zero_guess, cudaStream_t s)
+void launch_half(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
-    k_smooth<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega,
-                                               zero_guess);
+    k_half<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, ov);
 }
 template <class T>
 void launch_restrict(const Table &tb, cudaStream_t s)
@@ -737,9 +1038,9 @@ void launch_restrict(const Table &tb, cudaStream_t s)
     k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
 }
 template <class T>
-void launch_prolong(const Table &tb, cudaStream_t s)
+void launch_prolong(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
 {
-    k_prolong<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
+    k_prolong<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
 }
 template <class T>
 void launch_apply(const Table &tb, cudaStream_t s)
@@ -747,9 +1048,9 @@ void launch_apply(const Table &tb, cudaStream_t s)
     k_apply<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
 }
 template <class T>
-void launch_coarse_solve(const CoarseView *cv, int count, cudaStream_t s)
+void launch_coarse_solve(const CoarseView *cv, int count, const OuterView *ov, cudaStream_t s)
 {
-    k_coarse_solve<T><<<count, kThreads, 0, s>>>(cv);
+    k_coarse_solve<T><<<count, kThreads, 0, s>>>(cv, ov);
 }
 void launch_coarse_setup(const CoarseView *cv, int count, cudaStream_t s)
 {
@@ -774,14 +1075,14 @@ void launch_coarsen_faces(const CoarsenArgs &a, cudaStream_t s)
     k_coarsen_faces<<<cells_grid((long long)a.nc[0] * a.nc[1] * a.nc[2]), kThreads, 0, s>>>(a);
 }
 void launch_begin(const OuterView *ov, int count, cudaStream_t s) { k_begin<<<count, 32, 0, s>>>(ov); }
-void launch_bsum(const OuterTable &ot, cudaStream_t s)
+void launch_sum(const OuterTable &ot, int which, cudaStream_t s)
 {
-    k_bsum<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    k_sum<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, which);
 }
 template <class Te>
-void launch_residual(const OuterTable &ot, int update, cudaStream_t s)
+void launch_residual(const OuterTable &ot, int init, cudaStream_t s)
 {
-    k_residual<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, update);
+    k_residual<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, init);
 }
 void launch_finalize(const OuterTable &ot, int mode, cudaStream_t s)
 {
@@ -792,16 +1093,16 @@ void launch_final(const OuterTable &ot, cudaStream_t s)
     k_final<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
 }
 
-template void launch_smooth<float>(const Table &, int, double, int, cudaStream_t);
-template void launch_smooth<double>(const Table &, int, double, int, cudaStream_t);
+template void launch_half<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_half<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
 template void launch_restrict<float>(const Table &, cudaStream_t);
 template void launch_restrict<double>(const Table &, cudaStream_t);
-template void launch_prolong<float>(const Table &, cudaStream_t);
-template void launch_prolong<double>(const Table &, cudaStream_t);
+template void launch_prolong<float>(const Table &, const OuterView *, int, cudaStream_t);
+template void launch_prolong<double>(const Table &, const OuterView *, int, cudaStream_t);
 template void launch_apply<float>(const Table &, cudaStream_t);
 template void launch_apply<double>(const Table &, cudaStream_t);
-template void launch_coarse_solve<float>(const CoarseView *, int, cudaStream_t);
-template void launch_coarse_solve<double>(const CoarseView *, int, cudaStream_t);
+template void launch_coarse_solve<float>(const CoarseView *, int, const OuterView *, cudaStream_t);
+template void launch_coarse_solve<double>(const CoarseView *, int, const OuterView *, cudaStream_t);
 template void launch_residual<float>(const OuterTable &, int, cudaStream_t);
 template void launch_residual<double>(const OuterTable &, int, cudaStream_t);
 

@@ -42,18 +42,25 @@ struct CoarsenArgs {
     float *wc32[3];
 };
 
-template <class T> void launch_smooth(const Table &, int colour, double omega, int zero_guess, cudaStream_t);
+// red-black half-sweep of one colour; flags: 1 zero initial iterate (red
+// launch), 4 add the relaxed values to the FP64 iterate
+constexpr int kHalfZero = 1, kHalfOuter = 4;
+int half_sweep_blocks(const int n[3]);
+int restrict_blocks(const int n[3], const int nc[3]);
+int prolong_blocks(const int n[3]);
+template <class T> void launch_half(const Table &, int colour, double omega, int flags,
+                                    const OuterView *ov, cudaStream_t);
 template <class T> void launch_restrict(const Table &, cudaStream_t);
-template <class T> void launch_prolong(const Table &, cudaStream_t);
+template <class T> void launch_prolong(const Table &, const OuterView *ov, int outer_update, cudaStream_t);
 template <class T> void launch_apply(const Table &, cudaStream_t);
-template <class T> void launch_coarse_solve(const CoarseView *, int count, cudaStream_t);
+template <class T> void launch_coarse_solve(const CoarseView *, int count, const OuterView *ov, cudaStream_t);
 void launch_coarse_setup(const CoarseView *, int count, cudaStream_t);
 void launch_faces_from_density(const FaceArgs &, cudaStream_t);
 void launch_scale_faces(const FaceArgs &, cudaStream_t);
 void launch_coarsen_faces(const CoarsenArgs &, cudaStream_t);
 void launch_begin(const OuterView *, int count, cudaStream_t);
-void launch_bsum(const OuterTable &, cudaStream_t);
-template <class Te> void launch_residual(const OuterTable &, int update, cudaStream_t);
+void launch_sum(const OuterTable &, int which, cudaStream_t);
+template <class Te> void launch_residual(const OuterTable &, int init, cudaStream_t);
 void launch_finalize(const OuterTable &, int mode, cudaStream_t);
 void launch_final(const OuterTable &, cudaStream_t);
 void launch_gather_states(const OuterTable &, GridState *out, cudaStream_t);

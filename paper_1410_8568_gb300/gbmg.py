@@ -40,7 +40,8 @@ class Grid(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
-                ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -131,13 +132,16 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
     return g
 
 
-def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True) -> Params:
+def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
+                inner_cycles=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
     p.max_iters = int(max_iters)
     p.precision = int(precision)
     p.use_graph = 1 if use_graph else 0
+    if inner_cycles is not None:
+        p.inner_cycles = int(inner_cycles)
     return p
 
 
@@ -186,7 +190,8 @@ class Solver:
     """One grid's hierarchy (mg_create ... mg_destroy)."""
 
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
-                 precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None):
+                 precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
+                 inner_cycles=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -195,7 +200,7 @@ class Solver:
         self.cells = int(np.prod(self.shape))
         self.precision = precision
         self.grid = make_grid(self.shape, self.bc, self.length)
-        self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph)
+        self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:
@@ -295,8 +300,8 @@ class Solver:
     def apply(self, level, x, y, prec=FP64):
         check(lib().mg_apply(self._h, int(level), int(prec), _ptr(x), _ptr(y)), "mg_apply")
 
-    def smooth(self, level, b, x, half_sweeps, prec=FP64):
-        check(lib().mg_smooth(self._h, int(level), int(prec), _ptr(b), _ptr(x), int(half_sweeps)), "mg_smooth")
+    def smooth(self, level, b, x, sweeps, prec=FP64):
+        check(lib().mg_smooth(self._h, int(level), int(prec), _ptr(b), _ptr(x), int(sweeps)), "mg_smooth")
 
     def restrict_residual(self, level, b, x, coarse_b, prec=FP64):
         check(lib().mg_restrict_residual(self._h, int(level), int(prec), _ptr(b), _ptr(x), _ptr(coarse_b)),
