@@ -72,6 +72,7 @@ extern "C" {
 #define MG_EBUDGET 9
 #define MG_ESINGULAR 10
 #define MG_ENOTFOUND 11
+#define MG_ETOOBIG 12 /* larger than the fixed scratch area of mg_coarse_solve_static */
 
 #define MG_BC_NEUMANN 0  /* walls at both ends of the axis: zero normal flux */
 #define MG_BC_PERIODIC 1 /* the axis wraps around */
@@ -83,6 +84,7 @@ extern "C" {
 #define MG_FACE_ARITHMETIC 1 /* (a_L + a_R) / 2 */
 
 #define MG_MAX_COARSE 512 /* most cells allowed on the coarsest grid */
+#define MG_STATIC_MAX_CELLS 512 /* most cells of a grid solved by mg_coarse_solve_static */
 #define MG_MAX_LEVELS 16
 
 typedef struct {
@@ -263,6 +265,32 @@ int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x)
 
 /* e = zero-mean solution of A e = r - mean(r) on the coarsest level (item 6). */
 int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e);
+
+/* Exact solve of a small grid without allocating any memory (the paper has no
+ * counterpart: this serves callers that cannot allocate device memory when
+ * they need the solve, e.g. while a stream is being captured into a CUDA
+ * graph, in a real-time loop with a fixed memory budget, or inside a host
+ * whose allocator owns the device memory).
+ *
+ * Solves A e = r - mean(r) for the grid `grid` (at most MG_STATIC_MAX_CELLS
+ * cells, any size per axis, walls or periodic) with face coefficients ax, ay,
+ * az (DEVICE, alpha = 1/rho in the layout above, > 0 off the walls) and writes
+ * e (DEVICE, nx*ny*nz doubles), all in FP64: it assembles -A + c 1 1^T, inverts
+ * it by Gauss-Jordan elimination and applies the inverse, the same arithmetic
+ * as the coarsest-grid solve of a handle.  The result has a constant offset
+ * -sum(r) / (c n^2) (zero when sum(r) = 0), like mg_coarse_solve.
+ *
+ * Scratch: a 2 MiB array in the library's static device memory, held by every
+ * device that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (make that first call before
+ * any stream capture starts); no call allocates or frees memory.  Every call
+ * on a device shares the array: calls whose kernels can overlap on the GPU
+ * (unordered streams) race and must be serialised by the caller.  Synchronous
+ * on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * Returns MG_ETOOBIG above MG_STATIC_MAX_CELLS cells, MG_EINVAL for bad
+ * arguments or coefficients, MG_ESINGULAR for a grid cut into pieces. */
+int mg_coarse_solve_static(const mg_grid *grid, const double *ax, const double *ay,
+                           const double *az, const double *r, double *e, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Timing of individual kernels.  While enabled, every kernel launch of the

@@ -775,6 +775,7 @@ const char *mg_strerror(int s)
     case MG_EBUDGET: return "request exceeds the device-memory budget";
     case MG_ESINGULAR: return "coarsest-grid matrix is singular (grid cut by zero coefficients)";
     case MG_ENOTFOUND: return "unknown ticket";
+    case MG_ETOOBIG: return "grid larger than the static scratch area (MG_STATIC_MAX_CELLS cells)";
     default: return "unknown status";
     }
 }

@@ -19,7 +19,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgbmg.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EDIVERGED, ETIMEOUT, EBUSY, EAGAIN, EBUDGET, ESINGULAR, ENOTFOUND = range(12)
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EDIVERGED, ETIMEOUT, EBUSY, EAGAIN, EBUDGET, ESINGULAR, ENOTFOUND, ETOOBIG = range(13)
+STATIC_MAX_CELLS = 512
 NEUMANN, PERIODIC = 0, 1
 FP64, MIXED = 0, 1
 HARMONIC, ARITHMETIC = 0, 1
@@ -100,6 +101,7 @@ def lib():
             "mg_profile_read": (_I, [_V, _I, _I, _P(ctypes.c_int64), _P(_D)]),
             "mg_memory_bytes": (_I, [_V, _P(ctypes.c_size_t)]),
             "mg_memory_estimate": (_I, [_P(Grid), _P(Params), _P(ctypes.c_size_t)]),
+            "mg_coarse_solve_static": (_I, [_P(Grid), _V, _V, _V, _V, _V, _V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -327,6 +329,18 @@ class Solver:
         v = ctypes.c_size_t()
         check(lib().mg_memory_bytes(self._h, ctypes.byref(v)))
         return v.value
+
+
+def coarse_solve_static(shape, bc, faces, r, e, length=(1.0, 1.0, 1.0), stream=None) -> int:
+    """Exact FP64 solve of a grid of at most STATIC_MAX_CELLS cells without any
+    device allocation (mg_coarse_solve_static).  Returns the status code."""
+    import torch
+
+    g = make_grid(shape, bc, length)
+    n = int(np.prod(shape))
+    d = torch.float64
+    return lib().mg_coarse_solve_static(ctypes.byref(g), *[_ptr(f, n, d) for f in faces], _ptr(r, n, d),
+                                        _ptr(e, n, d), _stream(stream))
 
 
 def memory_estimate(shape, bc, precision=MIXED, length=(1.0, 1.0, 1.0)) -> int:
