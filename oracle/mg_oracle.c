@@ -23,8 +23,9 @@
  * and the stopping test and average reduction rate of Eq. 15.
  *
  * Readings where the paper is silent (each one also listed in the design notes):
- *  - restriction "linear interpolation of the residual" (3) is read as the mean
- *    of the 8 fine children of a coarse cell;
+ *  - the restriction of the residual (3), for which the paper names a linear
+ *    interpolation but gives no formula, is read as the mean of the 8 fine
+ *    children of a coarse cell;
  *  - the coarse face coefficient is the mean of the 4 fine face coefficients
  *    that tile the coarse face (flux through a coarse face = sum of fine fluxes);
  *  - prolongation (4) uses trilinear weights 3/4, 1/4 per axis; at a Neumann
