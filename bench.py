@@ -1,7 +1,7 @@
 """Benchmark of the GB300 pressure multigrid (arXiv 1410.8568, Sec. 2.3).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload drop_film_128|drop_film_512|sphere_32]
+                    [--workload drop_film_128|drop_film_256|drop_film_512|sphere_32]
 
 Metric: Poisson multigrid solves per second to a relative residual of 1e-10,
 mixed precision (FP32 V(2,2) cycles inside FP64 iterative refinement) next to
@@ -50,6 +50,8 @@ L2_FLUSH_BYTES = 256 << 20
 WORKLOADS = {
     "drop_film_128": dict(kind="config2", n=128,
                           desc="drop_film_128^3_1000to1: film depth 0.1 + drop R 0.125 at z 0.3, periodic x,y, Neumann z, Fourier-divergence RHS"),
+    "drop_film_256": dict(kind="config2", n=256,
+                          desc="drop_film_256^3_1000to1: film depth 0.1 + drop R 0.125 at z 0.3, periodic x,y, Neumann z, Fourier-divergence RHS"),
     "drop_film_512": dict(kind="config3", n=512,
                           desc="drop_film_512^3_1000to1: film + drop + 0-4 droplets, periodic x,y, Neumann z, Fourier-divergence RHS"),
     "sphere_32": dict(kind="config1", n=32,
@@ -159,11 +161,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def count_launches(levels, iters, nu1=2, nu2=2, inner=2):
-    """Kernels of one step: coefficient set-up, prologue, refinement steps, epilogue."""
-    setup = 1 + (levels - 1) + 1       # faces from density, coarsening per level, coarsest inverse
+def level_shapes(shape):
+    """Multigrid levels of a grid: all axes halved while every axis is even and > 2."""
+    out = [tuple(shape)]
+    while all(n % 2 == 0 and n > 2 for n in out[-1]):
+        out.append(tuple(n // 2 for n in out[-1]))
+    return out
+
+
+def count_launches(shape, iters, nu1=2, nu2=2, inner=2, tail_cells=4096, mixed=True):
+    """Kernels of one step: coefficient set-up, prologue, refinement steps, epilogue.
+    In FP32 cycles the levels of at most tail_cells cells (below the finest) run in one launch."""
+    lv = level_shapes(shape)
+    L = len(lv)
+    lt = next((l for l in range(1, L - 1) if math.prod(lv[l]) <= tail_cells), L) if mixed else L
+    normal = lt if lt < L else L - 1
+    setup = 1 + (L - 1) + 1            # faces from density, coarsening per level, coarsest inverse
     prologue = 6                       # begin, sum b, mean, residual, finalize, loop control
-    cycle = (levels - 1) * (2 * nu1 + 1 + 1 + 2 * nu2) + 1  # half-sweeps, restriction, prolongation; coarsest
+    cycle = normal * (2 * nu1 + 1 + 1 + 2 * nu2) + 1  # half-sweeps, restriction, prolongation; tail or coarsest
     step = inner * cycle + 3           # + residual, finalize, loop control
     epilogue = 3                       # sum p, mean, p - mean
     return setup + prologue + (iters // inner) * step + epilogue
@@ -352,7 +367,7 @@ def main():
 
     if rank == 0:
         m, f = results[gbmg.MIXED], results[gbmg.FP64]
-        launches = args.steps * count_launches(m["levels"], m["iters"])
+        launches = args.steps * count_launches(P.shape, m["iters"])
         line = {
             "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"],

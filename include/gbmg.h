@@ -29,10 +29,11 @@
  * the right-hand side (reported in mg_stats.rhs_mean) and returns the solution
  * with zero mean.
  *
- * Size rule.  Every axis is n = m * 2^k with m in {2, 3, 4} (2, 3, 4, 6, 8, 12,
- * 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, ...).  All axes are
- * coarsened together while every axis is even and larger than 4; the coarsest
- * grid must have at most MG_MAX_COARSE cells (it is solved exactly).
+ * Size rule.  Every axis has n >= 2 cells and the grid fewer than 2^31 cells.
+ * All axes are coarsened together while every axis is even and larger than 2;
+ * the coarsest grid must have at most MG_MAX_COARSE cells (it is solved
+ * exactly).  Every n = m * 2^k with m in {1, 2, 3, 4} qualifies (2, 3, 4, 6, 8,
+ * 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, ...).
  *
  * Ownership.  The caller owns every buffer it passes.  Device pointers are
  * device memory of the current CUDA device.  A handle owns its hierarchy (all
@@ -305,7 +306,8 @@ int mg_coarse_solve_static(const mg_grid *grid, const double *ax, const double *
 #define MG_K_COARSE 3
 #define MG_K_RESIDUAL 4 /* the FP64 outer update + residual + norms */
 #define MG_K_OTHER 5
-#define MG_K_KINDS 6
+#define MG_K_TAIL 6 /* the levels of at most 4096 cells and the coarsest solve, one block per grid */
+#define MG_K_KINDS 7
 
 int mg_profile_enable(mg_handle *h, int enable);
 int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double *total_ms);

@@ -53,7 +53,7 @@ int make_levels(const mg_grid &g, int n[][3], int *L)
         const int *p = n[l - 1];
         bool ok = true;
         for (int d = 0; d < 3; d++)
-            if (p[d] % 2 != 0 || p[d] <= 4) ok = false;
+            if (p[d] % 2 != 0 || p[d] <= 2) ok = false;
         if (!ok) break;
         for (int d = 0; d < 3; d++) n[l][d] = p[d] / 2;
         l++;
@@ -73,7 +73,7 @@ int check_grid(const mg_grid *g)
         if (!(l[d] > 0.0) || !isfinite(l[d])) return MG_EINVAL;
         if (g->bc[d] != MG_BC_NEUMANN && g->bc[d] != MG_BC_PERIODIC) return MG_EINVAL;
     }
-    if ((long long)n[0] * n[1] * n[2] > (1LL << 34)) return MG_EINVAL;
+    if ((long long)n[0] * n[1] * n[2] >= (1LL << 31)) return MG_EINVAL;
     int lv[MG_MAX_LEVELS][3], L;
     return make_levels(*g, lv, &L);
 }
@@ -93,7 +93,7 @@ struct Layout {
     int L;
     int n[MG_MAX_LEVELS][3];
     size_t w64[MG_MAX_LEVELS][3], w32[MG_MAX_LEVELS][3], x[MG_MAX_LEVELS], b[MG_MAX_LEVELS];
-    size_t G, b0, part, err, state, dstate, dview, dstart, dcview, total;
+    size_t G, b0, part, err, state, dstate, dview, dstart, dcview, setup_cv, total;
     int nblk0;
 };
 
@@ -125,6 +125,7 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
     lay.dview = c.take(sizeof(LevelView));
     lay.dstart = c.take(2 * sizeof(int));
     lay.dcview = c.take(sizeof(CoarseView));
+    lay.setup_cv = c.take(sizeof(CoarseView));
     lay.total = c.off;
     return MG_OK;
 }
@@ -169,6 +170,21 @@ int Plan::build(mg_handle *const *handles, int count)
     prm = hs[0]->prm;
     Lmax = 0;
     for (auto *h : hs) Lmax = std::max(Lmax, h->L);
+    // first level of each grid handled by the bottom-of-cycle kernel: the first
+    // level below the finest with at most kTailCells cells, if at least one
+    // level above the coarsest qualifies (else the grid has no tail: lt = L).
+    // FP32 cycles only: one block per grid runs at one SM's FP64 rate, which on
+    // this GPU is far below that of the per-level FP64 kernels spread over all SMs.
+    std::vector<int> lt(G);
+    for (int g = 0; g < G; g++) {
+        mg_handle *h = hs[g];
+        lt[g] = h->L;
+        for (int l = 1; mixed && l + 1 < h->L && l < MG_MAX_LEVELS; l++)
+            if (h->lev[l].N <= kTailCells && h->L - l <= kMaxTail) {
+                lt[g] = l;
+                break;
+            }
+    }
     // host copies of the tables
     std::vector<LevelView> lv;
     std::vector<int> starts;
@@ -179,7 +195,7 @@ int Plan::build(mg_handle *const *handles, int count)
         std::vector<int> sf{0}, sc{0}, sh{0};
         for (int g = 0; g < G; g++) {
             mg_handle *h = hs[g];
-            if (l + 1 >= h->L) continue;
+            if (l + 1 >= h->L || l >= lt[g]) continue;
             const HLevel &F = h->lev[l], &C = h->lev[l + 1];
             LevelView v;
             memset(&v, 0, sizeof(v));
@@ -221,12 +237,14 @@ int Plan::build(mg_handle *const *handles, int count)
     const size_t o_lv = c.take(std::max<size_t>(1, lv.size()) * sizeof(LevelView));
     const size_t o_st = c.take(starts.size() * sizeof(int));
     const size_t o_cv = c.take(G * sizeof(CoarseView));
+    const size_t o_tv = c.take(G * sizeof(TailView));
     const size_t o_ov = c.take(G * sizeof(OuterView));
     const size_t o_gs = c.take(G * sizeof(GridState));
     CK(cudaMalloc((void **)&mem, c.off));
     LevelView *d_lv = (LevelView *)(mem + o_lv);
     int *d_starts = (int *)(mem + o_st);
     cv = (CoarseView *)(mem + o_cv);
+    tv = (TailView *)(mem + o_tv);
     ov = (OuterView *)(mem + o_ov);
     st = (GridState *)(mem + o_gs);
     for (int l = 0; l < MG_MAX_LEVELS; l++) {
@@ -241,11 +259,41 @@ int Plan::build(mg_handle *const *handles, int count)
         half[l] = Table{d_lv + r.lv0, d_starts + r.sh, r.count, r.bh};
     }
     ot = OuterTable{ov, d_starts + so_off, G, so.back()};
-    std::vector<CoarseView> cvh(G);
+    std::vector<CoarseView> cvh;
+    std::vector<TailView> tvh;
+    const size_t esz = mixed ? sizeof(float) : sizeof(double);
+    tail_smem = 0;
     for (int g = 0; g < G; g++) {
         mg_handle *h = hs[g];
+        if (lt[g] >= h->L) continue;
+        TailView v;
+        memset(&v, 0, sizeof(v));
+        v.nt = h->L - lt[g];
+        v.per = h->per;
+        int off = 0;
+        for (int t = 0; t < v.nt; t++) {
+            const HLevel &Lv = h->lev[lt[g] + t];
+            for (int d = 0; d < 3; d++) {
+                v.n[t][d] = Lv.n[d];
+                v.w[t][d] = mixed ? (void *)Lv.w32[d] : (void *)Lv.w64[d];
+            }
+            v.off[t] = off;
+            off += 5 * (int)Lv.N;
+            off = (off + 3) & ~3;
+        }
+        v.x0 = h->lev[lt[g]].x;
+        v.b0 = h->lev[lt[g]].b;
+        v.G = h->G;
+        v.st = h->state;
+        tvh.push_back(v);
+        tail_smem = std::max(tail_smem, (size_t)off * esz);
+    }
+    for (int g = 0; g < G; g++) {
+        mg_handle *h = hs[g];
+        if (lt[g] < h->L) continue;
         const HLevel &Cl = h->lev[h->L - 1];
-        CoarseView &v = cvh[g];
+        cvh.emplace_back();
+        CoarseView &v = cvh.back();
         memset(&v, 0, sizeof(v));
         for (int d = 0; d < 3; d++) {
             v.n[d] = Cl.n[d];
@@ -283,7 +331,10 @@ int Plan::build(mg_handle *const *handles, int count)
     }
     if (!lv.empty()) CK(cudaMemcpy(d_lv, lv.data(), lv.size() * sizeof(LevelView), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_starts, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(cv, cvh.data(), G * sizeof(CoarseView), cudaMemcpyHostToDevice));
+    ncv = (int)cvh.size();
+    ntv = (int)tvh.size();
+    if (ncv) CK(cudaMemcpy(cv, cvh.data(), ncv * sizeof(CoarseView), cudaMemcpyHostToDevice));
+    if (ntv) CK(cudaMemcpy(tv, tvh.data(), ntv * sizeof(TailView), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ov, ov_h, G * sizeof(OuterView), cudaMemcpyHostToDevice));
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -368,9 +419,16 @@ static void vcycle(Plan &P, Prof &pf, int cycle_in_step, bool last_of_step)
         launch_restrict<T>(P.rest[l], s);
         pf.end(s);
     }
-    pf.begin(s, MG_K_COARSE, P.Lmax - 1);
-    launch_coarse_solve<T>(P.cv, P.G, last_of_step ? P.ov : nullptr, s);
-    pf.end(s);
+    if (P.ntv) {
+        pf.begin(s, MG_K_TAIL, 0);
+        launch_tail<T>(P.tv, P.ntv, P.tail_smem, q.omega, q.nu1, q.nu2, s);
+        pf.end(s);
+    }
+    if (P.ncv) {
+        pf.begin(s, MG_K_COARSE, P.Lmax - 1);
+        launch_coarse_solve<T>(P.cv, P.ncv, last_of_step ? P.ov : nullptr, s);
+        pf.end(s);
+    }
     for (int l = P.Lmax - 2; l >= 0; l--) {
         const Table &H = P.half[l];
         if (H.count == 0) continue;
@@ -640,7 +698,7 @@ static int upload_faces(mg_handle *h)
         }
         launch_coarsen_faces(a, h->stream);
     }
-    launch_coarse_setup(h->plan->cv, 1, h->stream);
+    launch_coarse_setup(h->setup_cv, 1, h->stream);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -738,12 +796,28 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
     h->dview = (LevelView *)(h->slab + lay.dview);
     h->dstart = (int *)(h->slab + lay.dstart);
     h->dcview = (CoarseView *)(h->slab + lay.dcview);
+    h->setup_cv = (CoarseView *)(h->slab + lay.setup_cv);
     GridState ds;
     memset(&ds, 0, sizeof(ds));
     ds.active = 1;
     CK(cudaMemcpy(h->dstate, &ds, sizeof(ds), cudaMemcpyHostToDevice));
     CK(cudaMemset(h->state, 0, sizeof(GridState)));
     CK(cudaMemset(h->err, 0, 16 * sizeof(int)));
+    {
+        // view of the coarsest level for building its inverse (mg_create / mg_set_faces)
+        const HLevel &Cl = h->lev[h->L - 1];
+        CoarseView v;
+        memset(&v, 0, sizeof(v));
+        for (int d = 0; d < 3; d++) {
+            v.n[d] = Cl.n[d];
+            v.w[d] = Cl.w64[d];
+        }
+        v.per = h->per;
+        v.nc = (int)Cl.N;
+        v.G = h->G;
+        v.err = h->err + 1;
+        CK(cudaMemcpy(h->setup_cv, &v, sizeof(v), cudaMemcpyHostToDevice));
+    }
     h->plan = new (std::nothrow) Plan();
     if (!h->plan) {
         mg_destroy(h);

@@ -77,6 +77,7 @@ struct mg_handle {
     gbmg::LevelView *dview = nullptr;    // view slot of the unit calls
     int *dstart = nullptr;
     gbmg::CoarseView *dcview = nullptr;
+    gbmg::CoarseView *setup_cv = nullptr;  // coarsest level, for building its inverse
     char *slab = nullptr;
     size_t bytes = 0;
     gbmg::Plan *plan = nullptr;          // single-grid launch plan
@@ -99,7 +100,11 @@ struct Plan {
     Table down[MG_MAX_LEVELS];  // prolongation (fine tiles of level l)
     Table rest[MG_MAX_LEVELS];  // restriction (coarse tiles of level l+1)
     Table half[MG_MAX_LEVELS];  // red-black half-sweeps of level l
-    CoarseView *cv = nullptr;
+    CoarseView *cv = nullptr;   // coarsest solves of the grids without a tail
+    int ncv = 0;
+    TailView *tv = nullptr;     // bottom-of-cycle blocks of the grids with a tail
+    int ntv = 0;
+    size_t tail_smem = 0;
     OuterView *ov = nullptr;
     OuterTable ot;
     GridState *st = nullptr;    // gathered copy of the grids' states (device)

@@ -83,6 +83,24 @@ struct CoarseView {
     int outer;           // 1 if this is also the finest level (x += e happens here)
 };
 
+// Bottom of the V-cycle in one block per grid (levels of at most kTailCells
+// cells, shared memory resident).
+constexpr int kTailCells = 4096;
+constexpr int kTailThreads = 1024;
+constexpr int kMaxTail = 8;
+
+struct TailView {
+    int nt;                  // tail levels: the first one down to the coarsest
+    int per;
+    int n[kMaxTail][3];
+    int off[kMaxTail];       // element offset of level t's x, b, wx, wy, wz (N each) in shared memory
+    void *w[kMaxTail][3];    // scaled faces of each tail level (V-cycle precision)
+    void *x0;                // first tail level: correction (out)
+    void *b0;                // first tail level: right-hand side (in)
+    const double *G;         // coarsest-level inverse
+    const GridState *st;
+};
+
 // Blocks of a launch over the cells of an n[0] x n[1] x n[2] level: a block is
 // 8 rows, each row split in segments of 64 cells along x.
 __host__ __device__ inline int fine_xtiles(int nx) { return (nx + kSeg - 1) / kSeg; }

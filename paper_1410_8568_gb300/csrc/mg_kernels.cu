@@ -564,6 +564,189 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
 }
 
 // ---------------------------------------------------------------------------
+// The bottom of the V-cycle in one launch: every level of a grid with at most
+// kTailCells cells (and the coarsest solve) is processed by one block of 1024
+// threads, all operands in shared memory, phases separated by block barriers.
+// These levels are too small to fill the GPU; as separate launches they cost
+// a launch latency each (10 per level per cycle) while doing almost no work.
+// The arithmetic is the same as the per-level kernels: red-black half-sweeps
+// (red first, zero initial correction), 8-child restriction of the residual,
+// trilinear prolongation, and the exact coarsest solve e = -G b in FP64.
+// ---------------------------------------------------------------------------
+
+// index of cell m of colour `colour` on an nx x ny x nz level (nx even)
+__device__ __forceinline__ int colour_cell(int m, int colour, int nx, int ny, int &i, int &j, int &k)
+{
+    const int hx = nx >> 1;
+    const int row = m / hx;
+    j = row % ny;
+    k = row / ny;
+    i = 2 * (m - row * hx) + ((colour + j + k) & 1);
+    return i + nx * row;
+}
+
+template <class T>
+__device__ __forceinline__ T smem_flux(const T *x, const T *wx, const T *wy, const T *wz, int nx,
+                                       int ny, int nz, int per, int i, int j, int k, int c, T xc,
+                                       T &diag)
+{
+    const int sy = nx, sz = nx * ny;
+    T a, d, f;
+    a = wx[c];
+    d = a;
+    f = a * (x[i > 0 ? c - 1 : ((per & 1) ? c + nx - 1 : c)] - xc);
+    if (i + 1 < nx) {
+        a = wx[c + 1];
+        d += a;
+        f += a * (x[c + 1] - xc);
+    } else if (per & 1) {
+        a = wx[c + 1 - nx];
+        d += a;
+        f += a * (x[c + 1 - nx] - xc);
+    }
+    a = wy[c];
+    d += a;
+    f += a * (x[j > 0 ? c - sy : ((per & 2) ? c + sy * (ny - 1) : c)] - xc);
+    if (j + 1 < ny) {
+        a = wy[c + sy];
+        d += a;
+        f += a * (x[c + sy] - xc);
+    } else if (per & 2) {
+        a = wy[c - sy * (ny - 1)];
+        d += a;
+        f += a * (x[c - sy * (ny - 1)] - xc);
+    }
+    a = wz[c];
+    d += a;
+    f += a * (x[k > 0 ? c - sz : ((per & 4) ? c + sz * (nz - 1) : c)] - xc);
+    if (k + 1 < nz) {
+        a = wz[c + sz];
+        d += a;
+        f += a * (x[c + sz] - xc);
+    } else if (per & 4) {
+        a = wz[c - sz * (nz - 1)];
+        d += a;
+        f += a * (x[c - sz * (nz - 1)] - xc);
+    }
+    diag = d;
+    return f;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restrict__ tv, T omega,
+                                                       int nu1, int nu2)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = (T *)smem_raw;
+    const TailView &V = tv[blockIdx.x];
+    if (!V.st->active) return;
+    const int nt = V.nt, per = V.per;
+    // stage the faces of every tail level and the right-hand side of the first
+    for (int t = 0; t < nt; t++) {
+        const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
+        T *base = sm + V.off[t];
+        for (int d = 0; d < 3; d++) {
+            const T *g = (const T *)V.w[t][d];
+            T *s = base + (2 + d) * N;
+            for (int c = threadIdx.x; c < N; c += blockDim.x) s[c] = g[c];
+        }
+    }
+    {
+        const int N = V.n[0][0] * V.n[0][1] * V.n[0][2];
+        const T *g = (const T *)V.b0;
+        T *s = sm + V.off[0] + N;
+        for (int c = threadIdx.x; c < N; c += blockDim.x) s[c] = g[c];
+    }
+    __syncthreads();
+
+    auto half = [&](int t, int colour) {
+        const int nx = V.n[t][0], ny = V.n[t][1], nz = V.n[t][2], N = nx * ny * nz;
+        T *x = sm + V.off[t];
+        const T *b = x + N, *wx = x + 2 * N, *wy = x + 3 * N, *wz = x + 4 * N;
+        for (int m = threadIdx.x; m < (N >> 1); m += blockDim.x) {
+            int i, j, k;
+            const int c = colour_cell(m, colour, nx, ny, i, j, k);
+            const T xc = x[c];
+            T d;
+            const T f = smem_flux(x, wx, wy, wz, nx, ny, nz, per, i, j, k, c, xc, d);
+            x[c] = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
+        }
+        __syncthreads();
+    };
+
+    for (int t = 0; t + 1 < nt; t++) {
+        for (int it = 0; it < nu1; it++) {
+            if (it == 0) {
+                // zero initial correction: no cell of the level may be read before it is set
+                const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
+                T *x = sm + V.off[t];
+                for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = T(0);
+                __syncthreads();
+            }
+            half(t, 0);
+            half(t, 1);
+        }
+        // restriction of the residual to level t + 1
+        const int nx = V.n[t][0], ny = V.n[t][1], nz = V.n[t][2], N = nx * ny * nz;
+        const int ncx = V.n[t + 1][0], ncy = V.n[t + 1][1], NC = ncx * ncy * V.n[t + 1][2];
+        const T *x = sm + V.off[t];
+        const T *b = x + N, *wx = x + 2 * N, *wy = x + 3 * N, *wz = x + 4 * N;
+        T *bc = sm + V.off[t + 1] + NC;
+        for (int C = threadIdx.x; C < NC; C += blockDim.x) {
+            const int I = C % ncx, J = (C / ncx) % ncy, K = C / (ncx * ncy);
+            T s = T(0);
+            for (int dz = 0; dz < 2; dz++)
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++) {
+                        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+                        const int c = i + nx * (j + ny * k);
+                        T d;
+                        s += b[c] - smem_flux(x, wx, wy, wz, nx, ny, nz, per, i, j, k, c, x[c], d);
+                    }
+            bc[C] = s * T(0.125);
+        }
+        __syncthreads();
+    }
+    {
+        // exact solve on the coarsest level: e = -G b, FP64, one warp per row
+        const int t = nt - 1;
+        const int n = V.n[t][0] * V.n[t][1] * V.n[t][2];
+        T *x = sm + V.off[t];
+        const T *b = x + n;
+        const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+        for (int r = threadIdx.x >> 5; r < n; r += warps) {
+            const double *Gr = V.G + (long long)r * n;
+            double s = 0.0;
+            for (int u = lane; u < n; u += 32) s += Gr[u] * (double)b[u];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) x[r] = (T)(-s);
+        }
+        __syncthreads();
+    }
+    for (int t = nt - 2; t >= 0; t--) {
+        const int nx = V.n[t][0], ny = V.n[t][1], N = nx * ny * V.n[t][2];
+        const int nc[3] = {V.n[t + 1][0], V.n[t + 1][1], V.n[t + 1][2]};
+        T *x = sm + V.off[t];
+        const T *ec = sm + V.off[t + 1];
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+            x[c] += prolong_at(ec, nc, per, i, j, k);
+        }
+        __syncthreads();
+        for (int it = 0; it < nu2; it++) {
+            half(t, 0);
+            half(t, 1);
+        }
+    }
+    {
+        const int N = V.n[0][0] * V.n[0][1] * V.n[0][2];
+        T *g = (T *)V.x0;
+        const T *s = sm + V.off[0];
+        for (int c = threadIdx.x; c < N; c += blockDim.x) g[c] = s[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // y = A x on one level (unit checks): x in x, y in b
 // ---------------------------------------------------------------------------
 
@@ -719,13 +902,12 @@ __global__ void __launch_bounds__(1024) k_coarse_setup(const CoarseView *__restr
 
 __global__ void __launch_bounds__(kThreads) k_faces_from_density(FaceArgs a)
 {
-    const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % a.n[0]);
-        const long long rest = c / a.n[0];
-        const int j = (int)(rest % a.n[1]);
-        const int k = (int)(rest / a.n[1]);
+    const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int i = c % a.n[0];
+        const int rest = c / a.n[0];
+        const int j = rest % a.n[1];
+        const int k = rest / a.n[1];
         const int q[3] = {i, j, k};
         const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
         const double rho_c = a.rho[c];
@@ -750,13 +932,12 @@ __global__ void __launch_bounds__(kThreads) k_faces_from_density(FaceArgs a)
 
 __global__ void __launch_bounds__(kThreads) k_scale_faces(FaceArgs a)
 {
-    const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % a.n[0]);
-        const long long rest = c / a.n[0];
-        const int j = (int)(rest % a.n[1]);
-        const int k = (int)(rest / a.n[1]);
+    const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int i = c % a.n[0];
+        const int rest = c / a.n[0];
+        const int j = rest % a.n[1];
+        const int k = rest / a.n[1];
         const int q[3] = {i, j, k};
         for (int d = 0; d < 3; d++) {
             double v = 0.0;
@@ -775,14 +956,13 @@ __global__ void __launch_bounds__(kThreads) k_scale_faces(FaceArgs a)
 // alpha_c = mean of the 4 fine alpha, and 1/(2h)^2 = (1/4)(1/h^2).
 __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
 {
-    const long long NC = (long long)a.nc[0] * a.nc[1] * a.nc[2];
+    const int NC = a.nc[0] * a.nc[1] * a.nc[2];
     const int nx = a.nf[0], ny = a.nf[1];
-    for (long long C = blockIdx.x * (long long)blockDim.x + threadIdx.x; C < NC;
-         C += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(C % a.nc[0]);
-        const long long rest = C / a.nc[0];
-        const int J = (int)(rest % a.nc[1]);
-        const int K = (int)(rest / a.nc[1]);
+    for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < NC; C += gridDim.x * blockDim.x) {
+        const int I = C % a.nc[0];
+        const int rest = C / a.nc[0];
+        const int J = rest % a.nc[1];
+        const int K = rest / a.nc[1];
         const int base[3] = {2 * I, 2 * J, 2 * K};
         for (int d = 0; d < 3; d++) {
             const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
@@ -1043,6 +1223,16 @@ void launch_prolong(const Table &tb, const OuterView *ov, int outer_update, cuda
     k_prolong<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
 }
 template <class T>
+void launch_tail(const TailView *tv, int count, size_t smem, double omega, int nu1, int nu2, cudaStream_t s)
+{
+    static size_t attr = 0;  // opt in to more than 48 KB of shared memory when needed
+    if (smem > attr) {
+        cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    k_tail<T><<<count, kTailThreads, smem, s>>>(tv, (T)omega, nu1, nu2);
+}
+template <class T>
 void launch_apply(const Table &tb, cudaStream_t s)
 {
     k_apply<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
@@ -1099,6 +1289,8 @@ template void launch_restrict<float>(const Table &, cudaStream_t);
 template void launch_restrict<double>(const Table &, cudaStream_t);
 template void launch_prolong<float>(const Table &, const OuterView *, int, cudaStream_t);
 template void launch_prolong<double>(const Table &, const OuterView *, int, cudaStream_t);
+template void launch_tail<float>(const TailView *, int, size_t, double, int, int, cudaStream_t);
+template void launch_tail<double>(const TailView *, int, size_t, double, int, int, cudaStream_t);
 template void launch_apply<float>(const Table &, cudaStream_t);
 template void launch_apply<double>(const Table &, cudaStream_t);
 template void launch_coarse_solve<float>(const CoarseView *, int, const OuterView *, cudaStream_t);

@@ -52,6 +52,8 @@ template <class T> void launch_half(const Table &, int colour, double omega, int
                                     const OuterView *ov, cudaStream_t);
 template <class T> void launch_restrict(const Table &, cudaStream_t);
 template <class T> void launch_prolong(const Table &, const OuterView *ov, int outer_update, cudaStream_t);
+template <class T> void launch_tail(const TailView *, int count, size_t smem, double omega, int nu1,
+                                    int nu2, cudaStream_t);
 template <class T> void launch_apply(const Table &, cudaStream_t);
 template <class T> void launch_coarse_solve(const CoarseView *, int count, const OuterView *ov, cudaStream_t);
 void launch_coarse_setup(const CoarseView *, int count, cudaStream_t);

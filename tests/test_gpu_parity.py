@@ -173,7 +173,7 @@ def test_restrict_residual_and_prolong_match_oracle(bc):
 
 
 @pytest.mark.parametrize("shape,bc", [((32, 32, 32), (0, 0, 0)), ((48, 48, 48), (1, 1, 0)), ((64, 48, 32), (1, 1, 1)),
-                                      ((4, 4, 4), (0, 1, 0)), ((6, 6, 6), (1, 1, 1))])
+                                      ((4, 4, 4), (0, 1, 0)), ((6, 6, 6), (1, 1, 1)), ((40, 40, 40), (0, 0, 0))])
 def test_coarse_solve_matches_oracle(shape, bc):
     P = random_problem(shape, bc, 1000.0, 8)
     f = oracle.faces_from_density(shape, bc, P.rho)
@@ -201,6 +201,7 @@ CASES = [
     ("periodic_32_ratio10", lambda: random_problem((32, 32, 32), (1, 1, 1), 10.0, 11)),
     ("sphere_24_ratio1e5", lambda: random_problem((24, 24, 24), (0, 0, 0), 1e5, 12)),
     ("tiny_4", lambda: random_problem((4, 4, 4), (0, 0, 0), 1000.0, 13)),
+    ("single_level_8x8x2", lambda: random_problem((8, 8, 2), (0, 0, 0), 1000.0, 17)),
     ("odd_coarsest_6_periodic", lambda: random_problem((6, 6, 6), (1, 1, 1), 100.0, 14)),
     ("two_cells_periodic", lambda: random_problem((2, 4, 2), (1, 1, 1), 1.0, 15)),
 ]
@@ -315,7 +316,7 @@ def test_edge_cases():
         solver_for(P, bad)
     assert e.value.code == gbmg.EINVAL
     with pytest.raises(gbmg.MGError):
-        gbmg.Solver((4, 4, 64), (0, 0, 0), faces=[torch.ones(4 * 4 * 64, dtype=torch.float64, device="cuda")] * 3)
+        gbmg.Solver((2, 2, 256), (0, 0, 0), faces=[torch.ones(2 * 2 * 256, dtype=torch.float64, device="cuda")] * 3)
 
 
 def test_host_entry_points_match_device_path():

@@ -33,8 +33,8 @@ def faces_for(shape, bc, seed):
 
 # grids that are their own coarsest level (no axis can be halved), so a
 # handle's mg_coarse_solve acts on the same operator
-@pytest.mark.parametrize("shape,bc", [((8, 8, 4), (1, 1, 0)), ((4, 4, 4), (0, 0, 0)), ((6, 3, 5), (1, 0, 1)),
-                                      ((8, 4, 8), (0, 1, 0))])
+@pytest.mark.parametrize("shape,bc", [((8, 8, 2), (1, 1, 0)), ((4, 3, 4), (0, 0, 0)), ((6, 3, 5), (1, 0, 1)),
+                                      ((16, 2, 8), (0, 1, 0))])
 def test_static_solve_matches_handle_twice(shape, bc):
     faces = faces_for(shape, bc, sum(shape))
     with gbmg.Solver(shape, bc, faces=faces, precision=gbmg.FP64) as S:
