@@ -1,7 +1,7 @@
 """Benchmark of the GB300 pressure multigrid (arXiv 1410.8568, Sec. 2.3).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload drop_film_128|drop_film_256|drop_film_512|sphere_32]
+                    [--workload drop_film_128|drop_film_256|drop_film_512|sphere_32|batch64|serve_stream]
 
 Metric: Poisson multigrid solves per second to a relative residual of 1e-10,
 mixed precision (FP32 V(2,2) cycles inside FP64 iterative refinement) next to
@@ -56,6 +56,12 @@ WORKLOADS = {
                           desc="drop_film_512^3_1000to1: film + drop + 0-4 droplets, periodic x,y, Neumann z, Fourier-divergence RHS"),
     "sphere_32": dict(kind="config1", n=32,
                       desc="sphere_32^3_1000to1: R 0.2 centred, Neumann walls, N(0,1) RHS"),
+    "batch64": dict(kind="batch", n=0,
+                    desc="batch of 64 grids, n in {32,48,64,96,128}^3, seeded spheres R 0.05-0.2, ratio {10,100,1000}, "
+                         "Neumann walls, N(0,1) RHS; one batched graph launch per solve of all 64"),
+    "serve_stream": dict(kind="serve", n=0,
+                         desc="served stream: Poisson arrivals, n log-uniform in [64,512] rounded to "
+                              "{64,96,128,192,256,384,512}, drop/film fields, ratio 10-1000, continuous batching"),
 }
 
 
@@ -218,6 +224,184 @@ def run_reference(args, name):
     print(json.dumps(line))
 
 
+def _line(args, world, name, value, ms, p50, p99, extra):
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[name]["desc"], "tol": TOL,
+                       "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "p50_ms": p50, "p99_ms": p99}
+    line.update(extra)
+    return line
+
+
+def run_batch(args, rank, world, local_rank, dist):
+    """64 independent grids of uneven sizes solved by one batched graph launch."""
+    import torch
+
+    import oracle
+    from paper_1410_8568_gb300 import gbmg
+    from paper_1410_8568_gb300 import inputs as I
+
+    probs = I.config4_batch(64)
+    rho = [torch.from_numpy(P.rho).cuda() for P in probs]
+    rhs = [torch.from_numpy(P.rhs).cuda() for P in probs]
+    ps = [torch.zeros_like(r) for r in rhs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    cells = sum(P.cells for P in probs)
+    res = {}
+    for prec in (gbmg.MIXED, gbmg.FP64):
+        with torch.cuda.stream(stream):
+            solvers = [gbmg.Solver(P.shape, P.bc, rho=r, precision=prec, stream=stream) for P, r in zip(probs, rho)]
+            B = gbmg.Batch(solvers)
+
+        def step():
+            for S, r, p in zip(solvers, rho, ps):
+                S.set_density(r)
+                p.zero_()
+            return B.solve(rhs, ps, tol=TOL)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+            times = []
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            if dist is not None:
+                dist.barrier()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                sts = step()
+                ev[k][1].record(stream)
+            stream.synchronize()
+        times = [a.elapsed_time(b) for a, b in ev]
+        bad = [st.status for st in sts if st.status != gbmg.OK]
+        if bad:
+            raise RuntimeError("batch solve failed: %s" % bad)
+        tot = sum(times)
+        if dist is not None:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = t.item()
+        errs = []
+        if rank == 0:
+            # error against the oracle's p* on the 4 smallest grids of the batch
+            for g in sorted(range(len(probs)), key=lambda g: probs[g].cells)[:4]:
+                P = probs[g]
+                f = oracle.faces_from_density(P.shape, P.bc, P.rho)
+                pstar = oracle.solve_exact(P.shape, P.bc, f, P.rhs).x
+                x = ps[g].cpu().numpy()
+                errs.append(float(np.linalg.norm(x - pstar) / np.linalg.norm(pstar)))
+        res[prec] = dict(ms=tot / args.steps, value=world * 64 * args.steps / (tot / 1000.0),
+                         p50=statistics.median(times), p99=float(np.percentile(times, 99)),
+                         iters=[st.iters for st in sts], err=max(errs) if errs else None)
+        B.close()
+        for S in solvers:
+            S.close()
+    if rank == 0:
+        m, f = res[gbmg.MIXED], res[gbmg.FP64]
+        line = _line(args, world, args.workload, m["value"], m["ms"], m["p50"], m["p99"], {
+            "batch": {"grids": 64, "cells": cells, "cycles_min": min(m["iters"]), "cycles_max": max(m["iters"]),
+                      "step": "set density of every grid + one batched solve (cold start) of all 64"},
+            "err_vs_oracle_max_4_smallest": m["err"],
+            "fp64": {"value": f["value"], "unit": "solves/s", "ms_per_step": f["ms"], "p50_ms": f["p50"],
+                     "p99_ms": f["p99"], "err_vs_oracle_max_4_smallest": f["err"]},
+            "mixed_over_fp64": m["value"] / f["value"],
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None})
+        print(json.dumps(line))
+
+
+def run_serve(args, rank, world, local_rank, dist):
+    """Poisson-arrival request stream through the continuous-batching server."""
+    import torch
+
+    from paper_1410_8568_gb300 import gbmg
+    from paper_1410_8568_gb300 import inputs as I
+
+    stream_spec = I.config5_stream(count=args.requests, rate=1.0)
+    # one field per (edge, ratio bucket); the stream's ratios are log-uniform in
+    # [10, 1000] and are mapped to the nearest of 10, 100, 1000
+    buckets = (10.0, 100.0, 1000.0)
+    fields, rhs_of = {}, {}
+    for _, n, ratio, seed in stream_spec:
+        rb = min(buckets, key=lambda b: abs(math.log(b) - math.log(ratio)))
+        if (n, rb) in fields:
+            continue
+        shape = (n, n, n)
+        if n not in rhs_of:
+            rng = np.random.default_rng(I.config_seed(5, n))
+            rhs_of[n] = torch.from_numpy(I.rhs_fourier_divergence(shape, I.DROP_FILM_BC, rng)).cuda()
+        rho = torch.from_numpy(I.density_field(shape, 0.1, [((0.5, 0.5, 0.3), 0.125)], rb)).cuda()
+        faces = [torch.empty_like(rho) for _ in range(3)]
+        gbmg.faces_from_density(shape, I.DROP_FILM_BC, rho, *faces)
+        fields[(n, rb)] = (shape, I.DROP_FILM_BC, faces, rhs_of[n])
+        del rho
+    torch.cuda.synchronize()
+    res = {}
+    for prec in (gbmg.MIXED, gbmg.FP64):
+        # service time of each edge alone: sets the arrival rate (0.8 x capacity of the mixed path)
+        if prec == gbmg.MIXED:
+            svc = {}
+            for (n, rb), (shape, bc, faces, rhs) in fields.items():
+                if n in svc:
+                    continue
+                with gbmg.Solver(shape, bc, faces=faces, precision=prec) as S:
+                    p = torch.zeros_like(rhs)
+                    S.solve(rhs, p)
+                    t = time.perf_counter()
+                    S.solve(rhs, p.zero_())
+                    svc[n] = time.perf_counter() - t
+            mean_svc = sum(svc[n] for _, n, _, _ in stream_spec) / len(stream_spec)
+            rate = 0.8 / mean_svc
+        srv = gbmg.Server(hbm_budget_bytes=args.hbm_budget << 30, max_slots=args.slots, precision=prec)
+        outs, tickets, lat = [], [], []
+        t0 = time.perf_counter()
+        arrivals = [a / rate for a, _, _, _ in stream_spec]
+        pending = {}
+        k = 0
+        done = 0
+        while done < len(stream_spec):
+            now = time.perf_counter() - t0
+            while k < len(stream_spec) and arrivals[k] <= now:
+                _, n, ratio, seed = stream_spec[k]
+                rb = min(buckets, key=lambda b: abs(math.log(b) - math.log(ratio)))
+                shape, bc, faces, rhs = fields[(n, rb)]
+                p = torch.zeros_like(rhs)
+                torch.cuda.synchronize()
+                pending[srv.submit(shape, bc, faces, rhs, p, tol=TOL)] = (p, n)
+                k += 1
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    rc, st = r
+                    if rc != gbmg.OK:
+                        raise RuntimeError("served solve failed: %s" % gbmg.strerror(rc))
+                    lat.append(st.ms)
+                    pending.pop(t)
+                    done += 1
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        info = srv.info()
+        srv.close()
+        res[prec] = dict(value=len(stream_spec) / wall, p50=statistics.median(lat),
+                         p99=float(np.percentile(lat, 99)), wall=wall, info=info)
+    if rank == 0:
+        m, f = res[gbmg.MIXED], res[gbmg.FP64]
+        line = _line(args, world, args.workload, m["value"], 1000.0 * m["wall"] / len(stream_spec), m["p50"], m["p99"], {
+            "serve": {"requests": len(stream_spec), "arrival_rate_per_s": rate,
+                      "rate_rule": "0.8 x capacity of the mixed path (mean solo service time of the stream's sizes)",
+                      "slots": args.slots, "hbm_budget_gib": args.hbm_budget,
+                      "peak_bytes": m["info"]["peak_bytes"], "max_in_flight": m["info"]["max_in_flight"],
+                      "latency": "submission to completion, ms"},
+            "fp64": {"value": f["value"], "unit": "solves/s", "p50_ms": f["p50"], "p99_ms": f["p99"],
+                     "max_in_flight": f["info"]["max_in_flight"]},
+            "mixed_over_fp64": m["value"] / f["value"],
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None})
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,6 +410,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="drop_film_128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=200, help="serve_stream: requests in the stream")
+    ap.add_argument("--slots", type=int, default=8, help="serve_stream: most requests on the GPU at once")
+    ap.add_argument("--hbm-budget", type=int, default=64, help="serve_stream: GiB of device memory for hierarchies")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -250,6 +437,11 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
+
+    if WORKLOADS[args.workload]["kind"] == "batch":
+        return run_batch(args, rank, world, local_rank, dist)
+    if WORKLOADS[args.workload]["kind"] == "serve":
+        return run_serve(args, rank, world, local_rank, dist)
 
     P = make_problem(args.workload)
     N = P.cells
