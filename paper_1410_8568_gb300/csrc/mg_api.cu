@@ -154,15 +154,64 @@ void Plan::release()
     mem = nullptr;
     if (ov_h) cudaFreeHost(ov_h);
     if (st_h) cudaFreeHost(st_h);
+    if (stage_h) cudaFreeHost(stage_h);
     ov_h = nullptr;
     st_h = nullptr;
+    stage_h = nullptr;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    e0 = e1 = nullptr;
+    if (staged) cudaEventDestroy(staged);
+    e0 = e1 = staged = nullptr;
+}
+
+// Device memory for the tables of up to `cap` grids (worst case of every
+// table), a pinned host copy of the same layout, and the per-solve mirrors.
+// Allocated once; fill() rewrites the tables without allocating.
+int Plan::alloc(int cap)
+{
+    capacity = cap;
+    const int LV = cap * (MG_MAX_LEVELS - 1);
+    const int ST = 3 * (cap + 1) * (MG_MAX_LEVELS - 1) + (cap + 1);
+    Carve c;
+    o_lv = c.take((size_t)LV * sizeof(LevelView));
+    o_starts = c.take((size_t)ST * sizeof(int));
+    o_cv = c.take((size_t)cap * sizeof(CoarseView));
+    o_tv = c.take((size_t)cap * sizeof(TailView));
+    tables_bytes = c.off;
+    const size_t o_ov = c.take((size_t)cap * sizeof(OuterView));
+    const size_t o_gs = c.take((size_t)cap * sizeof(GridState));
+    CK(cudaMalloc((void **)&mem, c.off));
+    CK(cudaMallocHost((void **)&stage_h, tables_bytes));
+    cv = (CoarseView *)(mem + o_cv);
+    tv = (TailView *)(mem + o_tv);
+    ov = (OuterView *)(mem + o_ov);
+    st = (GridState *)(mem + o_gs);
+    CK(cudaMallocHost((void **)&ov_h, (size_t)cap * sizeof(OuterView)));
+    CK(cudaMallocHost((void **)&st_h, (size_t)cap * sizeof(GridState)));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventCreateWithFlags(&staged, cudaEventDisableTiming));
+    return MG_OK;
 }
 
 int Plan::build(mg_handle *const *handles, int count)
 {
+    int rc = alloc(count);
+    if (rc) return rc;
+    stream = handles[0]->stream;
+    rc = fill(handles, count);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(stream));
+    return MG_OK;
+}
+
+// (Re)write the launch tables for `handles` (count <= capacity) into the
+// plan's memory: host tables in the pinned staging copy, one asynchronous
+// copy on the plan's stream.  No allocation, no device synchronisation.
+int Plan::fill(mg_handle *const *handles, int count)
+{
+    if (count < 1 || count > capacity) return MG_EINVAL;
+    CK(cudaEventSynchronize(staged));  // the previous copy out of the staging buffer is done
     hs.assign(handles, handles + count);
     G = count;
     mixed = hs[0]->mixed;
@@ -185,19 +234,28 @@ int Plan::build(mg_handle *const *handles, int count)
                 break;
             }
     }
-    // host copies of the tables
-    std::vector<LevelView> lv;
-    std::vector<int> starts;
-    struct Range { int lv0, count, sf, sc, sh, bf, bc, bh; };
-    std::vector<Range> ranges(Lmax);
+    LevelView *lv = (LevelView *)(stage_h + o_lv);
+    int *starts = (int *)(stage_h + o_starts);
+    CoarseView *cvh = (CoarseView *)(stage_h + o_cv);
+    TailView *tvh = (TailView *)(stage_h + o_tv);
+    LevelView *d_lv = (LevelView *)(mem + o_lv);
+    int *d_starts = (int *)(mem + o_starts);
+    int nlv = 0, nst = 0;
+    for (int l = 0; l < MG_MAX_LEVELS; l++) {
+        down[l] = Table{d_lv, d_starts, 0, 0};
+        rest[l] = down[l];
+        half[l] = down[l];
+    }
     for (int l = 0; l + 1 < Lmax; l++) {
-        Range r{(int)lv.size(), 0, 0, 0, 0, 0, 0, 0};
+        const int lv0 = nlv;
+        int sf0 = nst, sc0, sh0, cnt = 0;
+        // three prefix arrays, each count + 1 long, laid out one after the other
         std::vector<int> sf{0}, sc{0}, sh{0};
         for (int g = 0; g < G; g++) {
             mg_handle *h = hs[g];
             if (l + 1 >= h->L || l >= lt[g]) continue;
             const HLevel &F = h->lev[l], &C = h->lev[l + 1];
-            LevelView v;
+            LevelView &v = lv[nlv++];
             memset(&v, 0, sizeof(v));
             for (int d = 0; d < 3; d++) {
                 v.n[d] = F.n[d];
@@ -211,62 +269,35 @@ int Plan::build(mg_handle *const *handles, int count)
             v.bc = C.b;
             v.g = g;
             v.st = h->state;
-            lv.push_back(v);
             sf.push_back(sf.back() + prolong_blocks(F.n));
             sc.push_back(sc.back() + restrict_blocks(F.n, C.n));
             sh.push_back(sh.back() + half_sweep_blocks(F.n));
-            r.count++;
+            cnt++;
         }
-        r.sf = (int)starts.size();
-        starts.insert(starts.end(), sf.begin(), sf.end());
-        r.sc = (int)starts.size();
-        starts.insert(starts.end(), sc.begin(), sc.end());
-        r.sh = (int)starts.size();
-        starts.insert(starts.end(), sh.begin(), sh.end());
-        r.bf = sf.back();
-        r.bc = sc.back();
-        r.bh = sh.back();
-        ranges[l] = r;
+        for (int v : sf) starts[nst++] = v;
+        sc0 = nst;
+        for (int v : sc) starts[nst++] = v;
+        sh0 = nst;
+        for (int v : sh) starts[nst++] = v;
+        down[l] = Table{d_lv + lv0, d_starts + sf0, cnt, sf.back()};
+        rest[l] = Table{d_lv + lv0, d_starts + sc0, cnt, sc.back()};
+        half[l] = Table{d_lv + lv0, d_starts + sh0, cnt, sh.back()};
     }
-    std::vector<int> so{0};
-    for (int g = 0; g < G; g++) so.push_back(so.back() + hs[g]->nblk0);
-    const int so_off = (int)starts.size();
-    starts.insert(starts.end(), so.begin(), so.end());
-
-    Carve c;
-    const size_t o_lv = c.take(std::max<size_t>(1, lv.size()) * sizeof(LevelView));
-    const size_t o_st = c.take(starts.size() * sizeof(int));
-    const size_t o_cv = c.take(G * sizeof(CoarseView));
-    const size_t o_tv = c.take(G * sizeof(TailView));
-    const size_t o_ov = c.take(G * sizeof(OuterView));
-    const size_t o_gs = c.take(G * sizeof(GridState));
-    CK(cudaMalloc((void **)&mem, c.off));
-    LevelView *d_lv = (LevelView *)(mem + o_lv);
-    int *d_starts = (int *)(mem + o_st);
-    cv = (CoarseView *)(mem + o_cv);
-    tv = (TailView *)(mem + o_tv);
-    ov = (OuterView *)(mem + o_ov);
-    st = (GridState *)(mem + o_gs);
-    for (int l = 0; l < MG_MAX_LEVELS; l++) {
-        down[l] = Table{d_lv, d_starts, 0, 0};
-        rest[l] = down[l];
-        half[l] = down[l];
+    const int so0 = nst;
+    starts[nst++] = 0;
+    for (int g = 0; g < G; g++) {
+        starts[nst] = starts[nst - 1] + hs[g]->nblk0;
+        nst++;
     }
-    for (int l = 0; l + 1 < Lmax; l++) {
-        const Range &r = ranges[l];
-        down[l] = Table{d_lv + r.lv0, d_starts + r.sf, r.count, r.bf};
-        rest[l] = Table{d_lv + r.lv0, d_starts + r.sc, r.count, r.bc};
-        half[l] = Table{d_lv + r.lv0, d_starts + r.sh, r.count, r.bh};
-    }
-    ot = OuterTable{ov, d_starts + so_off, G, so.back()};
-    std::vector<CoarseView> cvh;
-    std::vector<TailView> tvh;
+    ot = OuterTable{ov, d_starts + so0, G, starts[nst - 1]};
     const size_t esz = mixed ? sizeof(float) : sizeof(double);
     tail_smem = 0;
+    ntv = 0;
+    ncv = 0;
     for (int g = 0; g < G; g++) {
         mg_handle *h = hs[g];
         if (lt[g] >= h->L) continue;
-        TailView v;
+        TailView &v = tvh[ntv++];
         memset(&v, 0, sizeof(v));
         v.nt = h->L - lt[g];
         v.per = h->per;
@@ -285,15 +316,13 @@ int Plan::build(mg_handle *const *handles, int count)
         v.b0 = h->lev[lt[g]].b;
         v.G = h->G;
         v.st = h->state;
-        tvh.push_back(v);
         tail_smem = std::max(tail_smem, (size_t)off * esz);
     }
     for (int g = 0; g < G; g++) {
         mg_handle *h = hs[g];
         if (lt[g] < h->L) continue;
         const HLevel &Cl = h->lev[h->L - 1];
-        cvh.emplace_back();
-        CoarseView &v = cvh.back();
+        CoarseView &v = cvh[ncv++];
         memset(&v, 0, sizeof(v));
         for (int d = 0; d < 3; d++) {
             v.n[d] = Cl.n[d];
@@ -309,8 +338,6 @@ int Plan::build(mg_handle *const *handles, int count)
         v.g = g;
         v.outer = h->L == 1 ? 1 : 0;
     }
-    CK(cudaMallocHost((void **)&ov_h, G * sizeof(OuterView)));
-    CK(cudaMallocHost((void **)&st_h, G * sizeof(GridState)));
     for (int g = 0; g < G; g++) {
         mg_handle *h = hs[g];
         OuterView &v = ov_h[g];
@@ -329,15 +356,8 @@ int Plan::build(mg_handle *const *handles, int count)
         v.max_iters = h->prm.max_iters;
         v.inner = prm.inner_cycles;
     }
-    if (!lv.empty()) CK(cudaMemcpy(d_lv, lv.data(), lv.size() * sizeof(LevelView), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_starts, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice));
-    ncv = (int)cvh.size();
-    ntv = (int)tvh.size();
-    if (ncv) CK(cudaMemcpy(cv, cvh.data(), ncv * sizeof(CoarseView), cudaMemcpyHostToDevice));
-    if (ntv) CK(cudaMemcpy(tv, tvh.data(), ntv * sizeof(TailView), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ov, ov_h, G * sizeof(OuterView), cudaMemcpyHostToDevice));
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    CK(cudaMemcpyAsync(mem, stage_h, tables_bytes, cudaMemcpyHostToDevice, stream));
+    CK(cudaEventRecord(staged, stream));
     return MG_OK;
 }
 

@@ -111,9 +111,15 @@ struct Plan {
     OuterView *ov_h = nullptr;  // pinned host mirror of ov
     GridState *st_h = nullptr;  // pinned host mirror of st
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t staged = nullptr;  // the last table copy out of stage_h has run
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int build(mg_handle *const *handles, int count);
+    int capacity = 0;              // most grids the tables can hold
+    char *stage_h = nullptr;       // pinned host copy of the table region of mem
+    size_t tables_bytes = 0, o_lv = 0, o_starts = 0, o_cv = 0, o_tv = 0;
+    int alloc(int cap);                                  // allocate once for up to cap grids
+    int fill(mg_handle *const *handles, int count);      // rewrite the tables (async, no allocation)
+    int build(mg_handle *const *handles, int count);     // alloc(count) + fill + wait
     void release();
 };
 

@@ -8,6 +8,8 @@
 // the launch, so a request's result is bitwise the same alone and in the mix.
 #include <string.h>
 
+#include <new>
+
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -190,11 +192,16 @@ void mg_server::loop()
             if (!rc) rc = plan_prologue(sp);
         }
         if (changed) {
-            drop_plan();
+            // the plan is allocated once for max_slots grids; a change of the
+            // running set only rewrites its tables (asynchronously, no allocation)
+            if (!plan) {
+                plan = new (std::nothrow) Plan();
+                if (!plan) rc = MG_ENOMEM;
+                else if (!rc) rc = plan->alloc(max_slots);
+            }
             std::vector<mg_handle *> hs;
             for (Request *r : running) hs.push_back(r->h);
-            plan = new Plan();
-            if (!rc) rc = plan->build(hs.data(), (int)hs.size());
+            if (!rc) rc = plan->fill(hs.data(), (int)hs.size());
             for (size_t g = 0; g < running.size() && !rc; g++)
                 plan_bind(*plan, (int)g, running[g]->rhs, running[g]->p, running[g]->tol, prm.max_iters);
             if (!rc) rc = plan_upload(*plan);
