@@ -86,7 +86,7 @@ def read_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mg_kernels.cu", "mg_device.cuh"):
+    for f in ("mg_kernels.cu", "mg_tiles.cu", "mg_stencil.cuh", "mg_device.cuh"):
         with open(os.path.join(ROOT, "paper_1410_8568_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -530,6 +530,7 @@ def main():
         e2e_tot = t.item()
 
     # roofline of the dominant kernel: finest-level half-sweep, per-launch events
+    v0 = S.tile_choice(gbmg.TILE_HALF, 0)
     S.profile(True)
     prof_steps = max(3, min(args.steps, 10))
     timed(S, prof_steps)
@@ -586,7 +587,8 @@ def main():
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_half<float> level 0 (one red or black half-sweep)",
+                         "kernel": "FP32 half-sweep of level 0 (one red or black colour), launch shape %d "
+                                   "(%d threads x %d quads)" % ((v0,) + gbmg.tile_shape(v0)),
                          "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
                          "launches_timed": n_l, "peak_source": peak_kind,
                          "residual_fp64_avg_launch_us": 1000.0 * ms_r / max(1, n_r)},

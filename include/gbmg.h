@@ -88,6 +88,13 @@ extern "C" {
 #define MG_STATIC_MAX_CELLS 512 /* most cells of a grid solved by mg_coarse_solve_static */
 #define MG_MAX_LEVELS 16
 
+#define MG_TILES_AUTO (-1)   /* mg_params.tiles: time every launch shape per level, keep the fastest */
+#define MG_TILES_ROWS 0      /* one grid row per warp, 8 rows per block (no tuning) */
+#define MG_TILE_VARIANTS 7   /* launch shapes 0 .. 6 (see mg_tile_shape) */
+#define MG_TILE_HALF 0       /* kernels with a tunable launch shape: red-black half-sweep, */
+#define MG_TILE_RESTRICT 1   /* residual + restriction, */
+#define MG_TILE_PROLONG 2    /* prolongation + correction */
+
 typedef struct {
     int nx, ny, nz;     /* cells per axis */
     double lx, ly, lz;  /* domain lengths (h_d = l_d / n_d) */
@@ -101,6 +108,9 @@ typedef struct {
     int precision;     /* MG_PREC_FP64 or MG_PREC_MIXED */
     int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
     int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1 */
+    int tiles;         /* launch shapes of the V-cycle kernels: MG_TILES_AUTO (autotuned per
+                          level), MG_TILES_ROWS, or a variant 1 .. MG_TILE_VARIANTS - 1 for
+                          every level whose rows are a multiple of 4 cells */
 } mg_params;
 
 typedef struct {
@@ -311,6 +321,32 @@ int mg_coarse_solve_static(const mg_grid *grid, const double *ax, const double *
 
 int mg_profile_enable(mg_handle *h, int enable);
 int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double *total_ms);
+
+/* ---------------------------------------------------------------------------
+ * Launch shapes of the V-cycle kernels (no counterpart in the paper, whose
+ * solver is an MPI Fortran code; this is the GPU's tiling of Sec. 2.3's
+ * relaxation, restriction and prolongation).  With mg_params.tiles =
+ * MG_TILES_AUTO, mg_create times every shape that fits each level (half-sweep,
+ * restriction, prolongation) on the handle's own work arrays and keeps the
+ * fastest; choices are cached per process by kernel, precision, periodic axes
+ * and level size.  A shape never changes a result, only its speed.  In a
+ * batch, a table of grids takes the shape of its largest grid on that level
+ * (the row shape if some grid's rows are not a multiple of 4 cells).
+ * --------------------------------------------------------------------------- */
+
+/* Shape chosen for kernel `kind` (MG_TILE_HALF, MG_TILE_RESTRICT,
+ * MG_TILE_PROLONG) on `level` of h: 0 .. MG_TILE_VARIANTS - 1 (0 on the
+ * coarsest level and on levels run by the bottom-of-cycle kernel). */
+int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant);
+
+/* Threads per block and items (4-cell quads; restriction: coarse cell pairs)
+ * per thread of shape `variant`; variant 0 is the row tiling (a warp per row
+ * of up to 32 quads, 8 rows per block: reports 256 threads, 1 item). */
+int mg_tile_shape(int variant, int *threads, int *items_per_thread);
+
+/* Forget every cached choice (the next mg_create times again).  Not safe
+ * while another thread is inside mg_create. */
+int mg_tune_cache_clear(void);
 
 /* Bytes of device memory the handle holds. */
 int mg_memory_bytes(const mg_handle *h, size_t *bytes);

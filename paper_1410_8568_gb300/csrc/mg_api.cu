@@ -85,6 +85,7 @@ int check_params(const mg_params *p)
     if (p->max_iters < 1 || p->max_iters > 100000) return MG_EINVAL;
     if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) return MG_EINVAL;
     if (p->inner_cycles < 1 || p->inner_cycles > 16) return MG_EINVAL;
+    if (p->tiles < MG_TILES_AUTO || p->tiles >= MG_TILE_VARIANTS) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -219,21 +220,8 @@ int Plan::fill(mg_handle *const *handles, int count)
     prm = hs[0]->prm;
     Lmax = 0;
     for (auto *h : hs) Lmax = std::max(Lmax, h->L);
-    // first level of each grid handled by the bottom-of-cycle kernel: the first
-    // level below the finest with at most kTailCells cells, if at least one
-    // level above the coarsest qualifies (else the grid has no tail: lt = L).
-    // FP32 cycles only: one block per grid runs at one SM's FP64 rate, which on
-    // this GPU is far below that of the per-level FP64 kernels spread over all SMs.
     std::vector<int> lt(G);
-    for (int g = 0; g < G; g++) {
-        mg_handle *h = hs[g];
-        lt[g] = h->L;
-        for (int l = 1; mixed && l + 1 < h->L && l < MG_MAX_LEVELS; l++)
-            if (h->lev[l].N <= kTailCells && h->L - l <= kMaxTail) {
-                lt[g] = l;
-                break;
-            }
-    }
+    for (int g = 0; g < G; g++) lt[g] = first_tail_level(hs[g]);
     LevelView *lv = (LevelView *)(stage_h + o_lv);
     int *starts = (int *)(stage_h + o_starts);
     CoarseView *cvh = (CoarseView *)(stage_h + o_cv);
@@ -249,6 +237,22 @@ int Plan::fill(mg_handle *const *handles, int count)
     for (int l = 0; l + 1 < Lmax; l++) {
         const int lv0 = nlv;
         int sf0 = nst, sc0, sh0, cnt = 0;
+        // launch shape of each table: that of the grid with the most cells on
+        // this level, if it fits every grid of the table, else the row shape
+        int var[3] = {0, 0, 0};
+        long long most = -1;
+        for (int g = 0; g < G; g++) {
+            mg_handle *h = hs[g];
+            if (l + 1 >= h->L || l >= lt[g] || h->lev[l].N <= most) continue;
+            most = h->lev[l].N;
+            for (int k = 0; k < 3; k++) var[k] = h->tile[k][l];
+        }
+        for (int g = 0; g < G; g++) {
+            mg_handle *h = hs[g];
+            if (l + 1 >= h->L || l >= lt[g]) continue;
+            for (int k = 0; k < 3; k++)
+                if (!tile_fits(h->lev[l].n, var[k])) var[k] = 0;
+        }
         // three prefix arrays, each count + 1 long, laid out one after the other
         std::vector<int> sf{0}, sc{0}, sh{0};
         for (int g = 0; g < G; g++) {
@@ -269,9 +273,10 @@ int Plan::fill(mg_handle *const *handles, int count)
             v.bc = C.b;
             v.g = g;
             v.st = h->state;
-            sf.push_back(sf.back() + prolong_blocks(F.n));
-            sc.push_back(sc.back() + restrict_blocks(F.n, C.n));
-            sh.push_back(sh.back() + half_sweep_blocks(F.n));
+            fill_fastdiv(v);
+            sf.push_back(sf.back() + prolong_blocks_v(F.n, var[MG_TILE_PROLONG]));
+            sc.push_back(sc.back() + restrict_blocks_v(F.n, C.n, var[MG_TILE_RESTRICT]));
+            sh.push_back(sh.back() + half_sweep_blocks_v(F.n, var[MG_TILE_HALF]));
             cnt++;
         }
         for (int v : sf) starts[nst++] = v;
@@ -279,9 +284,9 @@ int Plan::fill(mg_handle *const *handles, int count)
         for (int v : sc) starts[nst++] = v;
         sh0 = nst;
         for (int v : sh) starts[nst++] = v;
-        down[l] = Table{d_lv + lv0, d_starts + sf0, cnt, sf.back()};
-        rest[l] = Table{d_lv + lv0, d_starts + sc0, cnt, sc.back()};
-        half[l] = Table{d_lv + lv0, d_starts + sh0, cnt, sh.back()};
+        down[l] = Table{d_lv + lv0, d_starts + sf0, cnt, sf.back(), var[MG_TILE_PROLONG]};
+        rest[l] = Table{d_lv + lv0, d_starts + sc0, cnt, sc.back(), var[MG_TILE_RESTRICT]};
+        half[l] = Table{d_lv + lv0, d_starts + sh0, cnt, sh.back(), var[MG_TILE_HALF]};
     }
     const int so0 = nst;
     starts[nst++] = 0;
@@ -838,6 +843,11 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
         v.err = h->err + 1;
         CK(cudaMemcpy(h->setup_cv, &v, sizeof(v), cudaMemcpyHostToDevice));
     }
+    rc = tune_handle(h);
+    if (rc) {
+        mg_destroy(h);
+        return rc;
+    }
     h->plan = new (std::nothrow) Plan();
     if (!h->plan) {
         mg_destroy(h);
@@ -886,6 +896,7 @@ int mg_params_default(mg_params *p)
     p->precision = MG_PREC_MIXED;
     p->use_graph = 1;
     p->inner_cycles = 2;
+    p->tiles = MG_TILES_AUTO;
     return MG_OK;
 }
 
@@ -1121,13 +1132,16 @@ static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b,
     v.xc = (void *)xc;
     v.bc = bc;
     v.st = h->dstate;
-    const int blocks = tiles == kCoarseTiles ? restrict_blocks(v.n, v.nc)
-                       : tiles == kHalfTiles ? half_sweep_blocks(v.n)
-                       : tiles == kProlongTiles ? prolong_blocks(v.n) : fine_blocks(v.n);
+    fill_fastdiv(v);
+    // the shape the handle's solves use on this level (not on the coarsest)
+    const int kind = tiles == kCoarseTiles ? MG_TILE_RESTRICT : tiles == kProlongTiles ? MG_TILE_PROLONG
+                                                                                       : MG_TILE_HALF;
+    const int var = (tiles != kFineTiles && level + 1 < h->L) ? h->tile[kind][level] : 0;
+    const int blocks = tiles == kFineTiles ? fine_blocks(v.n) : kernel_blocks(kind, v.n, v.nc, var);
     const int starts[2] = {0, blocks};
     CK(cudaMemcpyAsync(h->dview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, h->stream));
-    *tb = Table{h->dview, h->dstart, 1, blocks};
+    *tb = Table{h->dview, h->dstart, 1, blocks, var};
     return MG_OK;
 }
 

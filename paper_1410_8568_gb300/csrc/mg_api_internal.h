@@ -83,6 +83,7 @@ struct mg_handle {
     gbmg::Plan *plan = nullptr;          // single-grid launch plan
     gbmg::Prof prof;
     double *io_rhs = nullptr, *io_p = nullptr, *io_rho = nullptr;  // host-call staging
+    signed char tile[3][MG_MAX_LEVELS] = {};  // launch shape per kernel (MG_TILE_*) and level
 };
 
 namespace gbmg {
@@ -139,6 +140,12 @@ int plan_body(Plan &P);
 int plan_final(Plan &P);
 // states of all grids of the plan into P.st_h (synchronises the stream)
 int plan_sync_states(Plan &P);
+// autotuner (mg_tune.cu): launch shapes of h's levels into h->tile
+int tune_handle(mg_handle *h);
+void tune_cache_clear();
+int first_tail_level(const mg_handle *h);
+void fill_fastdiv(LevelView &v);
+int kernel_blocks(int kind, const int n[3], const int nc[3], int v);
 // allocate a handle (no coefficients yet) / set its coefficients (async)
 int handle_alloc(const mg_grid *grid, const mg_params *params, void *stream, mg_handle **out);
 int set_faces_impl(mg_handle *h, const double *ax, const double *ay, const double *az);

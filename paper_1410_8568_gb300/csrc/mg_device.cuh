@@ -36,6 +36,61 @@ struct GridState {
     int active;     // 1 while the grid is being iterated
 };
 
+// Division by a fixed divisor d >= 1 of numerators n < 2^31 by one multiply
+// and a shift (Granlund & Montgomery, PLDI 1994, round-up variant): with
+// l = ceil(log2 d), m = floor(2^(32+l) / d) + 1, floor(n / d) = (n m) >> (32+l).
+// m overestimates 2^(32+l)/d by at most 1, so the error term n / 2^(32+l) is
+// below 1/(2d) for n < 2^31 and never carries the quotient past an integer.
+struct FastDiv {
+    unsigned long long m;
+    int s;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    int l = 0;
+    while ((1ull << l) < d) l++;
+    FastDiv f;
+    f.s = 32 + l;
+    f.m = ((1ull << f.s) / d) + 1;
+    return f;
+}
+
+__host__ __device__ __forceinline__ int fdiv(int n, const FastDiv &f)
+{
+#ifdef __CUDA_ARCH__
+    // 32 x 33-bit product: m = 2^32 mh + ml, mh in {0, 1}
+    const unsigned ml = (unsigned)f.m, mh = (unsigned)(f.m >> 32);
+    const unsigned long long p = (unsigned long long)(unsigned)n * ml + ((unsigned long long)(mh * (unsigned)n) << 32);
+    return (int)(p >> f.s);
+#else
+    return (int)(((unsigned __int128)(unsigned)n * f.m) >> f.s);
+#endif
+}
+
+// Launch shapes of the half-sweep, restriction and prolongation kernels
+// (chosen per level by the autotuner).  Variant 0 is the row tiling: a warp
+// owns one grid row of up to 32 quads (or 64 cells), 8 rows per 256-thread
+// block.  Variants 1.. are flat tilings for rows of a multiple of 4 cells: the
+// level's quads (restriction: coarse cell pairs) are numbered row by row and a
+// block of B threads owns Q * B consecutive ones, thread t the items t, t + B,
+// ...; short rows then fill whole warps, and B and Q set the blocks per SM and
+// the loads each thread has in flight.
+constexpr int kTileVariants = 7;
+struct TileShape {
+    int B, Q;
+};
+__host__ __device__ constexpr TileShape tile_shape(int v)
+{
+    return v == 1 ? TileShape{64, 1}
+         : v == 2 ? TileShape{128, 1}
+         : v == 3 ? TileShape{128, 2}
+         : v == 4 ? TileShape{256, 1}
+         : v == 5 ? TileShape{256, 2}
+         : v == 6 ? TileShape{512, 1}
+                  : TileShape{kThreads, 1};
+}
+
 // One level of one grid as seen by the V-cycle kernels (precision T is fixed
 // by the kernel instantiation; pointers are typeless here).
 struct LevelView {
@@ -49,6 +104,9 @@ struct LevelView {
     int nc[3];
     int g;          // index of the grid in its plan (selects its OuterView)
     const GridState *st;
+    // flat tilings: quads per fine row n[0]/4, fine rows per plane n[1],
+    // coarse cell pairs per coarse row nc[0]/2, coarse rows per plane nc[1]
+    FastDiv dq, dy, dp, dcy;
 };
 
 // The finest level of one grid for the FP64 outer iteration.

@@ -16,6 +16,7 @@
 // come through L1/L2.  Reductions are deterministic: fixed per-thread order,
 // fixed shuffle tree, per-block partials summed by one block in fixed order.
 #include "mg_kernels.h"
+#include "mg_stencil.cuh"
 
 #include <math.h>
 
@@ -24,19 +25,6 @@ namespace gbmg {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ int find_entry(const int *__restrict__ start, int count)
-{
-    if (count == 1) return 0;
-    const int blk = blockIdx.x;
-    int lo = 0, hi = count;  // start[lo] <= blk < start[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (__ldg(start + mid) <= blk) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
 
 // Neighbour offsets of cell (i,j,k) with the boundary rules of the layout:
 // low face of a cell is stored at the cell; at a Neumann low wall the stored
@@ -180,53 +168,6 @@ __device__ __forceinline__ Tile fine_tile(const int n[3], int lb)
 //                    iterate (last red and last black half-sweep of a
 //                    refinement step on the finest level).
 template <class T>
-struct Quad {
-    T v[4];
-};
-
-template <class T>
-__device__ __forceinline__ Quad<T> ldq(const T *__restrict__ p)
-{
-    Quad<T> q;
-    if constexpr (sizeof(T) == 4) {
-        const float4 a = *reinterpret_cast<const float4 *>(p);
-        q.v[0] = a.x;
-        q.v[1] = a.y;
-        q.v[2] = a.z;
-        q.v[3] = a.w;
-    } else {
-        const double2 a = reinterpret_cast<const double2 *>(p)[0];
-        const double2 b = reinterpret_cast<const double2 *>(p)[1];
-        q.v[0] = a.x;
-        q.v[1] = a.y;
-        q.v[2] = b.x;
-        q.v[3] = b.y;
-    }
-    return q;
-}
-
-template <class T>
-__device__ __forceinline__ void stq(T *p, const Quad<T> &q)
-{
-    if constexpr (sizeof(T) == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
-    } else {
-        reinterpret_cast<double2 *>(p)[0] = make_double2(q.v[0], q.v[1]);
-        reinterpret_cast<double2 *>(p)[1] = make_double2(q.v[2], q.v[3]);
-    }
-}
-
-template <class T>
-__device__ __forceinline__ T relax_div(T num, T den)
-{
-    if constexpr (sizeof(T) == 4) return __fdividef(num, den);  // inner cycle: 2-ulp division
-    else return num / den;
-}
-
-// outer_update / zero flags
-constexpr int kZeroGuess = 1, kOuter = 4;
-
-template <class T>
 __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
                                                    const int *__restrict__ start, int count,
                                                    int colour, T omega, int flags,
@@ -283,69 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
     if (row >= ny * nz) return;
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
-    const int j = row % ny, k = row / ny;
-    const int i0 = qx << 2;
-    const long long c = (long long)row * nx + i0;
-    const int par = (colour + j + k) & 1;  // first cell of the colour in the quad
-    const Quad<T> Z{{T(0), T(0), T(0), T(0)}};
-    const bool has_w = i0 > 0 || (per & 1), has_e = i0 + 4 < nx || (per & 1);
-    const long long cw = i0 > 0 ? c - 1 : c + nx - 1;
-    const long long ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
-    const bool has_s = j > 0 || (per & 2), has_n = j + 1 < ny || (per & 2);
-    const long long cs = j > 0 ? c - sy : c + sy * (ny - 1);
-    const long long cn = j + 1 < ny ? c + sy : c - sy * (ny - 1);
-    const bool has_b = k > 0 || (per & 4), has_t = k + 1 < nz || (per & 4);
-    const long long cb = k > 0 ? c - sz : c + sz * (nz - 1);
-    const long long ct = k + 1 < nz ? c + sz : c - sz * (nz - 1);
-    const Quad<T> bq = ldq(b + c);
-    const Quad<T> fx = ldq(wx + c);
-    const T fxe = has_e ? wx[ce] : T(0);  // high x face of the last cell
-    const Quad<T> fy = ldq(wy + c);
-    const Quad<T> fyn = has_n ? ldq(wy + cn) : Z;
-    const Quad<T> fz = ldq(wz + c);
-    const Quad<T> fzt = has_t ? ldq(wz + ct) : Z;
-    Quad<T> xq = Z, xs = Z, xn = Z, xb = Z, xt = Z;
-    T xw = T(0), xe = T(0);
-    if (!zero) {
-        xq = ldq(x + c);
-        if (has_s) xs = ldq(x + cs);
-        if (has_n) xn = ldq(x + cn);
-        if (has_b) xb = ldq(x + cb);
-        if (has_t) xt = ldq(x + ct);
-        if (has_w) xw = x[cw];
-        if (has_e) xe = x[ce];
-    }
-    Quad<T> out = xq;
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-        if ((u & 1) != par) continue;  // static indices; par is uniform over a warp (one row)
-        const T xc = xq.v[u];
-        const T xl = u > 0 ? xq.v[u - 1] : xw;
-        const T xr = u < 3 ? xq.v[u + 1] : xe;
-        T a, d, f;
-        a = fx.v[u];
-        d = a;
-        f = a * (xl - xc);
-        a = u < 3 ? fx.v[u + 1] : fxe;
-        d += a;
-        f += a * (xr - xc);
-        a = fy.v[u];
-        d += a;
-        f += a * (xs.v[u] - xc);
-        a = fyn.v[u];
-        d += a;
-        f += a * (xn.v[u] - xc);
-        a = fz.v[u];
-        d += a;
-        f += a * (xb.v[u] - xc);
-        a = fzt.v[u];
-        d += a;
-        f += a * (xt.v[u] - xc);
-        const T v = d > T(0) ? xc + omega * relax_div(f - bq.v[u], d) : xc;
-        out.v[u] = v;
-        if (pout) pout[c + u] += (double)v;
-    }
-    stq(x + c, out);
+    half_quad<T>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, pout);
 }
 
 // Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64
@@ -359,86 +238,9 @@ __host__ __device__ inline int half_blocks(const int n[3])
 int half_sweep_blocks(const int n[3]) { return half_blocks(n); }
 int prolong_blocks(const int n[3]) { return half_blocks(n); }
 
-__device__ __forceinline__ int partner(int i, int nc, int periodic)
-{
-    const int I = i >> 1;
-    int J = (i & 1) ? I + 1 : I - 1;
-    if (J < 0 || J >= nc) J = periodic ? (J + nc) % nc : I;  // wrap, or mirror at a wall
-    return J;
-}
-
-// (4) trilinear prolongation at fine cell (i,j,k): weights 3/4 on the coarse
-// cell containing the fine centre and 1/4 on its partner, per axis.
-template <class T>
-__device__ __forceinline__ T prolong_at(const T *__restrict__ ec, const int nc[3], int per, int i,
-                                        int j, int k)
-{
-    const int I0 = i >> 1, I1 = partner(i, nc[0], per & 1);
-    const int J0 = j >> 1, J1 = partner(j, nc[1], per & 2);
-    const int K0 = k >> 1, K1 = partner(k, nc[2], per & 4);
-    const long long r00 = (long long)nc[0] * (J0 + (long long)nc[1] * K0);
-    const long long r10 = (long long)nc[0] * (J1 + (long long)nc[1] * K0);
-    const long long r01 = (long long)nc[0] * (J0 + (long long)nc[1] * K1);
-    const long long r11 = (long long)nc[0] * (J1 + (long long)nc[1] * K1);
-    const T w0 = T(0.75), w1 = T(0.25);
-    // order: z outer, y, x inner; weight product (wx * wy) * wz
-    T s = T(0);
-    s += w0 * w0 * w0 * ec[r00 + I0];
-    s += w1 * w0 * w0 * ec[r00 + I1];
-    s += w0 * w1 * w0 * ec[r10 + I0];
-    s += w1 * w1 * w0 * ec[r10 + I1];
-    s += w0 * w0 * w1 * ec[r01 + I0];
-    s += w1 * w0 * w1 * ec[r01 + I1];
-    s += w0 * w1 * w1 * ec[r11 + I0];
-    s += w1 * w1 * w1 * ec[r11 + I1];
-    return s;
-}
-
 // ---------------------------------------------------------------------------
 // (3) residual and restriction: coarse b = mean of (b - A x) over 8 children
 // ---------------------------------------------------------------------------
-
-// Residual of the 4 cells of the quad at (i0, j, k): b - A x, faces in the
-// order of stencil() (x-, x+, y-, y+, z-, z+).
-template <class T>
-__device__ __forceinline__ Quad<T> residual_quad(const T *__restrict__ x, const T *__restrict__ b,
-                                                 const T *__restrict__ wx, const T *__restrict__ wy,
-                                                 const T *__restrict__ wz, int nx, int ny, int nz,
-                                                 int per, int i0, int j, int k)
-{
-    const long long sy = nx, sz = (long long)nx * ny;
-    const long long c = i0 + sy * j + sz * k;
-    const Quad<T> Z{{T(0), T(0), T(0), T(0)}};
-    const bool has_w = i0 > 0 || (per & 1), has_e = i0 + 4 < nx || (per & 1);
-    const long long cw = i0 > 0 ? c - 1 : c + nx - 1;
-    const long long ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
-    const bool has_s = j > 0 || (per & 2), has_n = j + 1 < ny || (per & 2);
-    const long long cs = j > 0 ? c - sy : c + sy * (ny - 1);
-    const long long cn = j + 1 < ny ? c + sy : c - sy * (ny - 1);
-    const bool has_b = k > 0 || (per & 4), has_t = k + 1 < nz || (per & 4);
-    const long long cb = k > 0 ? c - sz : c + sz * (nz - 1);
-    const long long ct = k + 1 < nz ? c + sz : c - sz * (nz - 1);
-    const Quad<T> xq = ldq(x + c), bq = ldq(b + c);
-    const Quad<T> fx = ldq(wx + c), fy = ldq(wy + c), fz = ldq(wz + c);
-    const Quad<T> fyn = has_n ? ldq(wy + cn) : Z, fzt = has_t ? ldq(wz + ct) : Z;
-    const Quad<T> xs = has_s ? ldq(x + cs) : Z, xn = has_n ? ldq(x + cn) : Z;
-    const Quad<T> xb = has_b ? ldq(x + cb) : Z, xt = has_t ? ldq(x + ct) : Z;
-    const T xw = has_w ? x[cw] : T(0), xe = has_e ? x[ce] : T(0);
-    const T fxe = has_e ? wx[ce] : T(0);
-    Quad<T> r;
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-        const T xc = xq.v[u];
-        T f = fx.v[u] * ((u > 0 ? xq.v[u - 1] : xw) - xc);
-        f += (u < 3 ? fx.v[u + 1] : fxe) * ((u < 3 ? xq.v[u + 1] : xe) - xc);
-        f += fy.v[u] * (xs.v[u] - xc);
-        f += fyn.v[u] * (xn.v[u] - xc);
-        f += fz.v[u] * (xb.v[u] - xc);
-        f += fzt.v[u] * (xt.v[u] - xc);
-        r.v[u] = bq.v[u] - f;
-    }
-    return r;
-}
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restrict__ lv,
@@ -463,22 +265,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
         if (crow >= ncy * ncz) return;
         const int P = (xt << 5) + (threadIdx.x & 31);
         if (P >= np) return;
-        const int J = crow % ncy, K = crow / ncy;
-        T s0 = T(0), s1 = T(0);
-#pragma unroll
-        for (int dz = 0; dz < 2; dz++)
-#pragma unroll
-            for (int dy = 0; dy < 2; dy++) {
-                const Quad<T> r = residual_quad(x, b, wx, wy, wz, nx, ny, nz, L.per, 4 * P, 2 * J + dy,
-                                                2 * K + dz);
-                s0 += r.v[0];
-                s0 += r.v[1];
-                s1 += r.v[2];
-                s1 += r.v[3];
-            }
-        T *bc = (T *)L.bc + (long long)ncx * crow + 2 * P;
-        bc[0] = s0 * T(0.125);
-        bc[1] = s1 * T(0.125);
+        restrict_pair<T>(L, crow, crow % ncy, crow / ncy, P);
         return;
     }
     const int xt_n = coarse_xtiles(ncx);
@@ -539,15 +326,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
-        const int j = row % ny, k = row / ny;
-        const long long c = (long long)row * nx + 4 * qx;
-        Quad<T> xq = ldq(x + c);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            xq.v[u] += prolong_at(ec, L.nc, L.per, 4 * qx + u, j, k);
-            if (pout) pout[c + u] += (double)xq.v[u];
-        }
-        stq(x + c, xq);
+        prolong_quad<T>(L, row, row % ny, row / ny, qx, pout);
         return;
     }
     const Tile t = fine_tile(L.n, lb);
@@ -755,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const LevelView *__restrict_
                                                     const int *__restrict__ start, int count)
 {
     const int e = find_entry(start, count);
-    const LevelView &L = lv[e];
+    const LevelView L = lv[e];
     const Tile t = fine_tile(L.n, blockIdx.x - start[e]);
     if (!t.ok) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
@@ -1208,17 +987,17 @@ void launch_loop_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStr
 }
 
 template <class T>
-void launch_half(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
+void launch_half_rows(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
     k_half<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, ov);
 }
 template <class T>
-void launch_restrict(const Table &tb, cudaStream_t s)
+void launch_restrict_rows(const Table &tb, cudaStream_t s)
 {
     k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
 }
 template <class T>
-void launch_prolong(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
+void launch_prolong_rows(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
 {
     k_prolong<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
 }
@@ -1283,12 +1062,12 @@ void launch_final(const OuterTable &ot, cudaStream_t s)
     k_final<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
 }
 
-template void launch_half<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
-template void launch_half<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
-template void launch_restrict<float>(const Table &, cudaStream_t);
-template void launch_restrict<double>(const Table &, cudaStream_t);
-template void launch_prolong<float>(const Table &, const OuterView *, int, cudaStream_t);
-template void launch_prolong<double>(const Table &, const OuterView *, int, cudaStream_t);
+template void launch_half_rows<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_half_rows<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_restrict_rows<float>(const Table &, cudaStream_t);
+template void launch_restrict_rows<double>(const Table &, cudaStream_t);
+template void launch_prolong_rows<float>(const Table &, const OuterView *, int, cudaStream_t);
+template void launch_prolong_rows<double>(const Table &, const OuterView *, int, cudaStream_t);
 template void launch_tail<float>(const TailView *, int, size_t, double, int, int, cudaStream_t);
 template void launch_tail<double>(const TailView *, int, size_t, double, int, int, cudaStream_t);
 template void launch_apply<float>(const Table &, cudaStream_t);

@@ -12,6 +12,7 @@ struct Table {
     const int *start;
     int count;
     int blocks;
+    int variant = 0;  // launch shape (tile_shape); 0 = row tiles
 };
 
 struct OuterTable {
@@ -48,10 +49,22 @@ constexpr int kHalfZero = 1, kHalfOuter = 4;
 int half_sweep_blocks(const int n[3]);
 int restrict_blocks(const int n[3], const int nc[3]);
 int prolong_blocks(const int n[3]);
+// the same for launch shape v (mg_tiles.cu); v > 0 needs n[0] % 4 == 0
+bool tile_fits(const int n[3], int v);
+int half_sweep_blocks_v(const int n[3], int v);
+int restrict_blocks_v(const int n[3], const int nc[3], int v);
+int prolong_blocks_v(const int n[3], int v);
+// launchers that dispatch on Table::variant (mg_tiles.cu) ...
 template <class T> void launch_half(const Table &, int colour, double omega, int flags,
                                     const OuterView *ov, cudaStream_t);
 template <class T> void launch_restrict(const Table &, cudaStream_t);
 template <class T> void launch_prolong(const Table &, const OuterView *ov, int outer_update, cudaStream_t);
+// ... and the row-tiled kernels they fall back to (mg_kernels.cu)
+template <class T> void launch_half_rows(const Table &, int colour, double omega, int flags,
+                                         const OuterView *ov, cudaStream_t);
+template <class T> void launch_restrict_rows(const Table &, cudaStream_t);
+template <class T> void launch_prolong_rows(const Table &, const OuterView *ov, int outer_update,
+                                            cudaStream_t);
 template <class T> void launch_tail(const TailView *, int count, size_t smem, double omega, int nu1,
                                     int nu2, cudaStream_t);
 template <class T> void launch_apply(const Table &, cudaStream_t);

@@ -1,0 +1,176 @@
+// mg_tiles.cu -- flat-tiled variants of the half-sweep, restriction and
+// prolongation kernels, and the launchers that run a table with the launch
+// shape chosen for it (Table::variant, see tile_shape in mg_device.cuh).
+//
+// The per-quad arithmetic is the same code as the row-tiled kernels
+// (mg_stencil.cuh), and every cell's result depends only on its own operands,
+// so a solve gives bitwise the same result whatever shapes are chosen.
+#include <type_traits>
+
+#include "mg_kernels.h"
+#include "mg_stencil.cuh"
+
+namespace gbmg {
+
+// Block lb of a table entry owns items [lb Q B, (lb + 1) Q B); thread t handles
+// lb Q B + q B + t for q < Q.  Items are numbered row by row, so consecutive
+// threads touch consecutive 16-byte vectors.
+template <class T, int B, int Q>
+__global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ lv,
+                                                 const int *__restrict__ start, int count,
+                                                 int colour, T omega, int flags,
+                                                 const OuterView *__restrict__ ov)
+{
+    const int e = find_entry(start, count);
+    const LevelView &L = lv[e];
+    if (!L.st->active) return;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2], nq = nx >> 2;
+    const int items = nq * ny * nz;
+    const int lb = blockIdx.x - start[e];
+    const bool zero = flags & kZeroGuess;
+    double *pout = (flags & kOuter) ? ov[L.g].p : nullptr;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        const int g = (lb * Q + q) * B + (int)threadIdx.x;
+        if (g >= items) return;
+        const int row = fdiv(g, L.dq);
+        const int k = fdiv(row, L.dy);
+        half_quad<T>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
+                     (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
+                     omega, zero, pout);
+    }
+}
+
+template <class T, int B, int Q>
+__global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict__ lv,
+                                                     const int *__restrict__ start, int count)
+{
+    const int e = find_entry(start, count);
+    const LevelView &L = lv[e];
+    if (!L.st->active) return;
+    const int np = L.nc[0] >> 1, ncy = L.nc[1];
+    const int items = np * ncy * L.nc[2];
+    const int lb = blockIdx.x - start[e];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        const int g = (lb * Q + q) * B + (int)threadIdx.x;
+        if (g >= items) return;
+        const int crow = fdiv(g, L.dp);
+        const int K = fdiv(crow, L.dcy);
+        restrict_pair<T>(L, crow, crow - K * ncy, K, g - crow * np);
+    }
+}
+
+template <class T, int B, int Q>
+__global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict__ lv,
+                                                    const int *__restrict__ start, int count,
+                                                    const OuterView *__restrict__ ov,
+                                                    int outer_update)
+{
+    const int e = find_entry(start, count);
+    const LevelView &L = lv[e];
+    if (!L.st->active) return;
+    const int nq = L.n[0] >> 2, ny = L.n[1];
+    const int items = nq * ny * L.n[2];
+    const int lb = blockIdx.x - start[e];
+    double *pout = outer_update ? ov[L.g].p : nullptr;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        const int g = (lb * Q + q) * B + (int)threadIdx.x;
+        if (g >= items) return;
+        const int row = fdiv(g, L.dq);
+        const int k = fdiv(row, L.dy);
+        prolong_quad<T>(L, row, row - k * ny, k, g - row * nq, pout);
+    }
+}
+
+namespace {
+
+// call f(std::integral_constant<int, v>) for a flat variant v (1 .. kTileVariants - 1)
+template <class F>
+bool with_variant(int v, F &&f)
+{
+    switch (v) {
+    case 1: f(std::integral_constant<int, 1>{}); return true;
+    case 2: f(std::integral_constant<int, 2>{}); return true;
+    case 3: f(std::integral_constant<int, 3>{}); return true;
+    case 4: f(std::integral_constant<int, 4>{}); return true;
+    case 5: f(std::integral_constant<int, 5>{}); return true;
+    case 6: f(std::integral_constant<int, 6>{}); return true;
+    default: return false;
+    }
+}
+static_assert(kTileVariants == 7, "with_variant lists every flat variant");
+
+int flat_blocks(long long items, int v)
+{
+    const TileShape ts = tile_shape(v);
+    const long long per = (long long)ts.B * ts.Q;
+    return (int)((items + per - 1) / per);
+}
+
+}  // namespace
+
+bool tile_fits(const int n[3], int v) { return v == 0 || (v > 0 && v < kTileVariants && (n[0] & 3) == 0); }
+
+int half_sweep_blocks_v(const int n[3], int v)
+{
+    if (v == 0) return half_sweep_blocks(n);
+    return flat_blocks((long long)(n[0] >> 2) * n[1] * n[2], v);
+}
+
+int prolong_blocks_v(const int n[3], int v)
+{
+    if (v == 0) return prolong_blocks(n);
+    return flat_blocks((long long)(n[0] >> 2) * n[1] * n[2], v);
+}
+
+int restrict_blocks_v(const int n[3], const int nc[3], int v)
+{
+    if (v == 0) return restrict_blocks(n, nc);
+    return flat_blocks((long long)(nc[0] >> 1) * nc[1] * nc[2], v);
+}
+
+template <class T>
+void launch_half(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
+{
+    if (tb.blocks == 0) return;
+    const bool flat = with_variant(tb.variant, [&](auto V) {
+        constexpr TileShape ts = tile_shape(decltype(V)::value);
+        k_half_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega,
+                                                              flags, ov);
+    });
+    if (!flat) launch_half_rows<T>(tb, colour, omega, flags, ov, s);
+}
+
+template <class T>
+void launch_restrict(const Table &tb, cudaStream_t s)
+{
+    if (tb.blocks == 0) return;
+    const bool flat = with_variant(tb.variant, [&](auto V) {
+        constexpr TileShape ts = tile_shape(decltype(V)::value);
+        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count);
+    });
+    if (!flat) launch_restrict_rows<T>(tb, s);
+}
+
+template <class T>
+void launch_prolong(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
+{
+    if (tb.blocks == 0) return;
+    const bool flat = with_variant(tb.variant, [&](auto V) {
+        constexpr TileShape ts = tile_shape(decltype(V)::value);
+        k_prolong_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, ov,
+                                                                 outer_update);
+    });
+    if (!flat) launch_prolong_rows<T>(tb, ov, outer_update, s);
+}
+
+template void launch_half<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_half<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_restrict<float>(const Table &, cudaStream_t);
+template void launch_restrict<double>(const Table &, cudaStream_t);
+template void launch_prolong<float>(const Table &, const OuterView *, int, cudaStream_t);
+template void launch_prolong<double>(const Table &, const OuterView *, int, cudaStream_t);
+
+}  // namespace gbmg

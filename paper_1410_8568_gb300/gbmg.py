@@ -25,6 +25,8 @@ NEUMANN, PERIODIC = 0, 1
 FP64, MIXED = 0, 1
 HARMONIC, ARITHMETIC = 0, 1
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL = range(7)
+TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
+TILE_HALF, TILE_RESTRICT, TILE_PROLONG = 0, 1, 2
 
 
 class MGError(RuntimeError):
@@ -42,7 +44,7 @@ class Grid(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("tiles", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -102,6 +104,9 @@ def lib():
             "mg_memory_bytes": (_I, [_V, _P(ctypes.c_size_t)]),
             "mg_memory_estimate": (_I, [_P(Grid), _P(Params), _P(ctypes.c_size_t)]),
             "mg_coarse_solve_static": (_I, [_P(Grid), _V, _V, _V, _V, _V, _V]),
+            "mg_tile_choice": (_I, [_V, _I, _I, _P(_I)]),
+            "mg_tile_shape": (_I, [_I, _P(_I), _P(_I)]),
+            "mg_tune_cache_clear": (_I, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -135,7 +140,7 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
 
 
 def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
-                inner_cycles=None) -> Params:
+                inner_cycles=None, tiles=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
@@ -144,7 +149,21 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
     p.use_graph = 1 if use_graph else 0
     if inner_cycles is not None:
         p.inner_cycles = int(inner_cycles)
+    if tiles is not None:
+        p.tiles = int(tiles)
     return p
+
+
+def tile_shape(variant):
+    """(threads per block, items per thread) of launch shape `variant`."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(lib().mg_tile_shape(int(variant), ctypes.byref(a), ctypes.byref(b)), "mg_tile_shape")
+    return (a.value, b.value)
+
+
+def tune_cache_clear():
+    """Forget the autotuner's cached launch shapes."""
+    check(lib().mg_tune_cache_clear(), "mg_tune_cache_clear")
 
 
 def _ptr(t, cells=None, dtype=None):
@@ -193,7 +212,7 @@ class Solver:
 
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
                  precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
-                 inner_cycles=None):
+                 inner_cycles=None, tiles=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -202,7 +221,7 @@ class Solver:
         self.cells = int(np.prod(self.shape))
         self.precision = precision
         self.grid = make_grid(self.shape, self.bc, self.length)
-        self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles)
+        self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:
@@ -279,6 +298,12 @@ class Solver:
         if rc not in (OK, ENOTCONV, EDIVERGED):
             check(rc, "mg_step_host")
         return st
+
+    def tile_choice(self, kind, level) -> int:
+        """Launch shape used for kernel `kind` (TILE_*) on `level`."""
+        v = ctypes.c_int()
+        check(lib().mg_tile_choice(self._h, int(kind), int(level), ctypes.byref(v)), "mg_tile_choice")
+        return v.value
 
     # -- single steps (unit checks) ----------------------------------------
     def num_levels(self) -> int:

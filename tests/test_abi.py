@@ -54,6 +54,30 @@ def test_host_only_calls():
         gbmg.memory_estimate((1, 8, 8), (0, 0, 0))
 
 
+def test_tile_shapes_and_params():
+    """Launch-shape table and the tiles parameter (host only)."""
+    L = gbmg.lib()
+    p = gbmg.Params()
+    assert L.mg_params_default(ctypes.byref(p)) == 0
+    assert p.tiles == gbmg.TILES_AUTO
+    shapes = [gbmg.tile_shape(v) for v in range(gbmg.TILE_VARIANTS)]
+    assert shapes[0] == (256, 1)  # row tiling: 8 rows of one warp
+    assert len(set(shapes[1:])) == gbmg.TILE_VARIANTS - 1
+    for threads, q in shapes:
+        assert threads % 32 == 0 and 32 <= threads <= 1024 and q >= 1
+    with pytest.raises(gbmg.MGError):
+        gbmg.tile_shape(gbmg.TILE_VARIANTS)
+    g = gbmg.make_grid((32, 32, 32), (0, 0, 0))
+    size = ctypes.c_size_t()
+    for tiles in (gbmg.TILES_AUTO, gbmg.TILES_ROWS, gbmg.TILE_VARIANTS - 1):
+        p.tiles = tiles
+        assert L.mg_memory_estimate(ctypes.byref(g), ctypes.byref(p), ctypes.byref(size)) == gbmg.OK
+    for tiles in (-2, gbmg.TILE_VARIANTS):
+        p.tiles = tiles
+        assert L.mg_memory_estimate(ctypes.byref(g), ctypes.byref(p), ctypes.byref(size)) == gbmg.EINVAL
+    assert gbmg.lib().mg_tune_cache_clear() == gbmg.OK
+
+
 def test_no_gpu_fails_loudly():
     """Without a usable GPU the product path raises instead of computing on the host."""
     import torch
