@@ -104,10 +104,12 @@ typedef struct {
 typedef struct {
     int nu1, nu2;      /* pre- and post-relaxation sweeps (one sweep = red then black), nu1 >= 1 */
     double omega;      /* SOR factor of the red-black relaxation, 0 < omega < 2 */
-    int max_iters;     /* most V-cycles per solve */
+    int max_iters;     /* most V-cycles per solve, rounded up to whole refinement steps
+                          (inner_cycles V-cycles each) */
     int precision;     /* MG_PREC_FP64 or MG_PREC_MIXED */
     int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
-    int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1 */
+    int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1;
+                          0 (default) = 3 in MIXED precision, 2 in FP64 */
     int tiles;         /* launch shapes of the V-cycle kernels: MG_TILES_AUTO (autotuned per
                           level), MG_TILES_ROWS, or a variant 1 .. MG_TILE_VARIANTS - 1 for
                           every level whose rows are a multiple of 4 cells */
@@ -344,9 +346,25 @@ int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant);
  * of up to 32 quads, 8 rows per block: reports 256 threads, 1 item). */
 int mg_tile_shape(int variant, int *threads, int *items_per_thread);
 
-/* Forget every cached choice (the next mg_create times again).  Not safe
- * while another thread is inside mg_create. */
+/* Forget every cached choice (the next mg_create times again). */
 int mg_tune_cache_clear(void);
+
+/* Write the cached choices to the text file `path` (one line per choice:
+ * kind precision periodic-bits nx ny nz variant), replacing it. */
+int mg_tune_cache_save(const char *path);
+
+/* Add the choices in `path` to the cache (lines that do not parse, or name a
+ * shape that does not fit the level, are skipped); *loaded (may be NULL) gets
+ * the number of choices read.  MG_ENOTFOUND if the file cannot be opened.
+ * When the environment variable MG_TUNE_CACHE names a file, the first tuning
+ * of the process loads it and each new choice is appended to it. */
+int mg_tune_cache_load(const char *path, int *loaded);
+
+/* Number of cached choices. */
+int mg_tune_cache_size(int *entries);
+
+/* The parameters h was created with, defaults resolved (inner_cycles). */
+int mg_handle_params(const mg_handle *h, mg_params *params);
 
 /* Bytes of device memory the handle holds. */
 int mg_memory_bytes(const mg_handle *h, size_t *bytes);

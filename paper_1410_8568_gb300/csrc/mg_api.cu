@@ -84,7 +84,7 @@ int check_params(const mg_params *p)
     if (!(p->omega > 0.0 && p->omega < 2.0)) return MG_EINVAL;
     if (p->max_iters < 1 || p->max_iters > 100000) return MG_EINVAL;
     if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) return MG_EINVAL;
-    if (p->inner_cycles < 1 || p->inner_cycles > 16) return MG_EINVAL;
+    if (p->inner_cycles < 0 || p->inner_cycles > 16) return MG_EINVAL;
     if (p->tiles < MG_TILES_AUTO || p->tiles >= MG_TILE_VARIANTS) return MG_EINVAL;
     return MG_OK;
 }
@@ -779,6 +779,10 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
     if (params) prm = *params;
     rc = check_params(&prm);
     if (rc) return rc;
+    // V-cycles per FP64 residual: FP32 cycles are cheap next to the FP64
+    // residual pass (FP64 arithmetic is slow on this GPU), so mixed precision
+    // takes 3; FP64 cycles cost as much as the pass, 2 balances them
+    if (prm.inner_cycles == 0) prm.inner_cycles = prm.precision == MG_PREC_MIXED ? 3 : 2;
     Layout lay;
     rc = plan_layout(*grid, prm, lay);
     if (rc) return rc;
@@ -895,7 +899,7 @@ int mg_params_default(mg_params *p)
     p->max_iters = 100;
     p->precision = MG_PREC_MIXED;
     p->use_graph = 1;
-    p->inner_cycles = 2;
+    p->inner_cycles = 0;
     p->tiles = MG_TILES_AUTO;
     return MG_OK;
 }
@@ -1244,6 +1248,13 @@ int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double
     if (!h || kind < 0 || kind >= MG_K_KINDS || level < 0 || level >= MG_MAX_LEVELS) return MG_EINVAL;
     if (launches) *launches = h->prof.launches[kind][level];
     if (total_ms) *total_ms = h->prof.total_ms[kind][level];
+    return MG_OK;
+}
+
+int mg_handle_params(const mg_handle *h, mg_params *params)
+{
+    if (!h || !params) return MG_EINVAL;
+    *params = h->prm;
     return MG_OK;
 }
 

@@ -73,77 +73,102 @@ __device__ __forceinline__ T relax_div(T num, T den)
 constexpr int kZeroGuess = 1, kOuter = 4;
 
 // Relaxation of the cells of colour `colour` in the aligned quad (4 qx .. 4 qx + 3,
-// j, k) of row `row` = j + ny k: all operands as 16-byte vectors, the two cells
-// of the other colour written back unchanged.
+// j, k) of row `row` = j + ny k.  The two cells of the colour are p0 = 4 qx + par
+// and p0 + 2 (par = 0 or 1).  The quad of x and its x-faces are loaded as
+// 16-byte vectors (each colour cell needs its in-row neighbours, which are
+// the other colour); b and the y/z neighbours and faces only at the two colour
+// cells.  The quad is written back whole, the other colour unchanged.  Per
+// cell, the terms are summed in the order x-, x+, y-, y+, z-, z+ as in every
+// other kernel.
+template <class T>
+__device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn, T fb, T ft, T xs,
+                                        T xn, T xb, T xt, T bc, T omega)
+{
+    T d, f;
+    d = fl;
+    f = fl * (xl - xc);
+    d += fr;
+    f += fr * (xr - xc);
+    d += fs;
+    f += fs * (xs - xc);
+    d += fn;
+    f += fn * (xn - xc);
+    d += fb;
+    f += fb * (xb - xc);
+    d += ft;
+    f += ft * (xt - xc);
+    return d > T(0) ? xc + omega * relax_div(f - bc, d) : xc;
+}
+
 template <class T>
 __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T *wy, const T *wz,
                                           int nx, int ny, int nz, int per, int row, int j, int k,
                                           int qx, int colour, T omega, bool zero, double *pout)
 {
-    const long long sy = nx, sz = (long long)nx * ny;
+    // cell indices fit in 32 bits: a grid has fewer than 2^31 cells
+    const int sy = nx, sz = nx * ny;
     const int i0 = qx << 2;
-    const long long c = (long long)row * nx + i0;
-    const int par = (colour + j + k) & 1;  // first cell of the colour in the quad
-    const Quad<T> Z{{T(0), T(0), T(0), T(0)}};
+    const int c = row * nx + i0;
+    const int par = (colour + j + k) & 1;
+    const int c0 = c + par;  // first cell of the colour; the second is c0 + 2
     const bool has_w = i0 > 0 || (per & 1), has_e = i0 + 4 < nx || (per & 1);
-    const long long cw = i0 > 0 ? c - 1 : c + nx - 1;
-    const long long ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
-    const bool has_s = j > 0 || (per & 2), has_n = j + 1 < ny || (per & 2);
-    const long long cs = j > 0 ? c - sy : c + sy * (ny - 1);
-    const long long cn = j + 1 < ny ? c + sy : c - sy * (ny - 1);
-    const bool has_b = k > 0 || (per & 4), has_t = k + 1 < nz || (per & 4);
-    const long long cb = k > 0 ? c - sz : c + sz * (nz - 1);
-    const long long ct = k + 1 < nz ? c + sz : c - sz * (nz - 1);
-    const Quad<T> bq = ldq(b + c);
+    const int cw = i0 > 0 ? c - 1 : c + nx - 1;
+    const int ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
+    const bool has_n = j + 1 < ny || (per & 2), has_t = k + 1 < nz || (per & 4);
+    const bool has_s = j > 0 || (per & 2), has_b = k > 0 || (per & 4);
+    const int ds = j > 0 ? -sy : sy * (ny - 1);  // offset of the y- neighbour
+    const int dn = j + 1 < ny ? sy : -sy * (ny - 1);
+    const int db = k > 0 ? -sz : sz * (nz - 1);
+    const int dt = k + 1 < nz ? sz : -sz * (nz - 1);
     const Quad<T> fx = ldq(wx + c);
-    const T fxe = has_e ? wx[ce] : T(0);  // high x face of the last cell
-    const Quad<T> fy = ldq(wy + c);
-    const Quad<T> fyn = has_n ? ldq(wy + cn) : Z;
-    const Quad<T> fz = ldq(wz + c);
-    const Quad<T> fzt = has_t ? ldq(wz + ct) : Z;
-    Quad<T> xq = Z, xs = Z, xn = Z, xb = Z, xt = Z;
+    const T fxe = has_e ? wx[ce] : T(0);  // high x face of the last cell of the quad
+    const T b0 = b[c0], b1 = b[c0 + 2];
+    const T fs0 = wy[c0], fs1 = wy[c0 + 2];
+    const T fn0 = has_n ? wy[c0 + dn] : T(0), fn1 = has_n ? wy[c0 + 2 + dn] : T(0);
+    const T fb0 = wz[c0], fb1 = wz[c0 + 2];
+    const T ft0 = has_t ? wz[c0 + dt] : T(0), ft1 = has_t ? wz[c0 + 2 + dt] : T(0);
+    Quad<T> xq{{T(0), T(0), T(0), T(0)}};
     T xw = T(0), xe = T(0);
+    T xs0 = T(0), xs1 = T(0), xn0 = T(0), xn1 = T(0), xb0 = T(0), xb1 = T(0), xt0 = T(0), xt1 = T(0);
     if (!zero) {
         xq = ldq(x + c);
-        if (has_s) xs = ldq(x + cs);
-        if (has_n) xn = ldq(x + cn);
-        if (has_b) xb = ldq(x + cb);
-        if (has_t) xt = ldq(x + ct);
         if (has_w) xw = x[cw];
         if (has_e) xe = x[ce];
+        if (has_s) {
+            xs0 = x[c0 + ds];
+            xs1 = x[c0 + 2 + ds];
+        }
+        if (has_n) {
+            xn0 = x[c0 + dn];
+            xn1 = x[c0 + 2 + dn];
+        }
+        if (has_b) {
+            xb0 = x[c0 + db];
+            xb1 = x[c0 + 2 + db];
+        }
+        if (has_t) {
+            xt0 = x[c0 + dt];
+            xt1 = x[c0 + 2 + dt];
+        }
     }
+    // cell p0 (u = par) and cell p0 + 2 (u = par + 2): centre, x neighbours, x faces
+    const T xc0 = par ? xq.v[1] : xq.v[0], xc1 = par ? xq.v[3] : xq.v[2];
+    const T xl0 = par ? xq.v[0] : xw, xr0 = par ? xq.v[2] : xq.v[1];
+    const T xl1 = par ? xq.v[2] : xq.v[1], xr1 = par ? xe : xq.v[3];
+    const T fl0 = par ? fx.v[1] : fx.v[0], fr0 = par ? fx.v[2] : fx.v[1];
+    const T fl1 = par ? fx.v[3] : fx.v[2], fr1 = par ? fxe : fx.v[3];
+    const T v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega);
+    const T v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega);
     Quad<T> out = xq;
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-        // static indices; par is uniform over a warp when the warp holds one row
-        if ((u & 1) != par) continue;
-        const T xc = xq.v[u];
-        const T xl = u > 0 ? xq.v[u - 1] : xw;
-        const T xr = u < 3 ? xq.v[u + 1] : xe;
-        T a, d, f;
-        a = fx.v[u];
-        d = a;
-        f = a * (xl - xc);
-        a = u < 3 ? fx.v[u + 1] : fxe;
-        d += a;
-        f += a * (xr - xc);
-        a = fy.v[u];
-        d += a;
-        f += a * (xs.v[u] - xc);
-        a = fyn.v[u];
-        d += a;
-        f += a * (xn.v[u] - xc);
-        a = fz.v[u];
-        d += a;
-        f += a * (xb.v[u] - xc);
-        a = fzt.v[u];
-        d += a;
-        f += a * (xt.v[u] - xc);
-        const T v = d > T(0) ? xc + omega * relax_div(f - bq.v[u], d) : xc;
-        out.v[u] = v;
-        if (pout) pout[c + u] += (double)v;
-    }
+    out.v[0] = par ? xq.v[0] : v0;
+    out.v[1] = par ? v0 : xq.v[1];
+    out.v[2] = par ? xq.v[2] : v1;
+    out.v[3] = par ? v1 : xq.v[3];
     stq(x + c, out);
+    if (pout) {
+        pout[c0] += (double)v0;
+        pout[c0 + 2] += (double)v1;
+    }
 }
 
 __device__ __forceinline__ int partner(int i, int nc, int periodic)
@@ -163,10 +188,10 @@ __device__ __forceinline__ T prolong_at(const T *__restrict__ ec, const int nc[3
     const int I0 = i >> 1, I1 = partner(i, nc[0], per & 1);
     const int J0 = j >> 1, J1 = partner(j, nc[1], per & 2);
     const int K0 = k >> 1, K1 = partner(k, nc[2], per & 4);
-    const long long r00 = (long long)nc[0] * (J0 + (long long)nc[1] * K0);
-    const long long r10 = (long long)nc[0] * (J1 + (long long)nc[1] * K0);
-    const long long r01 = (long long)nc[0] * (J0 + (long long)nc[1] * K1);
-    const long long r11 = (long long)nc[0] * (J1 + (long long)nc[1] * K1);
+    const int r00 = nc[0] * (J0 + nc[1] * K0);
+    const int r10 = nc[0] * (J1 + nc[1] * K0);
+    const int r01 = nc[0] * (J0 + nc[1] * K1);
+    const int r11 = nc[0] * (J1 + nc[1] * K1);
     const T w0 = T(0.75), w1 = T(0.25);
     // order: z outer, y, x inner; weight product (wx * wy) * wz
     T s = T(0);
@@ -189,18 +214,18 @@ __device__ __forceinline__ Quad<T> residual_quad(const T *__restrict__ x, const 
                                                  const T *__restrict__ wz, int nx, int ny, int nz,
                                                  int per, int i0, int j, int k)
 {
-    const long long sy = nx, sz = (long long)nx * ny;
-    const long long c = i0 + sy * j + sz * k;
+    const int sy = nx, sz = nx * ny;
+    const int c = i0 + sy * j + sz * k;
     const Quad<T> Z{{T(0), T(0), T(0), T(0)}};
     const bool has_w = i0 > 0 || (per & 1), has_e = i0 + 4 < nx || (per & 1);
-    const long long cw = i0 > 0 ? c - 1 : c + nx - 1;
-    const long long ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
+    const int cw = i0 > 0 ? c - 1 : c + nx - 1;
+    const int ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
     const bool has_s = j > 0 || (per & 2), has_n = j + 1 < ny || (per & 2);
-    const long long cs = j > 0 ? c - sy : c + sy * (ny - 1);
-    const long long cn = j + 1 < ny ? c + sy : c - sy * (ny - 1);
+    const int cs = j > 0 ? c - sy : c + sy * (ny - 1);
+    const int cn = j + 1 < ny ? c + sy : c - sy * (ny - 1);
     const bool has_b = k > 0 || (per & 4), has_t = k + 1 < nz || (per & 4);
-    const long long cb = k > 0 ? c - sz : c + sz * (nz - 1);
-    const long long ct = k + 1 < nz ? c + sz : c - sz * (nz - 1);
+    const int cb = k > 0 ? c - sz : c + sz * (nz - 1);
+    const int ct = k + 1 < nz ? c + sz : c - sz * (nz - 1);
     const Quad<T> xq = ldq(x + c), bq = ldq(b + c);
     const Quad<T> fx = ldq(wx + c), fy = ldq(wy + c), fz = ldq(wz + c);
     const Quad<T> fyn = has_n ? ldq(wy + cn) : Z, fzt = has_t ? ldq(wz + ct) : Z;
@@ -245,7 +270,7 @@ __device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int 
             s1 += r.v[2];
             s1 += r.v[3];
         }
-    T *bc = (T *)L.bc + (long long)ncx * crow + 2 * P;
+    T *bc = (T *)L.bc + ncx * crow + 2 * P;
     bc[0] = s0 * T(0.125);
     bc[1] = s1 * T(0.125);
 }
@@ -258,7 +283,7 @@ __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j,
     const int nx = L.n[0];
     const T *ec = (const T *)L.xc;
     T *x = (T *)L.x;
-    const long long c = (long long)row * nx + 4 * qx;
+    const int c = row * nx + 4 * qx;
     Quad<T> xq = ldq(x + c);
 #pragma unroll
     for (int u = 0; u < 4; u++) {

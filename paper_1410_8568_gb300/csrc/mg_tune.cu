@@ -16,9 +16,17 @@
 // do not change the timings.  A shape never changes a result: the per-cell
 // arithmetic is shared by all shapes, and the tests check solves bitwise equal
 // across shapes.
+//
+// The choices can outlive the process: mg_tune_cache_save / _load write and
+// read them as text, one line per choice ("kind mixed per nx ny nz variant"),
+// and when the environment variable MG_TUNE_CACHE names a file, the first
+// tuning of the process loads it and every new choice is appended to it.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
 #include <map>
 #include <mutex>
-#include <string.h>
 
 #include "mg_api_internal.h"
 
@@ -70,6 +78,49 @@ struct TuneKey {
 
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
+bool g_env_loaded = false;
+
+// read choices from `path` into the cache (caller holds g_tune_mu); lines that
+// do not parse or name an unknown shape are skipped
+int load_locked(const char *path, int *loaded)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) return MG_ENOTFOUND;
+    char line[256];
+    int n = 0;
+    while (fgets(line, sizeof(line), f)) {
+        TuneKey k;
+        memset(&k, 0, sizeof(k));
+        int v;
+        if (sscanf(line, "%d %d %d %d %d %d %d", &k.kind, &k.mixed, &k.per, &k.n[0], &k.n[1], &k.n[2], &v) != 7)
+            continue;
+        if (k.kind < 0 || k.kind > 2 || (k.mixed != 0 && k.mixed != 1) || k.per < 0 || k.per > 7 || v < 0 ||
+            v >= kTileVariants || !tile_fits(k.n, v))
+            continue;
+        g_tune[k] = v;
+        n++;
+    }
+    fclose(f);
+    if (loaded) *loaded = n;
+    return MG_OK;
+}
+
+void write_line(FILE *f, const TuneKey &k, int v)
+{
+    fprintf(f, "%d %d %d %d %d %d %d\n", k.kind, k.mixed, k.per, k.n[0], k.n[1], k.n[2], v);
+}
+
+// the environment's cache file, read once per process (caller holds g_tune_mu)
+const char *env_cache_locked()
+{
+    const char *path = getenv("MG_TUNE_CACHE");
+    if (!path || !*path) return nullptr;
+    if (!g_env_loaded) {
+        g_env_loaded = true;
+        load_locked(path, nullptr);
+    }
+    return path;
+}
 
 template <class T>
 int time_shape(mg_handle *h, int kind, int l, int v, float *ms)
@@ -151,6 +202,7 @@ int tune_handle(mg_handle *h)
             for (int d = 0; d < 3; d++) key.n[d] = n[d];
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
+                env_cache_locked();
                 auto it = g_tune.find(key);
                 if (it != g_tune.end()) {
                     h->tile[kind][l] = (signed char)it->second;
@@ -171,11 +223,15 @@ int tune_handle(mg_handle *h)
             int best = 0;
             for (int v = 1; v < kTileVariants; v++)
                 if (t[v] < t[best]) best = v;
-            // keep the row tiling unless another shape is clearly faster
-            if (t[0] <= 1.02f * t[best]) best = 0;
             h->tile[kind][l] = (signed char)best;
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune[key] = best;
+            if (const char *path = env_cache_locked()) {
+                if (FILE *f = fopen(path, "a")) {
+                    write_line(f, key, best);
+                    fclose(f);
+                }
+            }
         }
     }
     return MG_OK;
@@ -210,6 +266,31 @@ int mg_tile_shape(int variant, int *threads, int *items_per_thread)
 int mg_tune_cache_clear(void)
 {
     gbmg::tune_cache_clear();
+    return MG_OK;
+}
+
+int mg_tune_cache_save(const char *path)
+{
+    if (!path) return MG_EINVAL;
+    std::lock_guard<std::mutex> lk(gbmg::g_tune_mu);
+    FILE *f = fopen(path, "w");
+    if (!f) return MG_EINVAL;
+    for (const auto &kv : gbmg::g_tune) gbmg::write_line(f, kv.first, kv.second);
+    return fclose(f) == 0 ? MG_OK : MG_EINVAL;
+}
+
+int mg_tune_cache_load(const char *path, int *loaded)
+{
+    if (!path) return MG_EINVAL;
+    std::lock_guard<std::mutex> lk(gbmg::g_tune_mu);
+    return gbmg::load_locked(path, loaded);
+}
+
+int mg_tune_cache_size(int *entries)
+{
+    if (!entries) return MG_EINVAL;
+    std::lock_guard<std::mutex> lk(gbmg::g_tune_mu);
+    *entries = (int)gbmg::g_tune.size();
     return MG_OK;
 }
 

@@ -107,6 +107,10 @@ def lib():
             "mg_tile_choice": (_I, [_V, _I, _I, _P(_I)]),
             "mg_tile_shape": (_I, [_I, _P(_I), _P(_I)]),
             "mg_tune_cache_clear": (_I, []),
+            "mg_tune_cache_save": (_I, [ctypes.c_char_p]),
+            "mg_tune_cache_load": (_I, [ctypes.c_char_p, _P(_I)]),
+            "mg_tune_cache_size": (_I, [_P(_I)]),
+            "mg_handle_params": (_I, [_V, _P(Params)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -164,6 +168,22 @@ def tile_shape(variant):
 def tune_cache_clear():
     """Forget the autotuner's cached launch shapes."""
     check(lib().mg_tune_cache_clear(), "mg_tune_cache_clear")
+
+
+def tune_cache_save(path):
+    check(lib().mg_tune_cache_save(os.fsencode(path)), "mg_tune_cache_save")
+
+
+def tune_cache_load(path) -> int:
+    n = ctypes.c_int()
+    check(lib().mg_tune_cache_load(os.fsencode(path), ctypes.byref(n)), "mg_tune_cache_load")
+    return n.value
+
+
+def tune_cache_size() -> int:
+    n = ctypes.c_int()
+    check(lib().mg_tune_cache_size(ctypes.byref(n)), "mg_tune_cache_size")
+    return n.value
 
 
 def _ptr(t, cells=None, dtype=None):
@@ -298,6 +318,12 @@ class Solver:
         if rc not in (OK, ENOTCONV, EDIVERGED):
             check(rc, "mg_step_host")
         return st
+
+    def resolved_params(self) -> dict:
+        """The handle's parameters with defaults resolved (e.g. inner_cycles)."""
+        p = Params()
+        check(lib().mg_handle_params(self._h, ctypes.byref(p)), "mg_handle_params")
+        return {f: getattr(p, f) for f, _ in Params._fields_}
 
     def tile_choice(self, kind, level) -> int:
         """Launch shape used for kernel `kind` (TILE_*) on `level`."""

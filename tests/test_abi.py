@@ -78,6 +78,28 @@ def test_tile_shapes_and_params():
     assert gbmg.lib().mg_tune_cache_clear() == gbmg.OK
 
 
+def test_tune_cache_file_roundtrip(tmp_path):
+    """Saved launch-shape choices load back; bad lines are skipped (host only)."""
+    src = tmp_path / "tune.txt"
+    src.write_text("0 1 3 128 128 128 1\n"      # half-sweep, FP32, periodic x y
+                   "1 0 0 64 48 32 5\n"         # restriction, FP64
+                   "garbage line\n"
+                   "0 1 0 30 16 16 2\n"         # rows of 30 cells: flat shapes do not fit
+                   "2 1 0 64 64 64 9\n")        # no such shape
+    gbmg.tune_cache_clear()
+    assert gbmg.tune_cache_size() == 0
+    assert gbmg.tune_cache_load(str(src)) == 2
+    assert gbmg.tune_cache_size() == 2
+    out = tmp_path / "out.txt"
+    gbmg.tune_cache_save(str(out))
+    assert sorted(out.read_text().split("\n")[:-1]) == ["0 1 3 128 128 128 1", "1 0 0 64 48 32 5"]
+    with pytest.raises(gbmg.MGError) as e:
+        gbmg.tune_cache_load(str(tmp_path / "missing.txt"))
+    assert e.value.code == gbmg.ENOTFOUND
+    gbmg.tune_cache_clear()
+    assert gbmg.tune_cache_size() == 0
+
+
 def test_no_gpu_fails_loudly():
     """Without a usable GPU the product path raises instead of computing on the host."""
     import torch

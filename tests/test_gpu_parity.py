@@ -306,9 +306,11 @@ def test_edge_cases():
         # the handle is still usable afterwards
         p5 = torch.zeros_like(b)
         assert S.solve(b, p5).status == gbmg.OK and torch.equal(p5, p1)
-    with solver_for(P, f, max_iters=2) as S:
-        st = S.solve(dev(P.rhs), torch.zeros(cells(P.shape), dtype=torch.float64, device="cuda"))
-        assert st.status == gbmg.ENOTCONV and st.iters == 2
+    for max_iters, inner in ((2, 2), (2, 3), (4, 3), (1, 1)):
+        with solver_for(P, f, max_iters=max_iters, inner_cycles=inner) as S:
+            st = S.solve(dev(P.rhs), torch.zeros(cells(P.shape), dtype=torch.float64, device="cuda"))
+            # the solve stops after the first whole refinement step that reaches max_iters
+            assert st.status == gbmg.ENOTCONV and st.iters == inner * -(-max_iters // inner)
     # invalid coefficients and sizes are refused
     bad = [a.copy() for a in f]
     bad[0][5, 5, 5] = -1.0
@@ -345,9 +347,12 @@ def test_profiling_counts_launches():
         # one launch per colour of each of the nu1 + nu2 sweeps per V-cycle on the finest level
         n, ms = S.profile_read(gbmg.K_SMOOTH, 0)
         assert n == st.iters * 2 * (2 + 2) and ms > 0.0
-        # one FP64 residual per refinement step (2 V-cycles each) plus the starting one
+        # one FP64 residual per refinement step (inner_cycles V-cycles each) plus the starting one
+        inner = S.resolved_params()["inner_cycles"]
+        assert inner == 3  # the mixed-precision default
         n, ms = S.profile_read(gbmg.K_RESIDUAL, 0)
-        assert n == st.iters // 2 + 1 and ms > 0.0
+        assert st.iters % inner == 0
+        assert n == st.iters // inner + 1 and ms > 0.0
 
 
 # ---------------------------------------------------------------------------

@@ -96,6 +96,24 @@ def test_unit_kernels_bitwise_equal_across_shapes(shape, bc):
             assert torch.equal(a, b), tiles
 
 
+def test_tune_cache_save_and_load(tmp_path):
+    shape, bc = (64, 48, 32), (1, 0, 0)
+    rho, _ = problem(shape, bc, 31)
+    f = [dev(a) for a in oracle.faces_from_density(shape, bc, rho)]
+    gbmg.tune_cache_clear()
+    with gbmg.Solver(shape, bc, faces=f, precision=gbmg.FP64) as A:
+        ca = [[A.tile_choice(k, l) for l in range(A.num_levels())] for k in range(3)]
+    assert gbmg.tune_cache_size() > 0
+    path = str(tmp_path / "tune.txt")
+    gbmg.tune_cache_save(path)
+    n = gbmg.tune_cache_size()
+    gbmg.tune_cache_clear()
+    assert gbmg.tune_cache_load(path) == n
+    with gbmg.Solver(shape, bc, faces=f, precision=gbmg.FP64) as B:
+        cb = [[B.tile_choice(k, l) for l in range(B.num_levels())] for k in range(3)]
+    assert ca == cb
+
+
 def test_autotuned_choices_are_cached_and_skip_tail_levels():
     shape, bc = (128, 128, 64), (1, 1, 0)
     rho, _ = problem(shape, bc, 21)
