@@ -54,6 +54,8 @@ WORKLOADS = {
                           desc="drop_film_256^3_1000to1: film depth 0.1 + drop R 0.125 at z 0.3, periodic x,y, Neumann z, Fourier-divergence RHS"),
     "drop_film_512": dict(kind="config3", n=512,
                           desc="drop_film_512^3_1000to1: film + drop + 0-4 droplets, periodic x,y, Neumann z, Fourier-divergence RHS"),
+    "drop_film_1024": dict(kind="config3", n=1024,
+                           desc="drop_film_1024^3_1000to1: film + drop + 0-4 droplets, periodic x,y, Neumann z, Fourier-divergence RHS"),
     "sphere_32": dict(kind="config1", n=32,
                       desc="sphere_32^3_1000to1: R 0.2 centred, Neumann walls, N(0,1) RHS"),
     "batch64": dict(kind="batch", n=0,
@@ -551,6 +553,19 @@ def main():
         torch.cuda.nvtx.range_pop()
     n_l, ms_l = S.profile_read(gbmg.K_SMOOTH, 0)
     n_r, ms_r = S.profile_read(gbmg.K_RESIDUAL, 0)
+    # the other level-0 kernels of the cycle, algorithmic bytes per finest cell:
+    # restriction reads x, b, 3 faces (FP32) and writes the coarse b (1/8 cell);
+    # prolongation reads and writes x and reads the coarse correction (1/8);
+    # the FP64 residual reads p, b0 and 3 FP64 faces and writes r (FP32)
+    per_kernel = {}
+    for name, kind, bpc, bound in (("restrict", gbmg.K_RESTRICT, 20.5, "hbm"),
+                                   ("prolong", gbmg.K_PROLONG, 8.5, "hbm"),
+                                   ("residual_fp64", gbmg.K_RESIDUAL, 44.0, "fp64 alu")):
+        n_k, ms_k = S.profile_read(kind, 0)
+        if n_k:
+            us = 1000.0 * ms_k / n_k
+            per_kernel[name] = {"avg_launch_us": us, "bytes_per_launch": bpc * N,
+                                "achieved_gbs": bpc * N / (us * 1e3), "bound": bound}
     S.profile(False)
     avg_s = ms_l / n_l / 1000.0
     # FP32 half-sweep, algorithmic: read x (all cells), b of the colour (half),
@@ -606,7 +621,8 @@ def main():
                                    "(%d threads x %d quads)" % ((v0,) + gbmg.tile_shape(v0)),
                          "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
                          "launches_timed": n_l, "peak_source": peak_kind,
-                         "residual_fp64_avg_launch_us": 1000.0 * ms_r / max(1, n_r)},
+                         "residual_fp64_avg_launch_us": 1000.0 * ms_r / max(1, n_r),
+                         "level0_kernels": {k: dict(v, frac=v["achieved_gbs"] / peak) for k, v in per_kernel.items()}},
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": results.get("clocks"),

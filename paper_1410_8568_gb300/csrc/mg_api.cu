@@ -314,6 +314,9 @@ int Plan::fill(mg_handle *const *handles, int count)
                 v.w[t][d] = mixed ? (void *)Lv.w32[d] : (void *)Lv.w64[d];
             }
             v.off[t] = off;
+            v.dx[t] = make_fastdiv((unsigned)Lv.n[0]);
+            v.dhx[t] = make_fastdiv(Lv.n[0] >= 2 ? (unsigned)(Lv.n[0] >> 1) : 1u);
+            v.dy[t] = make_fastdiv((unsigned)Lv.n[1]);
             off += 5 * (int)Lv.N;
             off = (off + 3) & ~3;
         }

@@ -157,6 +157,7 @@ struct TailView {
     void *b0;                // first tail level: right-hand side (in)
     const double *G;         // coarsest-level inverse
     const GridState *st;
+    FastDiv dx[kMaxTail], dhx[kMaxTail], dy[kMaxTail];  // division by n[t][0], n[t][0] / 2, n[t][1]
 };
 
 // Blocks of a launch over the cells of an n[0] x n[1] x n[2] level: a block is

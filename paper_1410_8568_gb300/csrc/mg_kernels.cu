@@ -353,15 +353,17 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
 // trilinear prolongation, and the exact coarsest solve e = -G b in FP64.
 // ---------------------------------------------------------------------------
 
-// index of cell m of colour `colour` on an nx x ny x nz level (nx even)
-__device__ __forceinline__ int colour_cell(int m, int colour, int nx, int ny, int &i, int &j, int &k)
+// n elements (n % 4 == 0, both pointers 16-byte aligned) from global to shared memory
+template <class T>
+__device__ __forceinline__ void stage(T *__restrict__ dst, const T *__restrict__ src, int n)
 {
-    const int hx = nx >> 1;
-    const int row = m / hx;
-    j = row % ny;
-    k = row / ny;
-    i = 2 * (m - row * hx) + ((colour + j + k) & 1);
-    return i + nx * row;
+    if constexpr (sizeof(T) == 4) {
+        for (int c = threadIdx.x; c < (n >> 2); c += blockDim.x)
+            reinterpret_cast<float4 *>(dst)[c] = reinterpret_cast<const float4 *>(src)[c];
+    } else {
+        for (int c = threadIdx.x; c < (n >> 1); c += blockDim.x)
+            reinterpret_cast<double2 *>(dst)[c] = reinterpret_cast<const double2 *>(src)[c];
+    }
 }
 
 template <class T>
@@ -420,31 +422,31 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
     const TailView &V = tv[blockIdx.x];
     if (!V.st->active) return;
     const int nt = V.nt, per = V.per;
-    // stage the faces of every tail level and the right-hand side of the first
-    for (int t = 0; t < nt; t++) {
+    // stage the faces of every tail level but the coarsest (solved with G) and
+    // the right-hand side of the first; levels above the coarsest have even
+    // sizes, so N % 8 == 0 and the slab offsets keep 16-byte alignment
+    for (int t = 0; t + 1 < nt; t++) {
         const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
         T *base = sm + V.off[t];
-        for (int d = 0; d < 3; d++) {
-            const T *g = (const T *)V.w[t][d];
-            T *s = base + (2 + d) * N;
-            for (int c = threadIdx.x; c < N; c += blockDim.x) s[c] = g[c];
-        }
+        for (int d = 0; d < 3; d++) stage(base + (2 + d) * N, (const T *)V.w[t][d], N);
     }
-    {
-        const int N = V.n[0][0] * V.n[0][1] * V.n[0][2];
-        const T *g = (const T *)V.b0;
-        T *s = sm + V.off[0] + N;
-        for (int c = threadIdx.x; c < N; c += blockDim.x) s[c] = g[c];
-    }
+    stage(sm + V.off[0] + V.n[0][0] * V.n[0][1] * V.n[0][2], (const T *)V.b0,
+          V.n[0][0] * V.n[0][1] * V.n[0][2]);
     __syncthreads();
 
     auto half = [&](int t, int colour) {
         const int nx = V.n[t][0], ny = V.n[t][1], nz = V.n[t][2], N = nx * ny * nz;
         T *x = sm + V.off[t];
         const T *b = x + N, *wx = x + 2 * N, *wy = x + 3 * N, *wz = x + 4 * N;
+        const int hx = nx >> 1;
         for (int m = threadIdx.x; m < (N >> 1); m += blockDim.x) {
-            int i, j, k;
-            const int c = colour_cell(m, colour, nx, ny, i, j, k);
+            // m-th cell of the colour: rows of hx cells, the colour's cells at
+            // every other i starting from (colour + j + k) & 1
+            const int row = fdiv(m, V.dhx[t]);
+            const int k = fdiv(row, V.dy[t]);
+            const int j = row - k * ny;
+            const int i = 2 * (m - row * hx) + ((colour + j + k) & 1);
+            const int c = i + nx * row;
             const T xc = x[c];
             T d;
             const T f = smem_flux(x, wx, wy, wz, nx, ny, nz, per, i, j, k, c, xc, d);
@@ -472,7 +474,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
         const T *b = x + N, *wx = x + 2 * N, *wy = x + 3 * N, *wz = x + 4 * N;
         T *bc = sm + V.off[t + 1] + NC;
         for (int C = threadIdx.x; C < NC; C += blockDim.x) {
-            const int I = C % ncx, J = (C / ncx) % ncy, K = C / (ncx * ncy);
+            const int crow = fdiv(C, V.dx[t + 1]);
+            const int K = fdiv(crow, V.dy[t + 1]);
+            const int I = C - crow * ncx, J = crow - K * ncy;
             T s = T(0);
             for (int dz = 0; dz < 2; dz++)
                 for (int dy = 0; dy < 2; dy++)
@@ -508,8 +512,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
         T *x = sm + V.off[t];
         const T *ec = sm + V.off[t + 1];
         for (int c = threadIdx.x; c < N; c += blockDim.x) {
-            const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
-            x[c] += prolong_at(ec, nc, per, i, j, k);
+            const int row = fdiv(c, V.dx[t]);
+            const int k = fdiv(row, V.dy[t]);
+            x[c] += prolong_at(ec, nc, per, c - row * nx, row - k * ny, k);
         }
         __syncthreads();
         for (int it = 0; it < nu2; it++) {
@@ -517,12 +522,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
             half(t, 1);
         }
     }
-    {
-        const int N = V.n[0][0] * V.n[0][1] * V.n[0][2];
-        T *g = (T *)V.x0;
-        const T *s = sm + V.off[0];
-        for (int c = threadIdx.x; c < N; c += blockDim.x) g[c] = s[c];
-    }
+    stage((T *)V.x0, sm + V.off[0], V.n[0][0] * V.n[0][1] * V.n[0][2]);
 }
 
 // ---------------------------------------------------------------------------

@@ -383,7 +383,7 @@ def _mode(n, k, bcv, device):
     return torch.cos(2 * math.pi * k * i / n), 4.0 * math.sin(math.pi * k / n) ** 2
 
 
-@pytest.mark.parametrize("n,bc", [(512, (1, 1, 0)), (384, (0, 0, 0))])
+@pytest.mark.parametrize("n,bc", [(512, (1, 1, 0)), (384, (0, 0, 0)), (1024, (1, 1, 0))])
 def test_full_size_discrete_eigenvector(n, bc):
     """alpha = 1: b = lambda v has the exact solution v (discrete cosine mode)."""
     shape = (n, n, n)
