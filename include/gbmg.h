@@ -341,9 +341,11 @@ int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double
  * coarsest level and on levels run by the bottom-of-cycle kernel). */
 int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant);
 
-/* Threads per block and items (4-cell quads; restriction: coarse cell pairs)
- * per thread of shape `variant`; variant 0 is the row tiling (a warp per row
- * of up to 32 quads, 8 rows per block: reports 256 threads, 1 item). */
+/* Threads per block and items per thread of shape `variant`: an item is a
+ * 4-cell quad of the half-sweep, or a coarse cell pair of the restriction and
+ * prolongation (the quad of each of the 2 x 2 fine rows above it).  Variant 0
+ * is the row tiling (a warp per row of up to 32 quads, 8 rows per block:
+ * reports 256 threads, 1 item). */
 int mg_tile_shape(int variant, int *threads, int *items_per_thread);
 
 /* Forget every cached choice (the next mg_create times again). */

@@ -274,7 +274,7 @@ int Plan::fill(mg_handle *const *handles, int count)
             v.g = g;
             v.st = h->state;
             fill_fastdiv(v);
-            sf.push_back(sf.back() + prolong_blocks_v(F.n, var[MG_TILE_PROLONG]));
+            sf.push_back(sf.back() + prolong_blocks_v(F.n, C.n, var[MG_TILE_PROLONG]));
             sc.push_back(sc.back() + restrict_blocks_v(F.n, C.n, var[MG_TILE_RESTRICT]));
             sh.push_back(sh.back() + half_sweep_blocks_v(F.n, var[MG_TILE_HALF]));
             cnt++;

@@ -72,8 +72,9 @@ __host__ __device__ __forceinline__ int fdiv(int n, const FastDiv &f)
 // (chosen per level by the autotuner).  Variant 0 is the row tiling: a warp
 // owns one grid row of up to 32 quads (or 64 cells), 8 rows per 256-thread
 // block.  Variants 1.. are flat tilings for rows of a multiple of 4 cells: the
-// level's quads (restriction: coarse cell pairs) are numbered row by row and a
-// block of B threads owns Q * B consecutive ones, thread t the items t, t + B,
+// level's quads (restriction and prolongation: coarse cell pairs, a pair
+// covering one quad in each of the 2 x 2 fine rows above it) are numbered row
+// by row and a block of B threads owns Q * B consecutive ones, thread t the items t, t + B,
 // ...; short rows then fill whole warps, and B and Q set the blocks per SM and
 // the loads each thread has in flight.
 constexpr int kTileVariants = 7;

@@ -167,7 +167,7 @@ __device__ __forceinline__ Tile fine_tile(const int n[3], int lb)
 //        kOuter      the relaxed cells' final values are also added to the FP64
 //                    iterate (last red and last black half-sweep of a
 //                    refinement step on the finest level).
-template <class T>
+template <class T, bool OUT>
 __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
                                                    const int *__restrict__ start, int count,
                                                    int colour, T omega, int flags,
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
     const T *__restrict__ wy = (const T *)L.w[1];
     const T *__restrict__ wz = (const T *)L.w[2];
     const bool zero = flags & kZeroGuess;
-    double *__restrict__ pout = (flags & kOuter) ? ov[L.g].p : nullptr;
+    double *__restrict__ pout = OUT ? ov[L.g].p : nullptr;
     const long long sy = nx, sz = (long long)nx * ny;
     const int lb = blockIdx.x - start[e];
 
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
                 v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
             }
             x[c] = v;
-            if (pout) pout[c] += (double)v;
+            if constexpr (OUT) pout[c] += (double)v;
         }
         return;
     }
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
     if (row >= ny * nz) return;
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
-    half_quad<T>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, pout);
+    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, pout);
 }
 
 // Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64
@@ -304,7 +304,7 @@ int restrict_blocks(const int n[3], const int nc[3])
 // no post-smoothing, the refinement step ends here, so p += (double) x too.
 // ---------------------------------------------------------------------------
 
-template <class T>
+template <class T, bool OUT>
 __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
                                                       const int *__restrict__ start, int count,
                                                       const OuterView *__restrict__ ov,
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
     const T *ec = (const T *)L.xc;
     T *x = (T *)L.x;
     const int lb = blockIdx.x - start[e];
-    double *pout = outer_update ? ov[L.g].p : nullptr;
+    double *pout = OUT ? ov[L.g].p : nullptr;
     if ((nx & 3) == 0) {
         const int nq = nx >> 2;
         const int xt_n = (nq + 31) >> 5;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
-        prolong_quad<T>(L, row, row % ny, row / ny, qx, pout);
+        prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, pout);
         return;
     }
     const Tile t = fine_tile(L.n, lb);
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         const long long c = (long long)nx * t.row + i;
         const T xn = x[c] + prolong_at(ec, L.nc, L.per, i, t.j, t.k);
         x[c] = xn;
-        if (pout) pout[c] += (double)xn;
+        if constexpr (OUT) pout[c] += (double)xn;
     }
 }
 
@@ -989,7 +989,10 @@ void launch_loop_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStr
 template <class T>
 void launch_half_rows(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
-    k_half<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, ov);
+    if (flags & kOuter)
+        k_half<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, ov);
+    else
+        k_half<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, ov);
 }
 template <class T>
 void launch_restrict_rows(const Table &tb, cudaStream_t s)
@@ -999,7 +1002,10 @@ void launch_restrict_rows(const Table &tb, cudaStream_t s)
 template <class T>
 void launch_prolong_rows(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
 {
-    k_prolong<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
+    if (outer_update)
+        k_prolong<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
+    else
+        k_prolong<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
 }
 template <class T>
 void launch_tail(const TailView *tv, int count, size_t smem, double omega, int nu1, int nu2, cudaStream_t s)

@@ -53,7 +53,7 @@ int prolong_blocks(const int n[3]);
 bool tile_fits(const int n[3], int v);
 int half_sweep_blocks_v(const int n[3], int v);
 int restrict_blocks_v(const int n[3], const int nc[3], int v);
-int prolong_blocks_v(const int n[3], int v);
+int prolong_blocks_v(const int n[3], const int nc[3], int v);
 // launchers that dispatch on Table::variant (mg_tiles.cu) ...
 template <class T> void launch_half(const Table &, int colour, double omega, int flags,
                                     const OuterView *ov, cudaStream_t);

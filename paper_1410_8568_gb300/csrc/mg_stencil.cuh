@@ -100,7 +100,10 @@ __device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn
     return d > T(0) ? xc + omega * relax_div(f - bc, d) : xc;
 }
 
-template <class T>
+// OUT: also add the relaxed values to the FP64 iterate pout (a compile-time
+// choice: a run-time test would leave predicated FP64 instructions in every
+// launch, and FP64 throughput on this GPU is a small fraction of FP32's).
+template <class T, bool OUT>
 __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T *wy, const T *wz,
                                           int nx, int ny, int nz, int per, int row, int j, int k,
                                           int qx, int colour, T omega, bool zero, double *pout)
@@ -165,22 +168,37 @@ __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T
     out.v[2] = par ? xq.v[2] : v1;
     out.v[3] = par ? v1 : xq.v[3];
     stq(x + c, out);
-    if (pout) {
+    if constexpr (OUT) {
         pout[c0] += (double)v0;
         pout[c0 + 2] += (double)v1;
     }
 }
 
+// Coarse partner of fine index i along an axis of nc coarse cells: the coarse
+// cell across the coarse face nearer to the fine centre.  It lies one step
+// outside [0, nc) at most: wrap on a periodic axis, else (wall) the cell itself.
 __device__ __forceinline__ int partner(int i, int nc, int periodic)
 {
     const int I = i >> 1;
-    int J = (i & 1) ? I + 1 : I - 1;
-    if (J < 0 || J >= nc) J = periodic ? (J + nc) % nc : I;  // wrap, or mirror at a wall
+    const int J = (i & 1) ? I + 1 : I - 1;
+    if (J < 0) return periodic ? nc - 1 : I;
+    if (J >= nc) return periodic ? 0 : I;
     return J;
 }
 
-// (4) trilinear prolongation at fine cell (i,j,k): weights 3/4 on the coarse
-// cell containing the fine centre and 1/4 on its partner, per axis.
+// Linear interpolation to a fine centre between the coarse value it lies over
+// (weight 3/4) and its partner across the nearer coarse face (1/4), with one
+// explicit rounding order so that every kernel that prolongs gets bitwise the
+// same value for a cell.
+template <class T>
+__device__ __forceinline__ T lin(T own, T par)
+{
+    return fma(T(0.25), par, T(0.75) * own);
+}
+
+// (4) trilinear prolongation at fine cell (i,j,k): lin along x on the 4 coarse
+// rows (own/partner in y and z), then along y, then along z; the weights
+// multiply out to 27/9/3/1 over 64.
 template <class T>
 __device__ __forceinline__ T prolong_at(const T *__restrict__ ec, const int nc[3], int per, int i,
                                         int j, int k)
@@ -188,22 +206,11 @@ __device__ __forceinline__ T prolong_at(const T *__restrict__ ec, const int nc[3
     const int I0 = i >> 1, I1 = partner(i, nc[0], per & 1);
     const int J0 = j >> 1, J1 = partner(j, nc[1], per & 2);
     const int K0 = k >> 1, K1 = partner(k, nc[2], per & 4);
-    const int r00 = nc[0] * (J0 + nc[1] * K0);
-    const int r10 = nc[0] * (J1 + nc[1] * K0);
-    const int r01 = nc[0] * (J0 + nc[1] * K1);
-    const int r11 = nc[0] * (J1 + nc[1] * K1);
-    const T w0 = T(0.75), w1 = T(0.25);
-    // order: z outer, y, x inner; weight product (wx * wy) * wz
-    T s = T(0);
-    s += w0 * w0 * w0 * ec[r00 + I0];
-    s += w1 * w0 * w0 * ec[r00 + I1];
-    s += w0 * w1 * w0 * ec[r10 + I0];
-    s += w1 * w1 * w0 * ec[r10 + I1];
-    s += w0 * w0 * w1 * ec[r01 + I0];
-    s += w1 * w0 * w1 * ec[r01 + I1];
-    s += w0 * w1 * w1 * ec[r11 + I0];
-    s += w1 * w1 * w1 * ec[r11 + I1];
-    return s;
+    const T *r00 = ec + nc[0] * (J0 + nc[1] * K0), *r10 = ec + nc[0] * (J1 + nc[1] * K0);
+    const T *r01 = ec + nc[0] * (J0 + nc[1] * K1), *r11 = ec + nc[0] * (J1 + nc[1] * K1);
+    const T y0 = lin(lin(r00[I0], r00[I1]), lin(r10[I0], r10[I1]));
+    const T y1 = lin(lin(r01[I0], r01[I1]), lin(r11[I0], r11[I1]));
+    return lin(y0, y1);
 }
 
 // Residual of the 4 cells of the quad at (i0, j, k): b - A x, faces in the
@@ -275,22 +282,90 @@ __device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int 
     bc[1] = s1 * T(0.125);
 }
 
-// x += P e_c on the aligned quad (4 qx .. 4 qx + 3, j, k) of row `row`.
+// Interpolation along x on one coarse row `er` for the 4 fine cells of the quad
+// over coarse cells I0 = 2 qx and I0 + 1: own/partner pairs (I0, Im), (I0, I0+1),
+// (I0+1, I0), (I0+1, Ip), Im / Ip the partners of fine cells 4 qx / 4 qx + 3.
 template <class T>
+__device__ __forceinline__ void lin_x(const T *__restrict__ er, int Im, int I0, int Ip, T out[4])
+{
+    const T a = er[Im], b = er[I0], c = er[I0 + 1], d = er[Ip];
+    out[0] = lin(b, a);
+    out[1] = lin(b, c);
+    out[2] = lin(c, b);
+    out[3] = lin(c, d);
+}
+
+// x += P e_c on the aligned quad (4 qx .. 4 qx + 3, j, k) of row `row`: same
+// rounding order as prolong_at.  OUT: also p += x in FP64 (see half_quad).
+template <class T, bool OUT>
 __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j, int k, int qx,
                                              double *__restrict__ pout)
 {
-    const int nx = L.n[0];
-    const T *ec = (const T *)L.xc;
+    const int nx = L.n[0], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
+    const T *__restrict__ ec = (const T *)L.xc;
     T *x = (T *)L.x;
     const int c = row * nx + 4 * qx;
+    const int I0 = 2 * qx;
+    const int Im = partner(4 * qx, ncx, per & 1), Ip = partner(4 * qx + 3, ncx, per & 1);
+    const int J0 = j >> 1, J1 = partner(j, ncy, per & 2);
+    const int K0 = k >> 1, K1 = partner(k, ncz, per & 4);
+    T a00[4], a10[4], a01[4], a11[4];
+    lin_x(ec + ncx * (J0 + ncy * K0), Im, I0, Ip, a00);
+    lin_x(ec + ncx * (J1 + ncy * K0), Im, I0, Ip, a10);
+    lin_x(ec + ncx * (J0 + ncy * K1), Im, I0, Ip, a01);
+    lin_x(ec + ncx * (J1 + ncy * K1), Im, I0, Ip, a11);
     Quad<T> xq = ldq(x + c);
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-        xq.v[u] += prolong_at(ec, L.nc, L.per, 4 * qx + u, j, k);
-        if (pout) pout[c + u] += (double)xq.v[u];
+        xq.v[u] += lin(lin(a00[u], a10[u]), lin(a01[u], a11[u]));
+        if constexpr (OUT) pout[c + u] += (double)xq.v[u];
     }
     stq(x + c, xq);
+}
+
+// x += P e_c on the 2 x 2 fine rows (2J + dy, 2K + dz) above coarse row (J, K),
+// on the quad over the coarse cell pair (2P, 2P + 1).  The 4 fine rows share
+// coarse rows: they use J and its two partners Jm, Jp (and K, Km, Kp), 9 coarse
+// rows in all instead of 16.  Same rounding order as prolong_at.
+template <class T, bool OUT>
+__device__ __forceinline__ void prolong_block(const LevelView &L, int J, int K, int P,
+                                              double *__restrict__ pout)
+{
+    const int nx = L.n[0], ny = L.n[1], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
+    const T *__restrict__ ec = (const T *)L.xc;
+    T *x = (T *)L.x;
+    const int I0 = 2 * P;
+    const int Im = partner(4 * P, ncx, per & 1), Ip = partner(4 * P + 3, ncx, per & 1);
+    const int Jr[3] = {partner(2 * J, ncy, per & 2), J, partner(2 * J + 1, ncy, per & 2)};
+    const int Kr[3] = {partner(2 * K, ncz, per & 4), K, partner(2 * K + 1, ncz, per & 4)};
+    // along x then y for each coarse plane Km, K, Kp: ey[kz][dy][u]
+    T ey[3][2][4];
+#pragma unroll
+    for (int kz = 0; kz < 3; kz++) {
+        T am[4], a0[4], ap[4];
+        const T *plane = ec + ncx * ncy * Kr[kz];
+        lin_x(plane + ncx * Jr[0], Im, I0, Ip, am);
+        lin_x(plane + ncx * Jr[1], Im, I0, Ip, a0);
+        lin_x(plane + ncx * Jr[2], Im, I0, Ip, ap);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            ey[kz][0][u] = lin(a0[u], am[u]);  // fine row 2J: partner J - 1 side
+            ey[kz][1][u] = lin(a0[u], ap[u]);  // fine row 2J + 1: partner J + 1 side
+        }
+    }
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++) {
+            const int c = nx * ((2 * J + dy) + ny * (2 * K + dz)) + 4 * P;
+            Quad<T> xq = ldq(x + c);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                xq.v[u] += lin(ey[1][dy][u], ey[dz ? 2 : 0][dy][u]);
+                if constexpr (OUT) pout[c + u] += (double)xq.v[u];
+            }
+            stq(x + c, xq);
+        }
 }
 
 }  // namespace gbmg

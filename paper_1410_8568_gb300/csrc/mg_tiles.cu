@@ -15,7 +15,7 @@ namespace gbmg {
 // Block lb of a table entry owns items [lb Q B, (lb + 1) Q B); thread t handles
 // lb Q B + q B + t for q < Q.  Items are numbered row by row, so consecutive
 // threads touch consecutive 16-byte vectors.
-template <class T, int B, int Q>
+template <class T, int B, int Q, bool OUT>
 __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ lv,
                                                  const int *__restrict__ start, int count,
                                                  int colour, T omega, int flags,
@@ -28,14 +28,14 @@ __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ l
     const int items = nq * ny * nz;
     const int lb = blockIdx.x - start[e];
     const bool zero = flags & kZeroGuess;
-    double *pout = (flags & kOuter) ? ov[L.g].p : nullptr;
+    double *pout = OUT ? ov[L.g].p : nullptr;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
         const int g = (lb * Q + q) * B + (int)threadIdx.x;
         if (g >= items) return;
         const int row = fdiv(g, L.dq);
         const int k = fdiv(row, L.dy);
-        half_quad<T>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
+        half_quad<T, OUT>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
                      (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
                      omega, zero, pout);
     }
@@ -61,26 +61,27 @@ __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict
     }
 }
 
-template <class T, int B, int Q>
+template <class T, int B, int Q, bool OUT>
 __global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict__ lv,
                                                     const int *__restrict__ start, int count,
                                                     const OuterView *__restrict__ ov,
                                                     int outer_update)
 {
+    // items: coarse cell pairs; each covers a quad of the 2 x 2 fine rows above it
     const int e = find_entry(start, count);
     const LevelView &L = lv[e];
     if (!L.st->active) return;
-    const int nq = L.n[0] >> 2, ny = L.n[1];
-    const int items = nq * ny * L.n[2];
+    const int np = L.nc[0] >> 1, ncy = L.nc[1];
+    const int items = np * ncy * L.nc[2];
     const int lb = blockIdx.x - start[e];
-    double *pout = outer_update ? ov[L.g].p : nullptr;
+    double *pout = OUT ? ov[L.g].p : nullptr;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
         const int g = (lb * Q + q) * B + (int)threadIdx.x;
         if (g >= items) return;
-        const int row = fdiv(g, L.dq);
-        const int k = fdiv(row, L.dy);
-        prolong_quad<T>(L, row, row - k * ny, k, g - row * nq, pout);
+        const int crow = fdiv(g, L.dp);
+        const int K = fdiv(crow, L.dcy);
+        prolong_block<T, OUT>(L, crow - K * ncy, K, g - crow * np, pout);
     }
 }
 
@@ -119,10 +120,10 @@ int half_sweep_blocks_v(const int n[3], int v)
     return flat_blocks((long long)(n[0] >> 2) * n[1] * n[2], v);
 }
 
-int prolong_blocks_v(const int n[3], int v)
+int prolong_blocks_v(const int n[3], const int nc[3], int v)
 {
     if (v == 0) return prolong_blocks(n);
-    return flat_blocks((long long)(n[0] >> 2) * n[1] * n[2], v);
+    return flat_blocks((long long)(nc[0] >> 1) * nc[1] * nc[2], v);
 }
 
 int restrict_blocks_v(const int n[3], const int nc[3], int v)
@@ -137,8 +138,12 @@ void launch_half(const Table &tb, int colour, double omega, int flags, const Out
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_half_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega,
-                                                              flags, ov);
+        if (flags & kOuter)
+            k_half_flat<T, ts.B, ts.Q, true><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
+                                                                        (T)omega, flags, ov);
+        else
+            k_half_flat<T, ts.B, ts.Q, false><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
+                                                                         (T)omega, flags, ov);
     });
     if (!flat) launch_half_rows<T>(tb, colour, omega, flags, ov, s);
 }
@@ -160,8 +165,12 @@ void launch_prolong(const Table &tb, const OuterView *ov, int outer_update, cuda
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_prolong_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, ov,
-                                                                 outer_update);
+        if (outer_update)
+            k_prolong_flat<T, ts.B, ts.Q, true><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, ov,
+                                                                           outer_update);
+        else
+            k_prolong_flat<T, ts.B, ts.Q, false><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, ov,
+                                                                            outer_update);
     });
     if (!flat) launch_prolong_rows<T>(tb, ov, outer_update, s);
 }

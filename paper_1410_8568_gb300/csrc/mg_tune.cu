@@ -65,7 +65,7 @@ void fill_fastdiv(LevelView &v)
 int kernel_blocks(int kind, const int n[3], const int nc[3], int v)
 {
     return kind == MG_TILE_RESTRICT ? restrict_blocks_v(n, nc, v)
-         : kind == MG_TILE_PROLONG  ? prolong_blocks_v(n, v)
+         : kind == MG_TILE_PROLONG  ? prolong_blocks_v(n, nc, v)
                                     : half_sweep_blocks_v(n, v);
 }
 
