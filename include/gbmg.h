@@ -81,6 +81,9 @@ extern "C" {
 #define MG_PREC_FP64 0  /* every level in FP64 */
 #define MG_PREC_MIXED 1 /* FP32 V-cycles inside FP64 iterative refinement */
 
+#define MG_PROLONG_TRILINEAR 0 /* prolongation weights 27/9/3/1 over 64 */
+#define MG_PROLONG_FLUX 1      /* Sec. 2.3 item 4, Eqs. 13-14: cell flux conservation */
+
 #define MG_FACE_HARMONIC 0   /* Eqs. 11-12: 2 a_L a_R / (a_L + a_R), a = 1/rho */
 #define MG_FACE_ARITHMETIC 1 /* (a_L + a_R) / 2 */
 
@@ -110,6 +113,11 @@ typedef struct {
     int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
     int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1;
                           0 (default) = 3 in MIXED precision, 2 in FP64 */
+    int prolongation;  /* MG_PROLONG_TRILINEAR (default) or MG_PROLONG_FLUX: the coarse error
+                          at a coarse face, edge or node is the mean of the coarse cells meeting
+                          there weighted by their cell coefficient (flux continuity, Eq. 13), a
+                          fine cell takes the mean of its octant's 8 corner values; the cell
+                          coefficient is the mean alpha of the cell's non-wall faces */
     int tiles;         /* launch shapes of the V-cycle kernels: MG_TILES_AUTO (autotuned per
                           level), MG_TILES_ROWS, or a variant 1 .. MG_TILE_VARIANTS - 1 for
                           every level whose rows are a multiple of 4 cells */
@@ -261,6 +269,12 @@ int mg_level_shape(const mg_handle *h, int level, int *nx, int *ny, int *nz);
 
 /* Scaled coefficients w_d = alpha_d / h_d^2 of `level` (FP64, DEVICE out). */
 int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double *wz);
+
+/* Cell coefficients of `level` used by the flux-conserving prolongation
+ * (MG_PROLONG_FLUX, Sec. 2.3 item 4): the mean alpha of each cell's faces that
+ * are not walls, from the level's face coefficients; FP64, DEVICE buffer of the
+ * level's cells.  Synchronous on the handle's stream.  Any prolongation mode. */
+int mg_level_cell_alpha(const mg_handle *h, int level, double *alpha);
 
 /* y = A_level x (Eq. 10 / h^2 on that level). */
 int mg_apply(mg_handle *h, int level, int prec, const void *x, void *y);

@@ -47,9 +47,11 @@ def lib():
         L.oracle_coarsen_faces.argtypes = [G, P, P, P, P, P, P]
         L.oracle_restrict.argtypes = [G, P, P]
         L.oracle_prolong_add.argtypes = [G, P, P]
+        L.oracle_cell_alpha.argtypes = [G, P, P, P, P]
+        L.oracle_prolong_flux_add.argtypes = [G, P, P, P]
         L.oracle_coarse_solve.argtypes = [G, P, P, P, P, P]
         L.oracle_solve.argtypes = [G, P, P, P, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, P,
+                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P,
                                    ctypes.POINTER(ctypes.c_int)]
         L.oracle_gamma.argtypes = [P, ctypes.c_int]
         L.oracle_gamma.restype = ctypes.c_double
@@ -160,6 +162,28 @@ def prolong_add(shape, bc, e_coarse, x):
     return x
 
 
+def cell_alpha(shape, bc, faces, length=(1.0, 1.0, 1.0)):
+    """Cell coefficient of the flux-conserving prolongation: mean alpha of the
+    cell's non-wall faces."""
+    g = grid(shape, bc, length)
+    f = [_arr(a, shape) for a in faces]
+    out = np.empty(_cells(shape))
+    lib().oracle_cell_alpha(ctypes.byref(g), *[_ptr(a) for a in f], _ptr(out))
+    return out
+
+
+def prolong_flux_add(shape, bc, alpha_coarse, e_coarse, x):
+    """x + flux-conserving prolongation (Eqs. 13-14) of the coarse error, with
+    the coarse cell coefficients alpha_coarse (returns a new array)."""
+    g = grid(shape, bc)
+    cs = coarse_shape(shape)
+    a = _arr(alpha_coarse, cs)
+    e = _arr(e_coarse, cs)
+    x = np.array(_arr(x, shape), copy=True)
+    lib().oracle_prolong_flux_add(ctypes.byref(g), _ptr(a), _ptr(e), _ptr(x))
+    return x
+
+
 def coarse_solve(shape, bc, faces, r, length=(1.0, 1.0, 1.0)):
     g = grid(shape, bc, length)
     f = [_arr(a, shape) for a in faces]
@@ -187,9 +211,13 @@ class SolveResult:
         return float(self.history[-1] / self._bnorm) if self._bnorm else 0.0
 
 
+PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
+
+
 def solve(shape, bc, faces, b, tol=1e-10, max_cycles=200, nu1=2, nu2=2, omega=1.0,
-          x0=None, stagnate=False, length=(1.0, 1.0, 1.0)) -> SolveResult:
-    """V(nu1, nu2) multigrid to ||b - A x|| <= tol ||b|| (b projected to zero mean).
+          x0=None, stagnate=False, length=(1.0, 1.0, 1.0), prolong=PROLONG_TRILINEAR) -> SolveResult:
+    """V(nu1, nu2) multigrid to ||b - A x|| <= tol ||b|| (b projected to zero mean);
+    ``prolong`` selects trilinear or flux-conserving (Eqs. 13-14) prolongation.
 
     With ``stagnate=True`` the iteration continues to rounding level (stops
     when three cycles in a row have not lowered the best residual by 10%): the
@@ -202,7 +230,7 @@ def solve(shape, bc, faces, b, tol=1e-10, max_cycles=200, nu1=2, nu2=2, omega=1.
     hist = np.zeros(max_cycles + 1)
     nc = ctypes.c_int(0)
     st = lib().oracle_solve(ctypes.byref(g), *[_ptr(a) for a in f], _ptr(b), _ptr(x), tol,
-                            max_cycles, nu1, nu2, omega, 1 if stagnate else 0, _ptr(hist),
+                            max_cycles, nu1, nu2, omega, 1 if stagnate else 0, int(prolong), _ptr(hist),
                             ctypes.byref(nc))
     if st < 0:
         raise RuntimeError("oracle solve failed: %d" % st)
@@ -212,10 +240,11 @@ def solve(shape, bc, faces, b, tol=1e-10, max_cycles=200, nu1=2, nu2=2, omega=1.
     return res
 
 
-def solve_exact(shape, bc, faces, b, length=(1.0, 1.0, 1.0), max_cycles=400, nu1=2, nu2=2):
+def solve_exact(shape, bc, faces, b, length=(1.0, 1.0, 1.0), max_cycles=400, nu1=2, nu2=2,
+                prolong=PROLONG_TRILINEAR):
     """p*: the oracle multigrid iterated until the residual stops falling."""
     return solve(shape, bc, faces, b, tol=0.0, max_cycles=max_cycles, nu1=nu1, nu2=nu2,
-                 stagnate=True, length=length)
+                 stagnate=True, length=length, prolong=prolong)
 
 
 def gamma(history) -> float:

@@ -17,7 +17,8 @@
  *   (1) cell-centred second-order differences of Eq. 9  -> oracle_apply
  *   (2) harmonic face coefficient (Eqs. 11-12)          -> oracle_faces_from_density
  *   (3) restriction of the residual                      -> oracle_restrict (8-child mean)
- *   (4) prolongation of the coarse error                 -> oracle_prolong_add (trilinear)
+ *   (4) prolongation of the coarse error                 -> oracle_prolong_add (trilinear),
+ *       or by cell flux conservation (Eqs. 13-14)       -> oracle_prolong_flux_add
  *   (5) red-black relaxation                             -> oracle_smooth_colour
  *   (6) exact solve of the error on the coarsest grid    -> oracle_coarse_solve (dense LU)
  * and the stopping test and average reduction rate of Eq. 15.
@@ -35,7 +36,20 @@
  *    are those with (i+j+k) even and are relaxed first;
  *  - the coarsest-grid solve (GMRES in the paper, (6)) is an exact dense solve
  *    of the bordered system [-A 1; 1^T 0][e; l] = [-r; 0];
- *  - coarsening of all three axes continues while every axis is even and > 4.
+ *  - coarsening of all three axes continues while every axis is even and > 4;
+ *  - flux-conserving prolongation (4), Eqs. 13-14: Eq. 13 as printed does not
+ *    give a convex weighting; it is read as continuity of the flux alpha de/dx
+ *    across the coarse face between cells L and R, which gives the face value
+ *    e_f = (alpha_L e_L + alpha_R e_R) / (alpha_L + alpha_R).  The values at
+ *    the edges and nodes (the "analogous expressions" the paper mentions for
+ *    3D) are the alpha-weighted means of the 4 and 8 coarse cells that meet
+ *    there.  A fine cell occupies one octant of its coarse cell; its value is
+ *    the mean of the 8 corner values of that octant (coarse centre, 3 face
+ *    centres, 3 edge midpoints, the node), i.e. trilinear interpolation at the
+ *    octant's centre.  The cell coefficient alpha_c of a coarse cell, which the
+ *    paper does not define, is the mean of the coefficients of its faces that
+ *    are not walls.  Walls mirror (the partner is the cell itself), periodic
+ *    axes wrap.  For a constant alpha this is exactly the trilinear rule.
  *
  * Layout (the library's documented layout, shared as an interface only):
  * cell (i,j,k) of an nx*ny*nz grid is element i + nx*(j + ny*k).  Face array
@@ -366,6 +380,62 @@ void oracle_prolong_add(const og_grid *g, const double *e, double *x)
             }
 }
 
+/* Cell coefficient used by the flux-conserving prolongation: the mean of the
+ * alpha of the cell's faces that are not walls (1 for a cell with none). */
+void oracle_cell_alpha(const og_grid *g, const double *ax, const double *ay, const double *az,
+                       double *out)
+{
+    const double *a[3] = {ax, ay, az};
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g->n[2]; k++)
+        for (int j = 0; j < g->n[1]; j++)
+            for (int i = 0; i < g->n[0]; i++) {
+                double s = 0.0;
+                int m = 0;
+                for (int d = 0; d < 3; d++)
+                    for (int side = -1; side <= 1; side += 2) {
+                        long nb;
+                        double alpha = face_coef(g, a, i, j, k, d, side, &nb);
+                        if (nb < 0) continue; /* wall */
+                        s += alpha;
+                        m++;
+                    }
+                out[cell_index(g, i, j, k)] = m ? s / m : 1.0;
+            }
+}
+
+/* x_fine += flux-conserving interpolation of the coarse error e (Eqs. 13-14,
+ * read as above).  ac = cell coefficients of the coarse grid.  For a fine cell,
+ * the 8 coarse cells of its octant's corners are C (the coarse cell holding
+ * it) shifted by its partner along any subset S of the axes; the corner value
+ * of S is the alpha-weighted mean of the 2^|S| cells obtained from C by
+ * shifting along any subset of S. */
+void oracle_prolong_flux_add(const og_grid *g, const double *ac, const double *e, double *x)
+{
+    og_grid gc;
+    oracle_coarse_grid(g, &gc);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g->n[2]; k++)
+        for (int j = 0; j < g->n[1]; j++)
+            for (int i = 0; i < g->n[0]; i++) {
+                int I[2] = {i / 2, prolong_partner(i, gc.n[0], g->bc[0])};
+                int J[2] = {j / 2, prolong_partner(j, gc.n[1], g->bc[1])};
+                int K[2] = {k / 2, prolong_partner(k, gc.n[2], g->bc[2])};
+                double sum = 0.0;
+                for (int S = 0; S < 8; S++) { /* corner: bit 0 x, bit 1 y, bit 2 z */
+                    double num = 0.0, den = 0.0;
+                    for (int T = 0; T < 8; T++) {
+                        if ((T & S) != T) continue; /* shifts only along the axes of S */
+                        long c = cell_index(&gc, I[T & 1], J[(T >> 1) & 1], K[(T >> 2) & 1]);
+                        num += ac[c] * e[c];
+                        den += ac[c];
+                    }
+                    sum += num / den;
+                }
+                x[cell_index(g, i, j, k)] += sum / 8.0;
+            }
+}
+
 /* ------------------------------------------------------------------------ */
 /* (6) Exact solve on the coarsest grid                                      */
 /* ------------------------------------------------------------------------ */
@@ -444,6 +514,7 @@ typedef struct {
     og_grid g;
     double *a[3];
     double *x, *b, *r;
+    double *ac; /* cell coefficients (flux-conserving prolongation, coarse levels) */
 } og_level;
 
 typedef struct {
@@ -451,6 +522,7 @@ typedef struct {
     og_level lev[32];
     int nu1, nu2;
     double omega;
+    int prolong; /* 0 trilinear, 1 flux-conserving */
 } og_hier;
 
 static void free_hier(og_hier *H)
@@ -463,6 +535,7 @@ static void free_hier(og_hier *H)
             free(L->b);
         }
         free(L->r);
+        free(L->ac);
     }
 }
 
@@ -485,6 +558,10 @@ static int build_hier(og_hier *H, const og_grid *g, const double *ax, const doub
         C->b = (double *)malloc(sizeof(double) * (size_t)nc);
         C->r = (double *)malloc(sizeof(double) * (size_t)nc);
         oracle_coarsen_faces(&F->g, F->a[0], F->a[1], F->a[2], C->a[0], C->a[1], C->a[2]);
+        if (H->prolong == 1) {
+            C->ac = (double *)malloc(sizeof(double) * (size_t)nc);
+            oracle_cell_alpha(&C->g, C->a[0], C->a[1], C->a[2], C->ac);
+        }
         H->nlev++;
     }
     return 0;
@@ -510,7 +587,8 @@ static int vcycle(og_hier *H, int l)
     memset(C->x, 0, sizeof(double) * (size_t)cell_count(&C->g));
     int st = vcycle(H, l + 1);
     if (st) return st;
-    oracle_prolong_add(&L->g, C->x, L->x);
+    if (H->prolong == 1) oracle_prolong_flux_add(&L->g, C->ac, C->x, L->x);
+    else oracle_prolong_add(&L->g, C->x, L->x);
     smooth(H, L, H->nu2);
     return 0;
 }
@@ -521,17 +599,19 @@ static int vcycle(og_hier *H, int l)
  * R_0 .. R_nc (Eq. 15 uses R_nc and R_0).  If `stagnate` is non-zero the
  * iteration also stops once three cycles in a row have not lowered the best
  * residual by 10% (used to reach p* to rounding).
+ * prolong selects the prolongation (4): 0 trilinear, 1 flux-conserving.
  * Returns 0 converged, 1 not converged in max_cycles, 2 stopped on
  * stagnation, <0 error. */
 int oracle_solve(const og_grid *g, const double *ax, const double *ay, const double *az,
                  const double *b_in, double *x, double tol, int max_cycles, int nu1, int nu2,
-                 double omega, int stagnate, double *hist, int *ncycles)
+                 double omega, int stagnate, int prolong, double *hist, int *ncycles)
 {
     og_hier H;
     memset(&H, 0, sizeof(H));
     H.nu1 = nu1;
     H.nu2 = nu2;
     H.omega = omega;
+    H.prolong = prolong;
     build_hier(&H, g, ax, ay, az);
     og_level *L0 = &H.lev[0];
     long n = cell_count(g);

@@ -86,6 +86,7 @@ int check_params(const mg_params *p)
     if (p->precision != MG_PREC_FP64 && p->precision != MG_PREC_MIXED) return MG_EINVAL;
     if (p->inner_cycles < 0 || p->inner_cycles > 16) return MG_EINVAL;
     if (p->tiles < MG_TILES_AUTO || p->tiles >= MG_TILE_VARIANTS) return MG_EINVAL;
+    if (p->prolongation != MG_PROLONG_TRILINEAR && p->prolongation != MG_PROLONG_FLUX) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -94,6 +95,7 @@ struct Layout {
     int L;
     int n[MG_MAX_LEVELS][3];
     size_t w64[MG_MAX_LEVELS][3], w32[MG_MAX_LEVELS][3], x[MG_MAX_LEVELS], b[MG_MAX_LEVELS];
+    size_t alpha64[MG_MAX_LEVELS], alpha32[MG_MAX_LEVELS];
     size_t G, b0, part, err, state, dstate, dview, dstart, dcview, setup_cv, total;
     int nblk0;
 };
@@ -111,6 +113,9 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
         for (int d = 0; d < 3; d++) lay.w32[l][d] = mixed ? c.take(N * 4) : 0;
         lay.x[l] = c.take(N * vs);
         lay.b[l] = c.take(N * vs);
+        const bool flux = l > 0 && p.prolongation == MG_PROLONG_FLUX;
+        lay.alpha64[l] = flux ? c.take(N * 8) : 0;
+        lay.alpha32[l] = (flux && mixed) ? c.take(N * 4) : 0;
     }
     const int *nc = lay.n[lay.L - 1];
     const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
@@ -222,6 +227,7 @@ int Plan::fill(mg_handle *const *handles, int count)
     for (auto *h : hs) Lmax = std::max(Lmax, h->L);
     std::vector<int> lt(G);
     for (int g = 0; g < G; g++) lt[g] = first_tail_level(hs[g]);
+    const bool flux = prm.prolongation == MG_PROLONG_FLUX;
     LevelView *lv = (LevelView *)(stage_h + o_lv);
     int *starts = (int *)(stage_h + o_starts);
     CoarseView *cvh = (CoarseView *)(stage_h + o_cv);
@@ -241,6 +247,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         // this level, if it fits every grid of the table, else the row shape
         int var[3] = {0, 0, 0};
         long long most = -1;
+        // flux-conserving prolongation runs in the row-tiled kernel only
         for (int g = 0; g < G; g++) {
             mg_handle *h = hs[g];
             if (l + 1 >= h->L || l >= lt[g] || h->lev[l].N <= most) continue;
@@ -253,6 +260,7 @@ int Plan::fill(mg_handle *const *handles, int count)
             for (int k = 0; k < 3; k++)
                 if (!tile_fits(h->lev[l].n, var[k])) var[k] = 0;
         }
+        if (flux) var[MG_TILE_PROLONG] = 0;
         // three prefix arrays, each count + 1 long, laid out one after the other
         std::vector<int> sf{0}, sc{0}, sh{0};
         for (int g = 0; g < G; g++) {
@@ -273,6 +281,7 @@ int Plan::fill(mg_handle *const *handles, int count)
             v.bc = C.b;
             v.g = g;
             v.st = h->state;
+            v.ac = mixed ? (const void *)C.alpha32 : (const void *)C.alpha64;
             fill_fastdiv(v);
             sf.push_back(sf.back() + prolong_blocks_v(F.n, C.n, var[MG_TILE_PROLONG]));
             sc.push_back(sc.back() + restrict_blocks_v(F.n, C.n, var[MG_TILE_RESTRICT]));
@@ -284,7 +293,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         for (int v : sc) starts[nst++] = v;
         sh0 = nst;
         for (int v : sh) starts[nst++] = v;
-        down[l] = Table{d_lv + lv0, d_starts + sf0, cnt, sf.back(), var[MG_TILE_PROLONG]};
+        down[l] = Table{d_lv + lv0, d_starts + sf0, cnt, sf.back(), var[MG_TILE_PROLONG], flux ? 1 : 0};
         rest[l] = Table{d_lv + lv0, d_starts + sc0, cnt, sc.back(), var[MG_TILE_RESTRICT]};
         half[l] = Table{d_lv + lv0, d_starts + sh0, cnt, sh.back(), var[MG_TILE_HALF]};
     }
@@ -306,6 +315,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         memset(&v, 0, sizeof(v));
         v.nt = h->L - lt[g];
         v.per = h->per;
+        v.flux = flux ? 1 : 0;
         int off = 0;
         for (int t = 0; t < v.nt; t++) {
             const HLevel &Lv = h->lev[lt[g] + t];
@@ -317,7 +327,8 @@ int Plan::fill(mg_handle *const *handles, int count)
             v.dx[t] = make_fastdiv((unsigned)Lv.n[0]);
             v.dhx[t] = make_fastdiv(Lv.n[0] >= 2 ? (unsigned)(Lv.n[0] >> 1) : 1u);
             v.dy[t] = make_fastdiv((unsigned)Lv.n[1]);
-            off += 5 * (int)Lv.N;
+            v.a[t] = mixed ? (const void *)Lv.alpha32 : (const void *)Lv.alpha64;
+            off += (flux ? 6 : 5) * (int)Lv.N;
             off = (off + 3) & ~3;
         }
         v.x0 = h->lev[lt[g]].x;
@@ -725,6 +736,20 @@ static int upload_faces(mg_handle *h)
             a.wc32[d] = h->mixed ? h->lev[l].w32[d] : nullptr;
         }
         launch_coarsen_faces(a, h->stream);
+        if (h->lev[l].alpha64) {
+            // cell coefficients for the flux-conserving prolongation into level l - 1
+            AlphaArgs c;
+            memset(&c, 0, sizeof(c));
+            for (int d = 0; d < 3; d++) {
+                c.n[d] = h->lev[l].n[d];
+                c.h2[d] = h->lev[l].h[d] * h->lev[l].h[d];
+                c.w[d] = h->lev[l].w64[d];
+            }
+            c.per = h->per;
+            c.out64 = h->lev[l].alpha64;
+            c.out32 = h->lev[l].alpha32;
+            launch_cell_alpha(c, h->stream);
+        }
     }
     launch_coarse_setup(h->setup_cv, 1, h->stream);
     CK(cudaGetLastError());
@@ -816,6 +841,8 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
         }
         L.N = (long long)L.n[0] * L.n[1] * L.n[2];
         L.x = h->slab + lay.x[l];
+        L.alpha64 = lay.alpha64[l] ? (double *)(h->slab + lay.alpha64[l]) : nullptr;
+        L.alpha32 = lay.alpha32[l] ? (float *)(h->slab + lay.alpha32[l]) : nullptr;
         L.b = h->slab + lay.b[l];
     }
     h->G = (double *)(h->slab + lay.G);
@@ -904,6 +931,7 @@ int mg_params_default(mg_params *p)
     p->use_graph = 1;
     p->inner_cycles = 0;
     p->tiles = MG_TILES_AUTO;
+    p->prolongation = MG_PROLONG_TRILINEAR;
     return MG_OK;
 }
 
@@ -1049,7 +1077,9 @@ int mg_batch_create(mg_handle *const *handles, int count, mg_batch **out)
         if (handles[g]->mixed != handles[0]->mixed || handles[g]->stream != handles[0]->stream)
             return MG_EINVAL;
         if (handles[g]->prm.nu1 != handles[0]->prm.nu1 || handles[g]->prm.nu2 != handles[0]->prm.nu2 ||
-            handles[g]->prm.omega != handles[0]->prm.omega)
+            handles[g]->prm.omega != handles[0]->prm.omega ||
+            handles[g]->prm.inner_cycles != handles[0]->prm.inner_cycles ||
+            handles[g]->prm.prolongation != handles[0]->prm.prolongation)
             return MG_EINVAL;
         for (int q = 0; q < g; q++)
             if (handles[q] == handles[g]) return MG_EINVAL;
@@ -1106,6 +1136,24 @@ int mg_level_shape(const mg_handle *h, int level, int *nx, int *ny, int *nz)
     return MG_OK;
 }
 
+int mg_level_cell_alpha(const mg_handle *h, int level, double *alpha)
+{
+    if (!h || !alpha || level < 0 || level >= h->L) return MG_EINVAL;
+    AlphaArgs c;
+    memset(&c, 0, sizeof(c));
+    for (int d = 0; d < 3; d++) {
+        c.n[d] = h->lev[level].n[d];
+        c.h2[d] = h->lev[level].h[d] * h->lev[level].h[d];
+        c.w[d] = h->lev[level].w64[d];
+    }
+    c.per = h->per;
+    c.out64 = alpha;
+    launch_cell_alpha(c, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
 int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double *wz)
 {
     if (!h || level < 0 || level >= h->L || !wx || !wy || !wz) return MG_EINVAL;
@@ -1139,6 +1187,9 @@ static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b,
     v.xc = (void *)xc;
     v.bc = bc;
     v.st = h->dstate;
+    v.ac = level + 1 >= h->L ? nullptr
+           : prec == MG_PREC_MIXED ? (const void *)h->lev[level + 1].alpha32
+                                   : (const void *)h->lev[level + 1].alpha64;
     fill_fastdiv(v);
     // the shape the handle's solves use on this level (not on the coarsest)
     const int kind = tiles == kCoarseTiles ? MG_TILE_RESTRICT : tiles == kProlongTiles ? MG_TILE_PROLONG
@@ -1148,7 +1199,8 @@ static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b,
     const int starts[2] = {0, blocks};
     CK(cudaMemcpyAsync(h->dview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, h->stream));
-    *tb = Table{h->dview, h->dstart, 1, blocks, var};
+    *tb = Table{h->dview, h->dstart, 1, blocks, var,
+                (tiles == kProlongTiles && h->prm.prolongation == MG_PROLONG_FLUX) ? 1 : 0};
     return MG_OK;
 }
 

@@ -33,6 +33,8 @@ struct HLevel {
     float *w32[3];   // FP32 copy (mixed precision only)
     void *x;         // V-cycle iterate / correction (V-cycle precision)
     void *b;         // V-cycle right-hand side (V-cycle precision)
+    double *alpha64; // cell coefficients (flux-conserving prolongation, levels >= 1), FP64
+    float *alpha32;  // FP32 copy (mixed precision only)
 };
 
 // CUDA-event timing of kernel classes (host-driven solves only).

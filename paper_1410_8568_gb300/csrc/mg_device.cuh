@@ -108,6 +108,7 @@ struct LevelView {
     // flat tilings: quads per fine row n[0]/4, fine rows per plane n[1],
     // coarse cell pairs per coarse row nc[0]/2, coarse rows per plane nc[1]
     FastDiv dq, dy, dp, dcy;
+    const void *ac;  // cell coefficients of the next coarser level (flux-conserving prolongation)
 };
 
 // The finest level of one grid for the FP64 outer iteration.
@@ -159,6 +160,8 @@ struct TailView {
     const double *G;         // coarsest-level inverse
     const GridState *st;
     FastDiv dx[kMaxTail], dhx[kMaxTail], dy[kMaxTail];  // division by n[t][0], n[t][0] / 2, n[t][1]
+    int flux;                // flux-conserving prolongation: level t >= 1 also holds its cell
+    const void *a[kMaxTail]; //   coefficients (6th array of the level in shared memory)
 };
 
 // Blocks of a launch over the cells of an n[0] x n[1] x n[2] level: a block is

@@ -304,7 +304,7 @@ int restrict_blocks(const int n[3], const int nc[3])
 // no post-smoothing, the refinement step ends here, so p += (double) x too.
 // ---------------------------------------------------------------------------
 
-template <class T, bool OUT>
+template <class T, bool OUT, bool FLUX>
 __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
                                                       const int *__restrict__ start, int count,
                                                       const OuterView *__restrict__ ov,
@@ -326,7 +326,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
-        prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, pout);
+        if constexpr (FLUX) prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, pout);
+        else prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, pout);
         return;
     }
     const Tile t = fine_tile(L.n, lb);
@@ -336,7 +337,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
         if (i >= nx) continue;
         const long long c = (long long)nx * t.row + i;
-        const T xn = x[c] + prolong_at(ec, L.nc, L.per, i, t.j, t.k);
+        const T xn = x[c] + (FLUX ? prolong_at_flux(ec, (const T *)L.ac, L.nc, L.per, i, t.j, t.k)
+                                  : prolong_at(ec, L.nc, L.per, i, t.j, t.k));
         x[c] = xn;
         if constexpr (OUT) pout[c] += (double)xn;
     }
@@ -432,6 +434,16 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
     }
     stage(sm + V.off[0] + V.n[0][0] * V.n[0][1] * V.n[0][2], (const T *)V.b0,
           V.n[0][0] * V.n[0][1] * V.n[0][2]);
+    if (V.flux) {
+        // cell coefficients of the tail's coarse levels (a small odd-sized
+        // coarsest level rules out the vector copy)
+        for (int t = 1; t < nt; t++) {
+            const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
+            const T *g = (const T *)V.a[t];
+            T *d = sm + V.off[t] + 5 * N;
+            for (int c = threadIdx.x; c < N; c += blockDim.x) d[c] = g[c];
+        }
+    }
     __syncthreads();
 
     auto half = [&](int t, int colour) {
@@ -511,10 +523,12 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
         const int nc[3] = {V.n[t + 1][0], V.n[t + 1][1], V.n[t + 1][2]};
         T *x = sm + V.off[t];
         const T *ec = sm + V.off[t + 1];
+        const T *ac = ec + 5 * (nc[0] * nc[1] * nc[2]);
         for (int c = threadIdx.x; c < N; c += blockDim.x) {
             const int row = fdiv(c, V.dx[t]);
             const int k = fdiv(row, V.dy[t]);
-            x[c] += prolong_at(ec, nc, per, c - row * nx, row - k * ny, k);
+            x[c] += V.flux ? prolong_at_flux(ec, ac, nc, per, c - row * nx, row - k * ny, k)
+                           : prolong_at(ec, nc, per, c - row * nx, row - k * ny, k);
         }
         __syncthreads();
         for (int it = 0; it < nu2; it++) {
@@ -733,6 +747,37 @@ __global__ void __launch_bounds__(kThreads) k_scale_faces(FaceArgs a)
 
 // coarse w_d(I,J,K) = (1/16) * sum of the 4 fine w_d that tile the coarse face:
 // alpha_c = mean of the 4 fine alpha, and 1/(2h)^2 = (1/4)(1/h^2).
+// Cell coefficient of the flux-conserving prolongation: mean over the cell's
+// non-wall faces of alpha = w h_d^2 (1 for a cell without any).
+__global__ void __launch_bounds__(kThreads) k_cell_alpha(AlphaArgs a)
+{
+    const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
+    const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int rest = c / a.n[0];
+        const int q[3] = {c - rest * a.n[0], rest % a.n[1], rest / a.n[1]};
+        double s = 0.0;
+        int m = 0;
+        for (int d = 0; d < 3; d++) {
+            const bool periodic = (a.per >> d) & 1;
+            if (q[d] > 0 || periodic) {
+                s += a.w[d][c] * a.h2[d];
+                m++;
+            }
+            if (q[d] + 1 < a.n[d]) {
+                s += a.w[d][c + stride[d]] * a.h2[d];
+                m++;
+            } else if (periodic) {
+                s += a.w[d][c - stride[d] * (a.n[d] - 1)] * a.h2[d];
+                m++;
+            }
+        }
+        const double v = m ? s / m : 1.0;
+        if (a.out64) a.out64[c] = v;
+        if (a.out32) a.out32[c] = (float)v;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
 {
     const int NC = a.nc[0] * a.nc[1] * a.nc[2];
@@ -1002,10 +1047,13 @@ void launch_restrict_rows(const Table &tb, cudaStream_t s)
 template <class T>
 void launch_prolong_rows(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
 {
-    if (outer_update)
-        k_prolong<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
-    else
-        k_prolong<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
+    if (tb.flux) {
+        if (outer_update) k_prolong<T, true, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
+        else k_prolong<T, false, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
+    } else {
+        if (outer_update) k_prolong<T, true, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
+        else k_prolong<T, false, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
+    }
 }
 template <class T>
 void launch_tail(const TailView *tv, int count, size_t smem, double omega, int nu1, int nu2, cudaStream_t s)
@@ -1044,6 +1092,10 @@ void launch_faces_from_density(const FaceArgs &a, cudaStream_t s)
 void launch_scale_faces(const FaceArgs &a, cudaStream_t s)
 {
     k_scale_faces<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+}
+void launch_cell_alpha(const AlphaArgs &a, cudaStream_t s)
+{
+    k_cell_alpha<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
 }
 void launch_coarsen_faces(const CoarsenArgs &a, cudaStream_t s)
 {

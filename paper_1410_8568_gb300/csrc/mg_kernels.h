@@ -13,6 +13,7 @@ struct Table {
     int count;
     int blocks;
     int variant = 0;  // launch shape (tile_shape); 0 = row tiles
+    int flux = 0;     // prolongation tables: flux-conserving (row tiles only)
 };
 
 struct OuterTable {
@@ -33,6 +34,17 @@ struct FaceArgs {
     double *out64[3];
     float *out32[3];         // optional FP32 copy
     int *err;                // set to 1 on a non-positive / non-finite value
+};
+
+// cell coefficient of the flux-conserving prolongation: mean over the cell's
+// non-wall faces of alpha = w h_d^2 (w the scaled FP64 face coefficients)
+struct AlphaArgs {
+    int n[3];
+    int per;
+    double h2[3];
+    const double *w[3];
+    float *out32;   // optional
+    double *out64;  // optional
 };
 
 struct CoarsenArgs {
@@ -73,6 +85,7 @@ void launch_coarse_setup(const CoarseView *, int count, cudaStream_t);
 void launch_faces_from_density(const FaceArgs &, cudaStream_t);
 void launch_scale_faces(const FaceArgs &, cudaStream_t);
 void launch_coarsen_faces(const CoarsenArgs &, cudaStream_t);
+void launch_cell_alpha(const AlphaArgs &, cudaStream_t);
 void launch_begin(const OuterView *, int count, cudaStream_t);
 void launch_sum(const OuterTable &, int which, cudaStream_t);
 template <class Te> void launch_residual(const OuterTable &, int init, cudaStream_t);

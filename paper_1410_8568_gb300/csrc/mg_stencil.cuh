@@ -213,6 +213,52 @@ __device__ __forceinline__ T prolong_at(const T *__restrict__ ec, const int nc[3
     return lin(y0, y1);
 }
 
+// Flux-conserving prolongation (Sec. 2.3 item 4, Eqs. 13-14) at one fine cell.
+// e[q], a[q]: coarse error and cell coefficient of the 8 coarse cells around
+// the fine centre, q = bit 0 (x partner) | bit 1 (y partner) | bit 2 (z partner),
+// q = 0 the coarse cell holding the fine cell.  The corners of the fine cell's
+// octant are the coarse centre, 3 face centres, 3 edge midpoints and a node;
+// the value at each is the a-weighted mean of the coarse cells meeting there
+// (flux continuity across the face, Eq. 13, and its analogue at edges and
+// nodes), and the fine value is the mean of the 8 corners.  For constant a
+// this is the trilinear 27/9/3/1 rule.  Fixed summation order.
+template <class T>
+__device__ __forceinline__ T flux_corner_mean(const T e[8], const T a[8])
+{
+    T ae[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) ae[q] = a[q] * e[q];
+    const T s01 = ae[0] + ae[1], s02 = ae[0] + ae[2], s04 = ae[0] + ae[4];
+    const T d01 = a[0] + a[1], d02 = a[0] + a[2], d04 = a[0] + a[4];
+    const T s0123 = s01 + (ae[2] + ae[3]), d0123 = d01 + (a[2] + a[3]);
+    const T s0145 = s01 + (ae[4] + ae[5]), d0145 = d01 + (a[4] + a[5]);
+    const T s0246 = s02 + (ae[4] + ae[6]), d0246 = d02 + (a[4] + a[6]);
+    const T s_all = s0123 + ((ae[4] + ae[5]) + (ae[6] + ae[7]));
+    const T d_all = d0123 + ((a[4] + a[5]) + (a[6] + a[7]));
+    const T fx = relax_div(s01, d01), fy = relax_div(s02, d02), fz = relax_div(s04, d04);
+    const T exy = relax_div(s0123, d0123), exz = relax_div(s0145, d0145), eyz = relax_div(s0246, d0246);
+    const T node = relax_div(s_all, d_all);
+    return T(0.125) * (((e[0] + fx) + (fy + fz)) + ((exy + exz) + (eyz + node)));
+}
+
+// flux-conserving counterpart of prolong_at; ac = coarse cell coefficients
+template <class T>
+__device__ __forceinline__ T prolong_at_flux(const T *__restrict__ ec, const T *__restrict__ ac,
+                                             const int nc[3], int per, int i, int j, int k)
+{
+    const int I[2] = {i >> 1, partner(i, nc[0], per & 1)};
+    const int J[2] = {j >> 1, partner(j, nc[1], per & 2)};
+    const int K[2] = {k >> 1, partner(k, nc[2], per & 4)};
+    T e[8], a[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const int c = I[q & 1] + nc[0] * (J[(q >> 1) & 1] + nc[1] * K[q >> 2]);
+        e[q] = ec[c];
+        a[q] = ac[c];
+    }
+    return flux_corner_mean(e, a);
+}
+
 // Residual of the 4 cells of the quad at (i0, j, k): b - A x, faces in the
 // order of stencil() (x-, x+, y-, y+, z-, z+).
 template <class T>
@@ -318,6 +364,52 @@ __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j,
 #pragma unroll
     for (int u = 0; u < 4; u++) {
         xq.v[u] += lin(lin(a00[u], a10[u]), lin(a01[u], a11[u]));
+        if constexpr (OUT) pout[c + u] += (double)xq.v[u];
+    }
+    stq(x + c, xq);
+}
+
+// Flux-conserving x += P e_c on the aligned quad (4 qx .. 4 qx + 3, j, k): the
+// quad's 4 cells share the coarse x set {Im, I0, I0 + 1, Ip} on the 4 coarse
+// rows (J0 or its partner, K0 or its partner).
+template <class T, bool OUT>
+__device__ __forceinline__ void prolong_quad_flux(const LevelView &L, int row, int j, int k, int qx,
+                                                  double *__restrict__ pout)
+{
+    const int nx = L.n[0], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
+    const T *__restrict__ ec = (const T *)L.xc;
+    const T *__restrict__ ac = (const T *)L.ac;
+    T *x = (T *)L.x;
+    const int c = row * nx + 4 * qx;
+    const int I0 = 2 * qx;
+    const int Ix[4] = {partner(4 * qx, ncx, per & 1), I0, I0 + 1, partner(4 * qx + 3, ncx, per & 1)};
+    const int Jy[2] = {j >> 1, partner(j, ncy, per & 2)};
+    const int Kz[2] = {k >> 1, partner(k, ncz, per & 4)};
+    // coarse values: [row r = jy + 2 kz][x slot 0..3]
+    T ev[4][4], av[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int base = ncx * (Jy[r & 1] + ncy * Kz[r >> 1]);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            ev[r][m] = ec[base + Ix[m]];
+            av[r][m] = ac[base + Ix[m]];
+        }
+    }
+    // own and partner x slot of each fine cell of the quad
+    constexpr int own[4] = {1, 1, 2, 2}, par[4] = {0, 2, 1, 3};
+    Quad<T> xq = ldq(x + c);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        T e[8], a[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int r = ((q >> 1) & 1) + 2 * (q >> 2);
+            const int m = (q & 1) ? par[u] : own[u];
+            e[q] = ev[r][m];
+            a[q] = av[r][m];
+        }
+        xq.v[u] += flux_corner_mean(e, a);
         if constexpr (OUT) pout[c + u] += (double)xq.v[u];
     }
     stq(x + c, xq);

@@ -163,6 +163,10 @@ template <class T>
 void launch_prolong(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
 {
     if (tb.blocks == 0) return;
+    if (tb.flux) {  // flux-conserving prolongation: row tiles only
+        launch_prolong_rows<T>(tb, ov, outer_update, s);
+        return;
+    }
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
         if (outer_update)

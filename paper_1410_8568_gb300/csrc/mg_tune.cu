@@ -189,6 +189,7 @@ int tune_handle(mg_handle *h)
     for (int l = 0; l + 1 < h->L; l++) {
         const int *n = h->lev[l].n;
         for (int kind = 0; kind < 3; kind++) {
+            if (kind == MG_TILE_PROLONG && h->prm.prolongation == MG_PROLONG_FLUX) continue;  // row tiles
             if (forced >= 0) {
                 h->tile[kind][l] = (signed char)(tile_fits(n, forced) ? forced : 0);
                 continue;

@@ -26,6 +26,7 @@ FP64, MIXED = 0, 1
 HARMONIC, ARITHMETIC = 0, 1
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL = range(7)
 TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
+PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
 TILE_HALF, TILE_RESTRICT, TILE_PROLONG = 0, 1, 2
 
 
@@ -44,7 +45,7 @@ class Grid(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("tiles", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("prolongation", ctypes.c_int), ("tiles", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +95,7 @@ def lib():
             "mg_num_levels": (_I, [_V, _P(_I)]),
             "mg_level_shape": (_I, [_V, _I, _P(_I), _P(_I), _P(_I)]),
             "mg_level_faces": (_I, [_V, _I, _V, _V, _V]),
+            "mg_level_cell_alpha": (_I, [_V, _I, _V]),
             "mg_apply": (_I, [_V, _I, _I, _V, _V]),
             "mg_smooth": (_I, [_V, _I, _I, _V, _V, _I]),
             "mg_restrict_residual": (_I, [_V, _I, _I, _V, _V, _V]),
@@ -144,7 +146,7 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
 
 
 def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
-                inner_cycles=None, tiles=None) -> Params:
+                inner_cycles=None, tiles=None, prolongation=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
@@ -155,6 +157,8 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
         p.inner_cycles = int(inner_cycles)
     if tiles is not None:
         p.tiles = int(tiles)
+    if prolongation is not None:
+        p.prolongation = int(prolongation)
     return p
 
 
@@ -232,7 +236,7 @@ class Solver:
 
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
                  precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
-                 inner_cycles=None, tiles=None):
+                 inner_cycles=None, tiles=None, prolongation=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -241,7 +245,8 @@ class Solver:
         self.cells = int(np.prod(self.shape))
         self.precision = precision
         self.grid = make_grid(self.shape, self.bc, self.length)
-        self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles)
+        self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles,
+                                  prolongation)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:
@@ -348,6 +353,15 @@ class Solver:
         nx, ny, nz = self.level_shape(level)
         out = [torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
         check(lib().mg_level_faces(self._h, int(level), *[_ptr(o) for o in out]), "mg_level_faces")
+        return out
+
+    def level_cell_alpha(self, level):
+        """Cell coefficients of the flux-conserving prolongation on `level` (FP64)."""
+        import torch
+
+        nx, ny, nz = self.level_shape(level)
+        out = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+        check(lib().mg_level_cell_alpha(self._h, int(level), _ptr(out)), "mg_level_cell_alpha")
         return out
 
     def apply(self, level, x, y, prec=FP64):

@@ -449,3 +449,130 @@ def test_solve_zero_rhs_and_warm_start():
     warm = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=1e-10, x0=ex.x + 5.0)
     assert warm.cycles == 0
     assert np.allclose(warm.x, ex.x, rtol=0, atol=1e-12 * np.abs(ex.x).max())
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 item 4, Eqs. 13-14: flux-conserving prolongation
+# ---------------------------------------------------------------------------
+
+def load_flux_golden():
+    from fractions import Fraction
+    rows = {}
+    with open(os.path.join(GOLDEN, "flux_prolongation.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            rows[key] = [float(Fraction(v)) for v in vals]
+    return rows
+
+
+def test_flux_prolongation_golden():
+    g = load_flux_golden()
+    shape, bc = (8, 2, 2), (0, 0, 0)
+    ac = np.array(g["coarse_alpha"]).reshape(1, 1, 4)
+    ec = np.array(g["coarse_e"]).reshape(1, 1, 4)
+    got = oracle.prolong_flux_add(shape, bc, ac, ec, np.zeros(cells(shape)))
+    want = np.broadcast_to(np.array(g["fine"]), cells(shape))
+    np.testing.assert_allclose(got, want, rtol=2e-16, atol=0)
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("shape", [(8, 8, 8), (12, 8, 6), (6, 4, 10)])
+def test_flux_prolongation_constant_alpha_is_trilinear(bc, shape):
+    """For a constant coefficient the alpha-weighted corner values are plain
+    means, and the mean of an octant's 8 corners is the trilinear 27/9/3/1 rule."""
+    rng = np.random.default_rng(sum(shape))
+    cs = oracle.coarse_shape(shape)
+    e = rng.standard_normal(cells(cs))
+    x = rng.standard_normal(cells(shape))
+    got = oracle.prolong_flux_add(shape, bc, np.full(cells(cs), 3.7), e, x)
+    want = oracle.prolong_add(shape, bc, e, x)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_flux_prolongation_local_maximum_principle(bc):
+    """Every corner value is a convex combination (positive weights), so a fine
+    value lies between the extremes of the 2 x 2 x 2 coarse cells around it."""
+    shape = (8, 6, 10)
+    cs = oracle.coarse_shape(shape)
+    rng = np.random.default_rng(3)
+    ac = 10.0 ** rng.uniform(-3, 3, size=cells(cs))
+    e = rng.standard_normal(cells(cs))
+    got = oracle.prolong_flux_add(shape, bc, ac, e, np.zeros(cells(shape)))
+
+    def partner(i, nc, periodic):
+        I = i // 2
+        J = I - 1 if i % 2 == 0 else I + 1
+        if 0 <= J < nc:
+            return J
+        return J % nc if periodic else I
+
+    for k in range(shape[2]):
+        for j in range(shape[1]):
+            for i in range(shape[0]):
+                Is = [i // 2, partner(i, cs[0], bc[0])]
+                Js = [j // 2, partner(j, cs[1], bc[1])]
+                Ks = [k // 2, partner(k, cs[2], bc[2])]
+                vals = [e[K, J, I] for K in Ks for J in Js for I in Is]
+                assert min(vals) - 1e-15 <= got[k, j, i] <= max(vals) + 1e-15
+
+
+def test_flux_prolongation_follows_the_conductive_side():
+    """A coarse neighbour with a vanishing coefficient does not pull the face
+    value: next to it the fine value is the coarse cell's own (Eq. 13)."""
+    shape, bc = (4, 2, 2), (0, 0, 0)
+    ac = np.array([1.0, 1e-14]).reshape(1, 1, 2)
+    ec = np.array([5.0, -7.0]).reshape(1, 1, 2)
+    got = oracle.prolong_flux_add(shape, bc, ac, ec, np.zeros(cells(shape)))
+    np.testing.assert_allclose(got[..., 1], 5.0, rtol=1e-12)     # cell 1 of coarse 0, face to coarse 1
+    np.testing.assert_allclose(got[..., 2], (-7.0 + 5.0) / 2, rtol=1e-12)  # coarse 1 sees coarse 0's value
+
+
+def test_cell_alpha_hand_values():
+    """Mean of the non-wall face coefficients of each cell."""
+    shape, bc = (3, 2, 2), (0, 1, 0)  # walls in x and z, periodic y
+    ax = np.zeros(cells(shape))
+    ay = np.zeros(cells(shape))
+    az = np.zeros(cells(shape))
+    ax[...] = np.array([9.0, 2.0, 4.0])      # low x faces: wall (ignored), 2 between i=0|1, 4 between 1|2
+    ay[:, 0, :] = 3.0                        # y faces: low face of j=0 (= wrap face) 3, of j=1: 5
+    ay[:, 1, :] = 5.0
+    az[0] = 7.0                              # low z face of k=0 is a wall
+    az[1] = 6.0
+    got = oracle.cell_alpha(shape, bc, [ax, ay, az])
+    # cell (0,0,0): faces x+ 2, y- 3, y+ 5, z+ 6 (x- and z- are walls)
+    assert got[0, 0, 0] == pytest.approx((2 + 3 + 5 + 6) / 4, rel=1e-15)
+    # cell (1,1,1): x- 2, x+ 4, y- 5, y+ 3 (wrap), z- 6 (z+ wall)
+    assert got[1, 1, 1] == pytest.approx((2 + 4 + 5 + 3 + 6) / 5, rel=1e-15)
+    # cell (2,0,1): x- 4 (x+ wall), y- 3, y+ 5, z- 6
+    assert got[1, 0, 2] == pytest.approx((4 + 3 + 5 + 6) / 4, rel=1e-15)
+    # constant faces give the constant
+    np.testing.assert_allclose(oracle.cell_alpha((8, 6, 4), (1, 0, 1), [np.full(cells((8, 6, 4)), 0.3)] * 3),
+                               0.3, rtol=1e-15)
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("ratio", [1000.0, 1e5])
+def test_flux_prolongation_solve_matches_dense_direct(bc, ratio):
+    shape = (8, 8, 8)
+    rng = np.random.default_rng(int(ratio) + 11)
+    c = rng.uniform(0.3, 0.7, size=3)
+    rho = I.density_field(shape, None, [(tuple(c), 0.3)], ratio, eps_cells=1.0)
+    faces = oracle.faces_from_density(shape, bc, rho)
+    b = rng.standard_normal(cells(shape))
+    want = dense_solution(shape, bc, faces, b)
+    got = oracle.solve_exact(shape, bc, faces, b, max_cycles=600, prolong=oracle.PROLONG_FLUX)
+    assert got.status in (0, 2)
+    assert np.linalg.norm(got.x - want) <= 1e-12 * np.linalg.norm(want) * max(1.0, math.log10(ratio))
+
+
+@pytest.mark.parametrize("ratio", [1000.0, 1e5])
+def test_flux_prolongation_converges_on_drop_film(ratio):
+    """Multigrid health with the paper's prolongation on a drop/film field."""
+    P = I.config2(32)
+    rho = I.density_field(P.shape, 0.1, [((0.5, 0.5, 0.3), 0.125)], ratio)
+    faces = oracle.faces_from_density(P.shape, P.bc, rho)
+    r = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=1e-10, max_cycles=200, prolong=oracle.PROLONG_FLUX)
+    assert r.status == 0 and r.gamma < 0.5
