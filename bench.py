@@ -67,6 +67,9 @@ WORKLOADS = {
 }
 
 
+PROLONG = {"trilinear": 0, "flux": 1}
+
+
 def make_problem(name):
     from paper_1410_8568_gb300 import inputs as I
     w = WORKLOADS[name]
@@ -232,6 +235,7 @@ def _line(args, world, name, value, ms, p50, p99, extra):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[name]["desc"], "tol": TOL,
                        "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
+                       "prolongation": args.prolongation,
                        "parallelism": "replicas" if world > 1 else "single"},
             "p50_ms": p50, "p99_ms": p99}
     line.update(extra)
@@ -256,7 +260,8 @@ def run_batch(args, rank, world, local_rank, dist):
     res = {}
     for prec in (gbmg.MIXED, gbmg.FP64):
         with torch.cuda.stream(stream):
-            solvers = [gbmg.Solver(P.shape, P.bc, rho=r, precision=prec, stream=stream) for P, r in zip(probs, rho)]
+            solvers = [gbmg.Solver(P.shape, P.bc, rho=r, precision=prec, stream=stream, prolongation=PROLONG[args.prolongation])
+                       for P, r in zip(probs, rho)]
             B = gbmg.Batch(solvers)
 
         def step():
@@ -417,11 +422,13 @@ def run_serve(args, rank, world, local_rank, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="drop_film_128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prolongation", default="trilinear", choices=["trilinear", "flux"],
+                    help="prolongation of the V-cycle: trilinear or flux-conserving (Sec. 2.3 item 4)")
     ap.add_argument("--requests", type=int, default=200, help="serve_stream: requests in the stream")
     ap.add_argument("--slots", type=int, default=8, help="serve_stream: most requests on the GPU at once")
     ap.add_argument("--hbm-budget", type=int, default=64, help="serve_stream: GiB of device memory for hierarchies")
@@ -492,7 +499,8 @@ def main():
     solvers = {}
     for prec in (gbmg.MIXED, gbmg.FP64):
         with torch.cuda.stream(stream):
-            solvers[prec] = gbmg.Solver(P.shape, P.bc, rho=rho, precision=prec, stream=stream)
+            solvers[prec] = gbmg.Solver(P.shape, P.bc, rho=rho, precision=prec, stream=stream,
+                                        prolongation=PROLONG[args.prolongation])
         S = solvers[prec]
         timed(S, args.warmup)
         if dist is not None:
@@ -603,6 +611,7 @@ def main():
             "config": {"workload": WORKLOADS[args.workload]["desc"], "grid": list(P.shape),
                        "bc": list(P.bc), "density_ratio": P.ratio, "tol": TOL,
                        "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
+                       "prolongation": args.prolongation,
                        "step": "set density (faces, coarse faces, coarsest inverse) + cold-start solve",
                        "l2": "flushed before every step (256 MB write, outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single"},
