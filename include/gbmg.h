@@ -320,6 +320,35 @@ int mg_coarse_solve_static(const mg_grid *grid, const double *ax, const double *
                            const double *az, const double *r, double *e, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * The projection step around the solve (Sec. 2.2: Chorin's projection on the
+ * staggered MAC grid; S of Eq. 9 from the non-projected velocity).  Face
+ * velocities are DEVICE FP64 arrays of the grid's cell count in the layout of
+ * the face coefficients: u_d[c] is the normal velocity on the LOW face of cell
+ * c along axis d; on a Neumann axis the low face of the first cell is a wall
+ * (its entry is ignored: zero normal velocity) and the high wall of the last
+ * cell carries none.  The face coefficients are the handle's current ones
+ * (mg_create / mg_set_faces / mg_set_density).  Synchronous on the handle's
+ * stream; MG_EINVAL for a null pointer or dt not > 0.
+ * --------------------------------------------------------------------------- */
+
+/* S = D u / dt: per cell, the sum over axes of (u on the high face - u on the
+ * low face) / h_d, divided by dt (second-order centred differences). */
+int mg_divergence(mg_handle *h, const double *ux, const double *uy, const double *uz, double dt,
+                  double *S);
+
+/* u -= dt alpha G p on every face that is not a wall: u_f -= dt alpha_f
+ * (p_c - p_{c-1}) / h_d.  With the operator of Eq. 10 (A = D alpha G), the
+ * projected field has D u = dt (S - A p): dt times the solve's residual. */
+int mg_project(mg_handle *h, const double *p, double dt, double *ux, double *uy, double *uz);
+
+/* One projection: S = D u / dt (written to the caller's DEVICE buffer S),
+ * solve A p = S to tol (p = warm start in, solution out; as mg_solve), then
+ * u -= dt alpha G p in place.  Returns the solve's status (MG_OK or
+ * MG_ENOTCONV; u is projected with the last iterate) or an error. */
+int mg_projection_step(mg_handle *h, double *ux, double *uy, double *uz, double dt, double *p,
+                       double *S, double tol, mg_stats *st);
+
+/* ---------------------------------------------------------------------------
  * Timing of individual kernels.  While enabled, every kernel launch of the
  * handle is bracketed by CUDA events on its stream (solves then run as a
  * host-driven loop, not a graph).  mg_profile_read returns, for kernel class

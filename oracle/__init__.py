@@ -48,6 +48,8 @@ def lib():
         L.oracle_restrict.argtypes = [G, P, P]
         L.oracle_prolong_add.argtypes = [G, P, P]
         L.oracle_cell_alpha.argtypes = [G, P, P, P, P]
+        L.oracle_divergence.argtypes = [G, P, P, P, ctypes.c_double, P]
+        L.oracle_project.argtypes = [G, P, P, P, P, ctypes.c_double, P, P, P]
         L.oracle_prolong_flux_add.argtypes = [G, P, P, P]
         L.oracle_coarse_solve.argtypes = [G, P, P, P, P, P]
         L.oracle_solve.argtypes = [G, P, P, P, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -182,6 +184,25 @@ def prolong_flux_add(shape, bc, alpha_coarse, e_coarse, x):
     x = np.array(_arr(x, shape), copy=True)
     lib().oracle_prolong_flux_add(ctypes.byref(g), _ptr(a), _ptr(e), _ptr(x))
     return x
+
+
+def divergence(shape, bc, u, dt=1.0, length=(1.0, 1.0, 1.0)):
+    """S = D u / dt of face velocities u = (ux, uy, uz) (low-face layout)."""
+    g = grid(shape, bc, length)
+    uu = [_arr(a, shape) for a in u]
+    out = np.empty(_cells(shape))
+    lib().oracle_divergence(ctypes.byref(g), *[_ptr(a) for a in uu], float(dt), _ptr(out))
+    return out
+
+
+def project(shape, bc, faces, p, u, dt=1.0, length=(1.0, 1.0, 1.0)):
+    """u - dt alpha G p on every non-wall face (returns new arrays)."""
+    g = grid(shape, bc, length)
+    f = [_arr(a, shape) for a in faces]
+    p = _arr(p, shape)
+    out = [np.array(_arr(a, shape), copy=True) for a in u]
+    lib().oracle_project(ctypes.byref(g), *[_ptr(a) for a in f], _ptr(p), float(dt), *[_ptr(a) for a in out])
+    return out
 
 
 def coarse_solve(shape, bc, faces, r, length=(1.0, 1.0, 1.0)):

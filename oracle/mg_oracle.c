@@ -22,6 +22,10 @@
  *   (5) red-black relaxation                             -> oracle_smooth_colour
  *   (6) exact solve of the error on the coarsest grid    -> oracle_coarse_solve (dense LU)
  * and the stopping test and average reduction rate of Eq. 15.
+ * Around the solve, the projection step of the Navier-Stokes module (Sec. 2.2:
+ * Chorin's projection on the staggered MAC grid, S a function of the
+ * non-projected velocity) -> oracle_divergence (S = D u* / dt) and
+ * oracle_project (u = u* - dt alpha G p).
  *
  * Readings where the paper is silent (each one also listed in the design notes):
  *  - the restriction of the residual (3), for which the paper names a linear
@@ -433,6 +437,73 @@ void oracle_prolong_flux_add(const og_grid *g, const double *ac, const double *e
                     sum += num / den;
                 }
                 x[cell_index(g, i, j, k)] += sum / 8.0;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection step around the solve (Sec. 2.2, MAC grid)                     */
+/* ------------------------------------------------------------------------ */
+
+/* Face velocities use the face layout: u[d][c] is the normal velocity on the
+ * LOW face of cell c along d; on a Neumann axis the low face of the first cell
+ * is a wall (its entry is ignored: zero normal velocity) and the high wall of
+ * the last cell carries none.  Divergence at the cell centre (second-order
+ * centred differences, Sec. 2.2), divided by dt:
+ *   S_c = sum_d (u_d(high face) - u_d(low face)) / h_d / dt. */
+void oracle_divergence(const og_grid *g, const double *ux, const double *uy, const double *uz,
+                       double dt, double *S)
+{
+    const double *u[3] = {ux, uy, uz};
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g->n[2]; k++)
+        for (int j = 0; j < g->n[1]; j++)
+            for (int i = 0; i < g->n[0]; i++) {
+                int q[3] = {i, j, k};
+                double div = 0.0;
+                for (int d = 0; d < 3; d++) {
+                    int n = g->n[d];
+                    double lo = (q[d] == 0 && g->bc[d] == OG_NEUMANN) ? 0.0 : u[d][cell_index(g, i, j, k)];
+                    double hi;
+                    if (q[d] + 1 < n) {
+                        int r[3] = {i, j, k};
+                        r[d] = q[d] + 1;
+                        hi = u[d][cell_index(g, r[0], r[1], r[2])];
+                    } else if (g->bc[d] == OG_PERIODIC) {
+                        int r[3] = {i, j, k};
+                        r[d] = 0;
+                        hi = u[d][cell_index(g, r[0], r[1], r[2])];
+                    } else {
+                        hi = 0.0; /* wall */
+                    }
+                    div += (hi - lo) / g->h[d];
+                }
+                S[cell_index(g, i, j, k)] = div / dt;
+            }
+}
+
+/* u_f -= dt alpha_f (p_c - p_{c-1}) / h_d on every face that is not a wall
+ * (the face between the cell and its low neighbour along d; periodic: the low
+ * face of the first cell joins it to the last).  With the operator of Eq. 10,
+ * D(alpha G p) = A p, so the projected field satisfies D u = dt (S - A p). */
+void oracle_project(const og_grid *g, const double *ax, const double *ay, const double *az,
+                    const double *p, double dt, double *ux, double *uy, double *uz)
+{
+    const double *a[3] = {ax, ay, az};
+    double *u[3] = {ux, uy, uz};
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g->n[2]; k++)
+        for (int j = 0; j < g->n[1]; j++)
+            for (int i = 0; i < g->n[0]; i++) {
+                int q[3] = {i, j, k};
+                long c = cell_index(g, i, j, k);
+                for (int d = 0; d < 3; d++) {
+                    int r[3] = {i, j, k};
+                    if (q[d] > 0) r[d] = q[d] - 1;
+                    else if (g->bc[d] == OG_PERIODIC) r[d] = g->n[d] - 1;
+                    else continue; /* wall face */
+                    long m = cell_index(g, r[0], r[1], r[2]);
+                    u[d][c] -= dt * a[d][c] * (p[c] - p[m]) / g->h[d];
+                }
             }
 }
 

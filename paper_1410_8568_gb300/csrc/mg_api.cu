@@ -1007,6 +1007,70 @@ int mg_solve(mg_handle *h, const double *rhs, double *p, double tol, mg_stats *s
     return run_plan(*h->plan, h->prof, &rhs, &p, &tol, st ? st : &tmp);
 }
 
+static ProjArgs proj_args(const mg_handle *h, double dt)
+{
+    ProjArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int d = 0; d < 3; d++) {
+        a.n[d] = h->lev[0].n[d];
+        a.h[d] = h->lev[0].h[d];
+        a.w[d] = h->lev[0].w64[d];
+    }
+    a.per = h->per;
+    a.dt = dt;
+    return a;
+}
+
+int mg_divergence(mg_handle *h, const double *ux, const double *uy, const double *uz, double dt, double *S)
+{
+    if (!h || !ux || !uy || !uz || !S || !(dt > 0.0) || !std::isfinite(dt)) return MG_EINVAL;
+    ProjArgs a = proj_args(h, dt);
+    a.u[0] = (double *)ux;
+    a.u[1] = (double *)uy;
+    a.u[2] = (double *)uz;
+    a.S = S;
+    launch_divergence(a, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_project(mg_handle *h, const double *p, double dt, double *ux, double *uy, double *uz)
+{
+    if (!h || !p || !ux || !uy || !uz || !(dt > 0.0) || !std::isfinite(dt)) return MG_EINVAL;
+    ProjArgs a = proj_args(h, dt);
+    a.p = p;
+    a.u[0] = ux;
+    a.u[1] = uy;
+    a.u[2] = uz;
+    launch_project(a, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_projection_step(mg_handle *h, double *ux, double *uy, double *uz, double dt, double *p, double *S,
+                       double tol, mg_stats *st)
+{
+    if (!h || !ux || !uy || !uz || !p || !S || !(dt > 0.0) || !std::isfinite(dt)) return MG_EINVAL;
+    ProjArgs a = proj_args(h, dt);
+    a.u[0] = ux;
+    a.u[1] = uy;
+    a.u[2] = uz;
+    a.S = S;
+    a.p = p;
+    launch_divergence(a, h->stream);
+    CK(cudaGetLastError());
+    mg_stats tmp;
+    const double *rhs = S;
+    const int rc = run_plan(*h->plan, h->prof, &rhs, &p, &tol, st ? st : &tmp);
+    if (rc != MG_OK && rc != MG_ENOTCONV) return rc;
+    launch_project(a, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
 static int ensure_host_buffers(mg_handle *h, bool rho)
 {
     const size_t n = (size_t)h->lev[0].N * sizeof(double);

@@ -778,6 +778,54 @@ __global__ void __launch_bounds__(kThreads) k_cell_alpha(AlphaArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Projection step around the solve (Chorin's projection on the MAC grid).
+// u[d][c] is the normal velocity on the LOW face of cell c along d; on a
+// Neumann axis the low face of the first cell is a wall (zero) and the high
+// wall of the last cell carries no velocity.
+// ---------------------------------------------------------------------------
+
+// S = D u / dt: sum over axes of (high face - low face) / h_d, divided by dt
+__global__ void __launch_bounds__(kThreads) k_divergence(ProjArgs a)
+{
+    const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
+    const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int rest = c / a.n[0];
+        const int q[3] = {c - rest * a.n[0], rest % a.n[1], rest / a.n[1]};
+        double div = 0.0;
+        for (int d = 0; d < 3; d++) {
+            const bool periodic = (a.per >> d) & 1;
+            const double lo = (q[d] > 0 || periodic) ? a.u[d][c] : 0.0;
+            const double hi = q[d] + 1 < a.n[d] ? a.u[d][c + stride[d]]
+                              : periodic       ? a.u[d][c - stride[d] * (a.n[d] - 1)]
+                                               : 0.0;
+            div += (hi - lo) / a.h[d];
+        }
+        a.S[c] = div / a.dt;
+    }
+}
+
+// u_f -= dt alpha_f (p_c - p_low) / h_d on every face that is not a wall;
+// alpha_f / h_d = w h_d with the scaled coefficient w = alpha / h_d^2.  With
+// the operator of Eq. 10, D(alpha G p) = A p, so D u = dt (S - A p).
+__global__ void __launch_bounds__(kThreads) k_project(ProjArgs a)
+{
+    const int N = a.n[0] * a.n[1] * a.n[2];
+    const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int rest = c / a.n[0];
+        const int q[3] = {c - rest * a.n[0], rest % a.n[1], rest / a.n[1]};
+        const double pc = a.p[c];
+        for (int d = 0; d < 3; d++) {
+            const bool periodic = (a.per >> d) & 1;
+            if (q[d] == 0 && !periodic) continue;  // wall face
+            const int m = q[d] > 0 ? c - stride[d] : c + stride[d] * (a.n[d] - 1);
+            a.u[d][c] -= a.dt * (a.w[d][c] * a.h[d]) * (pc - a.p[m]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
 {
     const int NC = a.nc[0] * a.nc[1] * a.nc[2];
@@ -1096,6 +1144,14 @@ void launch_scale_faces(const FaceArgs &a, cudaStream_t s)
 void launch_cell_alpha(const AlphaArgs &a, cudaStream_t s)
 {
     k_cell_alpha<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+}
+void launch_divergence(const ProjArgs &a, cudaStream_t s)
+{
+    k_divergence<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+}
+void launch_project(const ProjArgs &a, cudaStream_t s)
+{
+    k_project<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
 }
 void launch_coarsen_faces(const CoarsenArgs &a, cudaStream_t s)
 {

@@ -47,6 +47,18 @@ struct AlphaArgs {
     double *out64;  // optional
 };
 
+// projection step around the solve (MAC grid, low-face layout of the velocity)
+struct ProjArgs {
+    int n[3];
+    int per;
+    double h[3];
+    double dt;
+    const double *w[3];   // scaled FP64 faces alpha / h^2 of level 0 (project)
+    const double *p;      // pressure (project)
+    double *u[3];         // face velocities (divergence: read; project: updated)
+    double *S;            // divergence / dt (divergence: written)
+};
+
 struct CoarsenArgs {
     int nf[3];
     int nc[3];
@@ -86,6 +98,8 @@ void launch_faces_from_density(const FaceArgs &, cudaStream_t);
 void launch_scale_faces(const FaceArgs &, cudaStream_t);
 void launch_coarsen_faces(const CoarsenArgs &, cudaStream_t);
 void launch_cell_alpha(const AlphaArgs &, cudaStream_t);
+void launch_divergence(const ProjArgs &, cudaStream_t);
+void launch_project(const ProjArgs &, cudaStream_t);
 void launch_begin(const OuterView *, int count, cudaStream_t);
 void launch_sum(const OuterTable &, int which, cudaStream_t);
 template <class Te> void launch_residual(const OuterTable &, int init, cudaStream_t);

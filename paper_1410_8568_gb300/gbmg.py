@@ -96,6 +96,9 @@ def lib():
             "mg_level_shape": (_I, [_V, _I, _P(_I), _P(_I), _P(_I)]),
             "mg_level_faces": (_I, [_V, _I, _V, _V, _V]),
             "mg_level_cell_alpha": (_I, [_V, _I, _V]),
+            "mg_divergence": (_I, [_V, _V, _V, _V, _D, _V]),
+            "mg_project": (_I, [_V, _V, _D, _V, _V, _V]),
+            "mg_projection_step": (_I, [_V, _V, _V, _V, _D, _V, _V, _D, _P(Stats)]),
             "mg_apply": (_I, [_V, _I, _I, _V, _V]),
             "mg_smooth": (_I, [_V, _I, _I, _V, _V, _I]),
             "mg_restrict_residual": (_I, [_V, _I, _I, _V, _V, _V]),
@@ -306,6 +309,36 @@ class Solver:
         if raise_on_error and rc not in (OK, ENOTCONV, EDIVERGED):
             check(rc, "mg_solve")
         st.status = rc if rc not in (OK, ENOTCONV, EDIVERGED) else st.status
+        return st
+
+    # -- projection step around the solve (MAC face velocities, low-face layout)
+    def divergence(self, u, dt, S):
+        """S = D u / dt for face velocities u = (ux, uy, uz)."""
+        import torch
+
+        d = torch.float64
+        check(lib().mg_divergence(self._h, *[_ptr(a, self.cells, d) for a in u], float(dt),
+                                  _ptr(S, self.cells, d)), "mg_divergence")
+
+    def project(self, p, dt, u):
+        """u -= dt alpha G p in place."""
+        import torch
+
+        d = torch.float64
+        check(lib().mg_project(self._h, _ptr(p, self.cells, d), float(dt), *[_ptr(a, self.cells, d) for a in u]),
+              "mg_project")
+
+    def projection_step(self, u, dt, p, S, tol=1e-10) -> Stats:
+        """S = D u / dt, solve A p = S (p warm start), u -= dt alpha G p."""
+        import torch
+
+        d = torch.float64
+        st = Stats()
+        rc = lib().mg_projection_step(self._h, *[_ptr(a, self.cells, d) for a in u], float(dt),
+                                      _ptr(p, self.cells, d), _ptr(S, self.cells, d), float(tol), ctypes.byref(st))
+        if rc not in (OK, ENOTCONV):
+            check(rc, "mg_projection_step")
+        st.status = rc
         return st
 
     def solve_host(self, rhs: np.ndarray, p: np.ndarray, tol=1e-10) -> Stats:

@@ -180,6 +180,57 @@ def rhs_fourier_divergence(shape, bc, rng: np.random.Generator, modes: int = 8,
     return b
 
 
+def fourier_velocity(shape, bc, rng: np.random.Generator, modes: int = 8,
+                     length=(1.0, 1.0, 1.0), zchunk=64):
+    """The random smooth velocity field behind ``rhs_fourier_divergence`` (same
+    draws from ``rng``), sampled on the MAC faces in the low-face layout:
+    component d of cell c is the normal velocity on c's LOW face along d.  On a
+    Neumann axis the low face of the first cell is a wall (set to 0); the high
+    wall of the last cell is not stored.  Sampling only: no divergence here.
+    """
+    nx, ny, nz = shape
+    kvec = rng.integers(1, 5, size=(modes, 3))
+    amp = rng.standard_normal((modes, 3))
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=modes)
+    h = [length[a] / shape[a] for a in range(3)]
+    n = (nx, ny, nz)
+
+    def coords(axis, face_axis):
+        m = n[axis]
+        if axis == face_axis:
+            return np.arange(m, dtype=np.float64) * h[axis]   # low faces
+        return (np.arange(m, dtype=np.float64) + 0.5) * h[axis]
+
+    out = []
+    for comp in range(3):
+        cx, cy, cz = coords(0, comp), coords(1, comp), coords(2, comp)
+        u = np.zeros((nz, ny, nx))
+        for k0 in range(0, nz, zchunk):
+            k1 = min(nz, k0 + zchunk)
+            zs = cz[k0:k1]
+            for m in range(modes):
+                ex = np.exp(2j * math.pi * kvec[m, 0] * cx)[None, None, :]
+                ey = np.exp(2j * math.pi * kvec[m, 1] * cy)[None, :, None]
+                ez = np.exp(2j * math.pi * kvec[m, 2] * zs)[:, None, None]
+                u[k0:k1] += amp[m, comp] * np.imag(ex * ey * ez * np.exp(1j * phase[m]))
+        if bc[comp] == NEUMANN:
+            sl = [slice(None)] * 3
+            sl[2 - comp] = 0
+            u[tuple(sl)] = 0.0
+        out.append(u)
+    return out
+
+
+def projection_problem(n: int = 128, ratio: float = 1000.0, dt: float = 1e-3):
+    """Drop/film density of config2 with its Fourier velocity field: the
+    non-projected velocity u* of one projection step."""
+    shape = (n, n, n)
+    rho = density_field(shape, 0.1, [((0.5, 0.5, 0.3), 0.125)], ratio)
+    rng = np.random.default_rng(config_seed(2, n))
+    u = fourier_velocity(shape, DROP_FILM_BC, rng)
+    return shape, DROP_FILM_BC, rho, u, dt
+
+
 def random_faces(shape, rng: np.random.Generator, lo=1e-3, hi=1.0):
     """Three arrays of log-uniform positive face values (operator tests)."""
     nx, ny, nz = shape

@@ -576,3 +576,57 @@ def test_flux_prolongation_converges_on_drop_film(ratio):
     faces = oracle.faces_from_density(P.shape, P.bc, rho)
     r = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=1e-10, max_cycles=200, prolong=oracle.PROLONG_FLUX)
     assert r.status == 0 and r.gamma < 0.5
+
+
+# ---------------------------------------------------------------------------
+# Projection step around the solve (Sec. 2.2, Chorin's projection on the MAC grid)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc", BCS)
+def test_divergence_of_projected_gradient_is_the_operator(bc):
+    """D(alpha G p) = A p: project a zero field with dt = 1 (u = -alpha G p),
+    take its divergence, compare with oracle_apply (Eq. 10)."""
+    shape, length = (12, 10, 8), (1.0, 0.7, 1.3)
+    rng = np.random.default_rng(21)
+    faces = [rng.uniform(0.01, 1.0, size=cells(shape)) for _ in range(3)]
+    p = rng.standard_normal(cells(shape))
+    zero = [np.zeros(cells(shape)) for _ in range(3)]
+    u = oracle.project(shape, bc, faces, p, zero, dt=1.0, length=length)
+    div = oracle.divergence(shape, bc, u, dt=1.0, length=length)
+    Ap = oracle.apply(shape, bc, faces, p, length=length)
+    np.testing.assert_allclose(div, -Ap, rtol=0, atol=1e-13 * np.abs(Ap).max())
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_divergence_matches_the_rhs_generator(bc):
+    """The Fourier velocity field and the RHS generator draw the same field;
+    the generator differences it on its own face samples (high faces sampled
+    directly), the oracle through the low-face layout and the wrap rule."""
+    shape = (16, 12, 20)
+    u = I.fourier_velocity(shape, bc, np.random.default_rng(33))
+    b = I.rhs_fourier_divergence(shape, bc, np.random.default_rng(33))
+    S = oracle.divergence(shape, bc, u, dt=0.25)
+    np.testing.assert_allclose(0.25 * S - (0.25 * S).mean(), b, rtol=0, atol=1e-12 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_divergence_sums_to_zero(bc):
+    """Discrete divergence theorem: walls carry no flux, periodic faces cancel."""
+    shape = (10, 6, 8)
+    rng = np.random.default_rng(8)
+    u = [rng.standard_normal(cells(shape)) for _ in range(3)]
+    S = oracle.divergence(shape, bc, u, dt=1.0)
+    assert abs(S.sum()) <= 1e-12 * np.abs(S).sum()
+
+
+def test_projection_step_removes_the_divergence():
+    """S = D u* / dt, p = p*(S), u = u* - dt alpha G p: D u = dt (S - A p)."""
+    shape, bc, rho, u, dt = I.projection_problem(32, ratio=1000.0, dt=1e-2)
+    faces = oracle.faces_from_density(shape, bc, rho)
+    S = oracle.divergence(shape, bc, u, dt=dt)
+    p = oracle.solve_exact(shape, bc, faces, S).x
+    un = oracle.project(shape, bc, faces, p, u, dt=dt)
+    div = oracle.divergence(shape, bc, un, dt=1.0)
+    assert np.linalg.norm(div) <= 1e-10 * np.linalg.norm(dt * S)
+    # walls keep zero normal velocity
+    assert np.all(un[2][0] == 0.0)
