@@ -58,6 +58,9 @@ WORKLOADS = {
                            desc="drop_film_1024^3_1000to1: film + drop + 0-4 droplets, periodic x,y, Neumann z, Fourier-divergence RHS"),
     "sphere_32": dict(kind="config1", n=32,
                       desc="sphere_32^3_1000to1: R 0.2 centred, Neumann walls, N(0,1) RHS"),
+    "projection_128": dict(kind="projection", n=128,
+                           desc="projection step at 128^3: S = div u*/dt of a Fourier MAC velocity field on the "
+                                "drop/film density (1000:1, periodic x,y, Neumann z), solve, u = u* - dt grad p / rho"),
     "batch64": dict(kind="batch", n=0,
                     desc="batch of 64 grids, n in {32,48,64,96,128}^3, seeded spheres R 0.05-0.2, ratio {10,100,1000}, "
                          "Neumann walls, N(0,1) RHS; one batched graph launch per solve of all 64"),
@@ -240,6 +243,74 @@ def _line(args, world, name, value, ms, p50, p99, extra):
             "p50_ms": p50, "p99_ms": p99}
     line.update(extra)
     return line
+
+
+def run_projection(args, rank, world, local_rank, dist):
+    """One projection step per step: divergence, solve to 1e-10, velocity update."""
+    import torch
+
+    from paper_1410_8568_gb300 import gbmg
+    from paper_1410_8568_gb300 import inputs as I
+
+    n = WORKLOADS[args.workload]["n"]
+    shape, bc, rho_np, u_np, dt = I.projection_problem(n, ratio=1000.0, dt=1e-2)
+    rho = torch.from_numpy(rho_np).cuda()
+    u0 = [torch.from_numpy(a).cuda() for a in u_np]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    res = {}
+    for prec in (gbmg.MIXED, gbmg.FP64):
+        with torch.cuda.stream(stream):
+            S = gbmg.Solver(shape, bc, rho=rho, precision=prec, stream=stream,
+                            prolongation=PROLONG[args.prolongation])
+            u = [a.clone() for a in u0]
+            p = torch.zeros_like(rho)
+            src = torch.empty_like(rho)
+
+            def step():
+                for a, b in zip(u, u0):
+                    a.copy_(b)
+                p.zero_()
+                return S.projection_step(u, dt, p, src, tol=TOL)
+
+            for _ in range(args.warmup):
+                step()
+            stream.synchronize()
+            if dist is not None:
+                dist.barrier()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                st = step()
+                ev[k][1].record(stream)
+                if st.status != gbmg.OK:
+                    raise RuntimeError("projection failed: %s" % gbmg.strerror(st.status))
+            stream.synchronize()
+        times = [a.elapsed_time(b) for a, b in ev]
+        tot = sum(times)
+        if dist is not None:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = t.item()
+        # divergence left in the projected field, relative to the field's before
+        div = torch.empty_like(rho)
+        S.divergence(u, 1.0, div)
+        S.divergence(u0, 1.0, src)
+        res[prec] = dict(value=world * args.steps / (tot / 1000.0), ms=tot / args.steps,
+                         p50=statistics.median(times), p99=float(np.percentile(times, 99)), iters=st.iters,
+                         div_ratio=(torch.linalg.vector_norm(div) / torch.linalg.vector_norm(src)).item())
+        S.close()
+    if rank == 0:
+        m, f = res[gbmg.MIXED], res[gbmg.FP64]
+        line = _line(args, world, args.workload, m["value"], m["ms"], m["p50"], m["p99"], {
+            "iters": m["iters"], "divergence_after_over_before": m["div_ratio"],
+            "step": "restore u*, p = 0; divergence + solve to 1e-10 + velocity update (timed, L2 flushed between steps)",
+            "fp64": {"value": f["value"], "unit": "solves/s", "ms_per_step": f["ms"], "iters": f["iters"],
+                     "divergence_after_over_before": f["div_ratio"]},
+            "mixed_over_fp64": m["value"] / f["value"],
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None})
+        print(json.dumps(line))
 
 
 def run_batch(args, rank, world, local_rank, dist):
@@ -461,6 +532,8 @@ def main():
         return run_batch(args, rank, world, local_rank, dist)
     if WORKLOADS[args.workload]["kind"] == "serve":
         return run_serve(args, rank, world, local_rank, dist)
+    if WORKLOADS[args.workload]["kind"] == "projection":
+        return run_projection(args, rank, world, local_rank, dist)
 
     P = make_problem(args.workload)
     N = P.cells

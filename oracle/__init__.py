@@ -55,6 +55,9 @@ def lib():
         L.oracle_solve.argtypes = [G, P, P, P, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P,
                                    ctypes.POINTER(ctypes.c_int)]
+        L.oracle_pcg_solve.argtypes = [G, P, P, P, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_int, P,
+                                       ctypes.POINTER(ctypes.c_int)]
         L.oracle_gamma.argtypes = [P, ctypes.c_int]
         L.oracle_gamma.restype = ctypes.c_double
         _lib = L
@@ -256,6 +259,27 @@ def solve(shape, bc, faces, b, tol=1e-10, max_cycles=200, nu1=2, nu2=2, omega=1.
     if st < 0:
         raise RuntimeError("oracle solve failed: %d" % st)
     res = SolveResult(x, st, hist[: nc.value + 1].copy())
+    bp = b - b.mean()
+    res._bnorm = float(np.sqrt(np.sum(bp * bp)))
+    return res
+
+
+def pcg_solve(shape, bc, faces, b, tol=1e-10, max_it=200, nu1=2, nu2=2, omega=1.0, precond=True,
+              x0=None, length=(1.0, 1.0, 1.0)) -> SolveResult:
+    """Conjugate gradients on -A, preconditioned by one V(nu1, nu2) cycle
+    (precond=True) or not; b projected to zero mean; history = recursive
+    residual norms."""
+    g = grid(shape, bc, length)
+    f = [_arr(a, shape) for a in faces]
+    b = _arr(b, shape)
+    x = np.zeros(_cells(shape)) if x0 is None else np.array(_arr(x0, shape), copy=True)
+    hist = np.zeros(max_it + 1)
+    nit = ctypes.c_int(0)
+    st = lib().oracle_pcg_solve(ctypes.byref(g), *[_ptr(a) for a in f], _ptr(b), _ptr(x), tol, max_it,
+                                nu1, nu2, omega, 1 if precond else 0, _ptr(hist), ctypes.byref(nit))
+    if st < 0:
+        raise RuntimeError("oracle PCG failed: %d" % st)
+    res = SolveResult(x, st, hist[: nit.value + 1].copy())
     bp = b - b.mean()
     res._bnorm = float(np.sqrt(np.sum(bp * bp)))
     return res

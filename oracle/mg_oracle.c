@@ -731,6 +731,96 @@ int oracle_solve(const og_grid *g, const double *ax, const double *ay, const dou
     return status;
 }
 
+/* Conjugate gradients on the SPD operator -A (zero-mean subspace), with the
+ * residual kept in the sign of the multigrid (r = b - A x, q = A d):
+ *   alpha = (r.z) / (d.q),  x += alpha d,  r -= alpha q,
+ *   beta = -alpha (z_new.q) / (r.z)_old   (Polak-Ribiere form, which equals the
+ *   Fletcher-Reeves one for a fixed symmetric preconditioner),
+ *   d = z_new + beta d.
+ * precond = 1: z = one V(nu1, nu2) cycle on A z = r from z = 0 (the multigrid
+ * of this file as the preconditioner), then z - mean(z); precond = 0: z = r
+ * (plain CG).  Stopping test and history as oracle_solve (hist[k] = ||r_k||,
+ * r the recursive residual).  Returns 0 converged, 1 not converged, -3 NaN,
+ * -4 breakdown (d.q >= 0). */
+int oracle_pcg_solve(const og_grid *g, const double *ax, const double *ay, const double *az,
+                     const double *b_in, double *x, double tol, int max_it, int nu1, int nu2,
+                     double omega, int precond, double *hist, int *nit)
+{
+    og_hier H;
+    memset(&H, 0, sizeof(H));
+    H.nu1 = nu1;
+    H.nu2 = nu2;
+    H.omega = omega;
+    H.prolong = 0;
+    build_hier(&H, g, ax, ay, az);
+    og_level *L0 = &H.lev[0];
+    long n = cell_count(g);
+    size_t bytes = sizeof(double) * (size_t)n;
+    double *b = (double *)malloc(bytes), *r = (double *)malloc(bytes), *z = (double *)malloc(bytes);
+    double *d = (double *)malloc(bytes), *q = (double *)malloc(bytes);
+    memcpy(b, b_in, bytes);
+    subtract_constant(g, b, oracle_mean(g, b));
+    double bnorm = oracle_norm2(g, b);
+    int status = 1, it = 0;
+    oracle_residual(g, ax, ay, az, b, x, r);
+    double rn = oracle_norm2(g, r);
+    hist[0] = rn;
+    double rz = 0.0;
+    if (bnorm == 0.0 || rn <= tol * bnorm) status = 0;
+    /* preconditioner: z = M r */
+#define OG_PRECOND()                                                             do {                                                                             if (precond) {                                                                   L0->b = r;                                                                   L0->x = z;                                                                   memset(z, 0, bytes);                                                         int st_ = vcycle(&H, 0);                                                     if (st_) { status = st_; break; }                                            subtract_constant(g, z, oracle_mean(g, z));                              } else {                                                                         memcpy(z, r, bytes);                                                     }                                                                        } while (0)
+    if (status == 1) {
+        do {
+            OG_PRECOND();
+        } while (0);
+        if (status == 1) {
+            memcpy(d, z, bytes);
+            rz = 0.0;
+            for (long c = 0; c < n; c++) rz += r[c] * z[c];
+        }
+    }
+    while (status == 1 && it < max_it) {
+        oracle_apply(g, ax, ay, az, d, q);
+        double dq = 0.0;
+        for (long c = 0; c < n; c++) dq += d[c] * q[c];
+        if (!(dq < 0.0)) { status = -4; break; }
+        double alpha = rz / dq;
+        for (long c = 0; c < n; c++) {
+            x[c] += alpha * d[c];
+            r[c] -= alpha * q[c];
+        }
+        it++;
+        rn = oracle_norm2(g, r);
+        hist[it] = rn;
+        if (!(rn == rn)) { status = -3; break; }
+        if (rn <= tol * bnorm) { status = 0; break; }
+        do {
+            OG_PRECOND();
+        } while (0);
+        if (status != 1) break;
+        double zq = 0.0, rz_new = 0.0;
+        for (long c = 0; c < n; c++) {
+            zq += z[c] * q[c];
+            rz_new += r[c] * z[c];
+        }
+        double beta = -alpha * zq / rz;
+        rz = rz_new;
+        for (long c = 0; c < n; c++) d[c] = z[c] + beta * d[c];
+    }
+#undef OG_PRECOND
+    subtract_constant(g, x, oracle_mean(g, x));
+    *nit = it;
+    L0->x = NULL;
+    L0->b = NULL;
+    free(b);
+    free(r);
+    free(z);
+    free(d);
+    free(q);
+    free_hier(&H);
+    return status;
+}
+
 /* Eq. 15: gamma = (R_nc / R_0)^(1/nc) */
 double oracle_gamma(const double *hist, int ncycles)
 {

@@ -630,3 +630,51 @@ def test_projection_step_removes_the_divergence():
     assert np.linalg.norm(div) <= 1e-10 * np.linalg.norm(dt * S)
     # walls keep zero normal velocity
     assert np.all(un[2][0] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Conjugate gradients preconditioned by the V-cycle (next rows: MG-PCG)
+# ---------------------------------------------------------------------------
+
+def test_cg_finite_termination_on_few_eigenvalues():
+    """Plain CG ends in at most as many steps as -A has distinct nonzero
+    eigenvalues: 4^3 periodic, alpha = 1: per axis 4 sin^2(pi k / 4) / h^2 is
+    0, 2, 4 (x 1/h^2), so the 3-axis sums take 6 distinct nonzero values."""
+    shape, bc = (4, 4, 4), (1, 1, 1)
+    b = np.random.default_rng(2).standard_normal(cells(shape))
+    r = oracle.pcg_solve(shape, bc, ones_faces(shape), b, tol=1e-12, max_it=50, precond=False)
+    assert r.status == 0 and r.cycles <= 6
+
+
+def test_cg_single_eigenvector_one_step():
+    """b an eigenvector of A: plain CG is exact after one step."""
+    shape, bc = (16, 8, 8), (0, 1, 0)
+    X, Y, Z = coords(shape)
+    b = np.cos(np.pi * 2 * X) * np.cos(2 * np.pi * Y)  # Neumann mode k=2 in x, periodic mode 1 in y
+    r = oracle.pcg_solve(shape, bc, ones_faces(shape), b, tol=1e-12, max_it=5, precond=False)
+    assert r.status == 0 and r.cycles == 1
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("ratio", [1.0, 1000.0, 1e5])
+def test_pcg_matches_dense_direct(bc, ratio):
+    shape = (8, 8, 8)
+    rng = np.random.default_rng(int(ratio) + 31)
+    c = rng.uniform(0.3, 0.7, size=3)
+    rho = I.density_field(shape, None, [(tuple(c), 0.3)], ratio, eps_cells=1.0)
+    faces = oracle.faces_from_density(shape, bc, rho)
+    b = rng.standard_normal(cells(shape))
+    want = dense_solution(shape, bc, faces, b)
+    got = oracle.pcg_solve(shape, bc, faces, b, tol=1e-14, max_it=100)
+    assert got.status == 0
+    assert np.linalg.norm(got.x - want) <= 1e-11 * np.linalg.norm(want) * max(1.0, math.log10(ratio))
+
+
+@pytest.mark.parametrize("ratio", [1000.0, 1e5])
+def test_pcg_converges_on_drop_film(ratio):
+    P = I.config2(32)
+    rho = I.density_field(P.shape, 0.1, [((0.5, 0.5, 0.3), 0.125)], ratio)
+    faces = oracle.faces_from_density(P.shape, P.bc, rho)
+    r = oracle.pcg_solve(P.shape, P.bc, faces, P.rhs, tol=1e-10)
+    mg = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=1e-10)
+    assert r.status == 0 and r.gamma < 0.5 and r.cycles <= mg.cycles
