@@ -81,6 +81,9 @@ extern "C" {
 #define MG_PREC_FP64 0  /* every level in FP64 */
 #define MG_PREC_MIXED 1 /* FP32 V-cycles inside FP64 iterative refinement */
 
+#define MG_SOLVER_MG 0   /* multigrid iteration: V-cycles inside FP64 iterative refinement */
+#define MG_SOLVER_PCG 1  /* conjugate gradients on -A (FP64), preconditioned by V-cycles */
+
 #define MG_PROLONG_TRILINEAR 0 /* prolongation weights 27/9/3/1 over 64 */
 #define MG_PROLONG_FLUX 1      /* Sec. 2.3 item 4, Eqs. 13-14: cell flux conservation */
 
@@ -112,7 +115,11 @@ typedef struct {
     int precision;     /* MG_PREC_FP64 or MG_PREC_MIXED */
     int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
     int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1;
-                          0 (default) = 3 in MIXED precision, 2 in FP64 */
+                          0 (default) = 3 in MIXED precision, 2 in FP64, 1 with MG_SOLVER_PCG */
+    int solver;        /* MG_SOLVER_MG (default) or MG_SOLVER_PCG: FP64 conjugate gradients on -A,
+                          each step preconditioned by inner_cycles V-cycles from zero (in the
+                          V-cycle precision), the preconditioned residual projected to zero mean;
+                          beta in the Polak-Ribiere form; iters counts V-cycles */
     int prolongation;  /* MG_PROLONG_TRILINEAR (default) or MG_PROLONG_FLUX: the coarse error
                           at a coarse face, edge or node is the mean of the coarse cells meeting
                           there weighted by their cell coefficient (flux continuity, Eq. 13), a

@@ -87,6 +87,7 @@ int check_params(const mg_params *p)
     if (p->inner_cycles < 0 || p->inner_cycles > 16) return MG_EINVAL;
     if (p->tiles < MG_TILES_AUTO || p->tiles >= MG_TILE_VARIANTS) return MG_EINVAL;
     if (p->prolongation != MG_PROLONG_TRILINEAR && p->prolongation != MG_PROLONG_FLUX) return MG_EINVAL;
+    if (p->solver != MG_SOLVER_MG && p->solver != MG_SOLVER_PCG) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -97,6 +98,7 @@ struct Layout {
     size_t w64[MG_MAX_LEVELS][3], w32[MG_MAX_LEVELS][3], x[MG_MAX_LEVELS], b[MG_MAX_LEVELS];
     size_t alpha64[MG_MAX_LEVELS], alpha32[MG_MAX_LEVELS];
     size_t G, b0, part, err, state, dstate, dview, dstart, dcview, setup_cv, total;
+    size_t pcg[4];
     int nblk0;
 };
 
@@ -122,6 +124,7 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
     lay.G = c.take(ncells * ncells * 8);
     const size_t N0 = (size_t)g.nx * g.ny * g.nz;
     lay.b0 = c.take(N0 * 8);
+    for (int v = 0; v < 4; v++) lay.pcg[v] = p.solver == MG_SOLVER_PCG ? c.take(N0 * 8) : 0;
     const int n0[3] = {g.nx, g.ny, g.nz};
     lay.nblk0 = outer_blocks(n0);
     lay.part = c.take((size_t)lay.nblk0 * kPart * 8);
@@ -374,6 +377,11 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.tol = 1e-10;
         v.max_iters = h->prm.max_iters;
         v.inner = prm.inner_cycles;
+        v.r64 = h->pcg[0];
+        v.z = h->pcg[1];
+        v.d = h->pcg[2];
+        v.q = h->pcg[3];
+        v.e = h->lev[0].x;
     }
     CK(cudaMemcpyAsync(mem, stage_h, tables_bytes, cudaMemcpyHostToDevice, stream));
     CK(cudaEventRecord(staged, stream));
@@ -487,6 +495,20 @@ static void vcycle(Plan &P, Prof &pf, int cycle_in_step, bool last_of_step)
     }
 }
 
+// Conjugate gradients: z = M r (inner_cycles V-cycles from zero, no update of
+// the FP64 iterate), the dot products of z, the new direction.
+template <class T>
+static void pcg_precondition(Plan &P, Prof &pf, int first)
+{
+    const cudaStream_t s = P.stream;
+    for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c, false);
+    pf.begin(s, MG_K_OTHER, 0);
+    launch_pcg_z<T>(P.ot, s);
+    launch_pcg_finalize(P.ot, first ? 0 : 2, s);
+    launch_pcg_dir(P.ot, first, s);
+    pf.end(s);
+}
+
 template <class T>
 static void prologue(Plan &P, Prof &pf)
 {
@@ -502,6 +524,7 @@ static void prologue(Plan &P, Prof &pf)
     pf.begin(s, MG_K_OTHER, 0);
     launch_finalize(P.ot, 1, s);
     pf.end(s);
+    if (P.prm.solver == MG_SOLVER_PCG) pcg_precondition<T>(P, pf, 1);
 }
 
 // One refinement step: inner_cycles V-cycles on A e = r (the first from e = 0,
@@ -511,6 +534,19 @@ template <class T>
 static void body(Plan &P, Prof &pf)
 {
     const cudaStream_t s = P.stream;
+    if (P.prm.solver == MG_SOLVER_PCG) {
+        // one CG step: q = A d, alpha, p and r updated, stopping test, z = M r, d
+        pf.begin(s, MG_K_RESIDUAL, 0);
+        launch_pcg_matvec(P.ot, s);
+        pf.end(s);
+        pf.begin(s, MG_K_OTHER, 0);
+        launch_pcg_finalize(P.ot, 1, s);
+        launch_pcg_update<T>(P.ot, s);
+        launch_finalize(P.ot, 2, s);
+        pf.end(s);
+        pcg_precondition<T>(P, pf, 0);
+        return;
+    }
     for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c, c == P.prm.inner_cycles - 1);
     pf.begin(s, MG_K_RESIDUAL, 0);
     launch_residual<T>(P.ot, 0, s);
@@ -810,7 +846,8 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
     // V-cycles per FP64 residual: FP32 cycles are cheap next to the FP64
     // residual pass (FP64 arithmetic is slow on this GPU), so mixed precision
     // takes 3; FP64 cycles cost as much as the pass, 2 balances them
-    if (prm.inner_cycles == 0) prm.inner_cycles = prm.precision == MG_PREC_MIXED ? 3 : 2;
+    if (prm.inner_cycles == 0)
+        prm.inner_cycles = prm.solver == MG_SOLVER_PCG ? 1 : prm.precision == MG_PREC_MIXED ? 3 : 2;
     Layout lay;
     rc = plan_layout(*grid, prm, lay);
     if (rc) return rc;
@@ -847,6 +884,7 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
     }
     h->G = (double *)(h->slab + lay.G);
     h->b0 = (double *)(h->slab + lay.b0);
+    for (int v = 0; v < 4; v++) h->pcg[v] = lay.pcg[v] ? (double *)(h->slab + lay.pcg[v]) : nullptr;
     h->part = (double *)(h->slab + lay.part);
     h->nblk0 = lay.nblk0;
     h->err = (int *)(h->slab + lay.err);
@@ -932,6 +970,7 @@ int mg_params_default(mg_params *p)
     p->inner_cycles = 0;
     p->tiles = MG_TILES_AUTO;
     p->prolongation = MG_PROLONG_TRILINEAR;
+    p->solver = MG_SOLVER_MG;
     return MG_OK;
 }
 
@@ -1143,7 +1182,8 @@ int mg_batch_create(mg_handle *const *handles, int count, mg_batch **out)
         if (handles[g]->prm.nu1 != handles[0]->prm.nu1 || handles[g]->prm.nu2 != handles[0]->prm.nu2 ||
             handles[g]->prm.omega != handles[0]->prm.omega ||
             handles[g]->prm.inner_cycles != handles[0]->prm.inner_cycles ||
-            handles[g]->prm.prolongation != handles[0]->prm.prolongation)
+            handles[g]->prm.prolongation != handles[0]->prm.prolongation ||
+            handles[g]->prm.solver != handles[0]->prm.solver)
             return MG_EINVAL;
         for (int q = 0; q < g; q++)
             if (handles[q] == handles[g]) return MG_EINVAL;

@@ -86,6 +86,7 @@ struct mg_handle {
     gbmg::Prof prof;
     double *io_rhs = nullptr, *io_p = nullptr, *io_rho = nullptr;  // host-call staging
     signed char tile[3][MG_MAX_LEVELS] = {};  // launch shape per kernel (MG_TILE_*) and level
+    double *pcg[4] = {nullptr, nullptr, nullptr, nullptr};  // CG: r, z, d, q (FP64, finest level)
 };
 
 namespace gbmg {

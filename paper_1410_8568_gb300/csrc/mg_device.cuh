@@ -34,6 +34,10 @@ struct GridState {
     int iters;      // completed V-cycles
     int status;     // gbmg status code
     int active;     // 1 while the grid is being iterated
+    double rz;      // conjugate gradients: r . z of the current step
+    double alpha;   //   step length
+    double beta;    //   direction update
+    double zmean;   //   mean of the preconditioned residual
 };
 
 // Division by a fixed divisor d >= 1 of numerators n < 2^31 by one multiply
@@ -126,6 +130,11 @@ struct OuterView {
     double tol;
     int max_iters;
     int inner;           // V-cycles per refinement step
+    // conjugate gradients (null otherwise): FP64 residual, preconditioned
+    // residual, direction, A times direction; e = the V-cycle's level-0
+    // correction (V-cycle precision)
+    double *r64, *z, *d, *q;
+    const void *e;
 };
 
 // The coarsest level of one grid.

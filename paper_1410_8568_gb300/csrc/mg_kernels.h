@@ -106,6 +106,12 @@ template <class Te> void launch_residual(const OuterTable &, int init, cudaStrea
 void launch_finalize(const OuterTable &, int mode, cudaStream_t);
 void launch_final(const OuterTable &, cudaStream_t);
 void launch_gather_states(const OuterTable &, GridState *out, cudaStream_t);
+// conjugate gradients (mg_pcg.cu)
+void launch_pcg_matvec(const OuterTable &, cudaStream_t);
+template <class Te> void launch_pcg_update(const OuterTable &, cudaStream_t);
+template <class Te> void launch_pcg_z(const OuterTable &, cudaStream_t);
+void launch_pcg_dir(const OuterTable &, int first, cudaStream_t);
+void launch_pcg_finalize(const OuterTable &, int mode, cudaStream_t);
 void launch_loop_ctl(cudaGraphConditionalHandle, const OuterTable &, cudaStream_t);
 
 }  // namespace gbmg

@@ -27,6 +27,7 @@ HARMONIC, ARITHMETIC = 0, 1
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL = range(7)
 TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
 PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
+SOLVER_MG, SOLVER_PCG = 0, 1
 TILE_HALF, TILE_RESTRICT, TILE_PROLONG = 0, 1, 2
 
 
@@ -45,7 +46,8 @@ class Grid(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("prolongation", ctypes.c_int), ("tiles", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("solver", ctypes.c_int), ("prolongation", ctypes.c_int),
+                ("tiles", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -149,7 +151,7 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
 
 
 def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
-                inner_cycles=None, tiles=None, prolongation=None) -> Params:
+                inner_cycles=None, tiles=None, prolongation=None, solver=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
@@ -162,6 +164,8 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
         p.tiles = int(tiles)
     if prolongation is not None:
         p.prolongation = int(prolongation)
+    if solver is not None:
+        p.solver = int(solver)
     return p
 
 
@@ -239,7 +243,7 @@ class Solver:
 
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
                  precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
-                 inner_cycles=None, tiles=None, prolongation=None):
+                 inner_cycles=None, tiles=None, prolongation=None, solver=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -249,7 +253,7 @@ class Solver:
         self.precision = precision
         self.grid = make_grid(self.shape, self.bc, self.length)
         self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles,
-                                  prolongation)
+                                  prolongation, solver)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:
@@ -487,8 +491,9 @@ class Batch:
 class Server:
     """Continuous-batching request loop (mg_server_*)."""
 
-    def __init__(self, hbm_budget_bytes, max_slots=16, precision=MIXED, max_iters=100, stream=None):
-        self.params = make_params(precision, max_iters=max_iters)
+    def __init__(self, hbm_budget_bytes, max_slots=16, precision=MIXED, max_iters=100, stream=None,
+                 solver=None, prolongation=None):
+        self.params = make_params(precision, max_iters=max_iters, solver=solver, prolongation=prolongation)
         self._s = ctypes.c_void_p()
         st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
         check(lib().mg_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(self.params), st,
