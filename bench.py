@@ -71,6 +71,7 @@ WORKLOADS = {
 
 
 PROLONG = {"trilinear": 0, "flux": 1}
+SOLVER = {"mg": 0, "pcg": 1}
 
 
 def make_problem(name):
@@ -183,8 +184,8 @@ def level_shapes(shape):
     return out
 
 
-def count_launches(shape, iters, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=True):
-    """Kernels of one step: coefficient set-up, prologue, refinement steps, epilogue.
+def count_launches(shape, iters, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=True, pcg=False):
+    """Kernels of one step: coefficient set-up, prologue, refinement (or CG) steps, epilogue.
     In FP32 cycles the levels of at most tail_cells cells (below the finest) run in one launch."""
     lv = level_shapes(shape)
     L = len(lv)
@@ -193,7 +194,11 @@ def count_launches(shape, iters, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=T
     setup = 1 + (L - 1) + 1            # faces from density, coarsening per level, coarsest inverse
     prologue = 6                       # begin, sum b, mean, residual, finalize, loop control
     cycle = normal * (2 * nu1 + 1 + 1 + 2 * nu2) + 1  # half-sweeps, restriction, prolongation; tail or coarsest
-    step = inner * cycle + 3           # + residual, finalize, loop control
+    if pcg:
+        prologue += inner * cycle + 3  # first preconditioning: V-cycles, z and its sums, direction
+        step = 4 + inner * cycle + 3 + 1  # A d, alpha, update, test; V-cycles, z, beta, direction; loop control
+    else:
+        step = inner * cycle + 3       # + residual, finalize, loop control
     epilogue = 3                       # sum p, mean, p - mean
     return setup + prologue + (iters // inner) * step + epilogue
 
@@ -238,7 +243,7 @@ def _line(args, world, name, value, ms, p50, p99, extra):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[name]["desc"], "tol": TOL,
                        "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
-                       "prolongation": args.prolongation,
+                       "prolongation": args.prolongation, "solver": args.solver,
                        "parallelism": "replicas" if world > 1 else "single"},
             "p50_ms": p50, "p99_ms": p99}
     line.update(extra)
@@ -262,7 +267,7 @@ def run_projection(args, rank, world, local_rank, dist):
     for prec in (gbmg.MIXED, gbmg.FP64):
         with torch.cuda.stream(stream):
             S = gbmg.Solver(shape, bc, rho=rho, precision=prec, stream=stream,
-                            prolongation=PROLONG[args.prolongation])
+                            prolongation=PROLONG[args.prolongation], solver=SOLVER[args.solver])
             u = [a.clone() for a in u0]
             p = torch.zeros_like(rho)
             src = torch.empty_like(rho)
@@ -331,7 +336,8 @@ def run_batch(args, rank, world, local_rank, dist):
     res = {}
     for prec in (gbmg.MIXED, gbmg.FP64):
         with torch.cuda.stream(stream):
-            solvers = [gbmg.Solver(P.shape, P.bc, rho=r, precision=prec, stream=stream, prolongation=PROLONG[args.prolongation])
+            solvers = [gbmg.Solver(P.shape, P.bc, rho=r, precision=prec, stream=stream, prolongation=PROLONG[args.prolongation],
+                                   solver=SOLVER[args.solver])
                        for P, r in zip(probs, rho)]
             B = gbmg.Batch(solvers)
 
@@ -500,6 +506,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prolongation", default="trilinear", choices=["trilinear", "flux"],
                     help="prolongation of the V-cycle: trilinear or flux-conserving (Sec. 2.3 item 4)")
+    ap.add_argument("--solver", default="mg", choices=["mg", "pcg"],
+                    help="outer iteration: V-cycles in FP64 refinement (mg) or V-cycle-preconditioned CG (pcg)")
     ap.add_argument("--requests", type=int, default=200, help="serve_stream: requests in the stream")
     ap.add_argument("--slots", type=int, default=8, help="serve_stream: most requests on the GPU at once")
     ap.add_argument("--hbm-budget", type=int, default=64, help="serve_stream: GiB of device memory for hierarchies")
@@ -573,7 +581,7 @@ def main():
     for prec in (gbmg.MIXED, gbmg.FP64):
         with torch.cuda.stream(stream):
             solvers[prec] = gbmg.Solver(P.shape, P.bc, rho=rho, precision=prec, stream=stream,
-                                        prolongation=PROLONG[args.prolongation])
+                                        prolongation=PROLONG[args.prolongation], solver=SOLVER[args.solver])
         S = solvers[prec]
         timed(S, args.warmup)
         if dist is not None:
@@ -675,7 +683,7 @@ def main():
 
     if rank == 0:
         m, f = results[gbmg.MIXED], results[gbmg.FP64]
-        launches = args.steps * count_launches(P.shape, m["iters"], inner=m["inner"])
+        launches = args.steps * count_launches(P.shape, m["iters"], inner=m["inner"], pcg=args.solver == "pcg")
         line = {
             "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"],
@@ -684,7 +692,7 @@ def main():
             "config": {"workload": WORKLOADS[args.workload]["desc"], "grid": list(P.shape),
                        "bc": list(P.bc), "density_ratio": P.ratio, "tol": TOL,
                        "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
-                       "prolongation": args.prolongation,
+                       "prolongation": args.prolongation, "solver": args.solver,
                        "step": "set density (faces, coarse faces, coarsest inverse) + cold-start solve",
                        "l2": "flushed before every step (256 MB write, outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single"},
