@@ -58,6 +58,8 @@ def lib():
         L.oracle_pcg_solve.argtypes = [G, P, P, P, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, P,
                                        ctypes.POINTER(ctypes.c_int)]
+        L.oracle_gmres.argtypes = [G, P, P, P, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int)]
         L.oracle_gamma.argtypes = [P, ctypes.c_int]
         L.oracle_gamma.restype = ctypes.c_double
         _lib = L
@@ -217,6 +219,19 @@ def coarse_solve(shape, bc, faces, r, length=(1.0, 1.0, 1.0)):
     if st != 0:
         raise RuntimeError("oracle coarse solve failed: %d" % st)
     return e
+
+
+def gmres(shape, bc, faces, r, tol=1e-12, max_it=500, m=30, length=(1.0, 1.0, 1.0)):
+    """Restarted GMRES(m) for A e = r - mean(r); returns (e with zero mean,
+    status 0 converged / 1 not, Arnoldi steps)."""
+    g = grid(shape, bc, length)
+    f = [_arr(a, shape) for a in faces]
+    r = _arr(r, shape)
+    e = np.empty(_cells(shape))
+    its = ctypes.c_int(0)
+    st = lib().oracle_gmres(ctypes.byref(g), *[_ptr(a) for a in f], _ptr(r), _ptr(e), float(tol), int(max_it),
+                            int(m), ctypes.byref(its))
+    return e, st, its.value
 
 
 class SolveResult:

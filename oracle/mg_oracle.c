@@ -39,7 +39,10 @@
  *  - SOR relaxation factor omega is a parameter (1 = Gauss-Seidel); red cells
  *    are those with (i+j+k) even and are relaxed first;
  *  - the coarsest-grid solve (GMRES in the paper, (6)) is an exact dense solve
- *    of the bordered system [-A 1; 1^T 0][e; l] = [-r; 0];
+ *    of the bordered system [-A 1; 1^T 0][e; l] = [-r; 0] on coarsest grids of
+ *    at most 512 cells; larger coarsest grids (sizes with a large odd factor)
+ *    are solved by restarted GMRES (oracle_gmres) to a relative residual of
+ *    1e-13, the solution projected to zero mean;
  *  - coarsening of all three axes continues while every axis is even and > 4;
  *  - flux-conserving prolongation (4), Eqs. 13-14: Eq. 13 as printed does not
  *    give a convex weighting; it is read as continuity of the flux alpha de/dx
@@ -577,6 +580,97 @@ int oracle_coarse_solve(const og_grid *g, const double *ax, const double *ay, co
     return status;
 }
 
+/* Restarted GMRES(m) (Saad & Schultz 1986) for A e = r - mean(r) on a grid
+ * with walls or periodic axes (A singular, the system consistent): Arnoldi
+ * with modified Gram-Schmidt, Givens rotations on the Hessenberg matrix, the
+ * least-squares update at the end of each cycle or on convergence; e starts
+ * at 0 and is returned with zero mean.  Stops when ||r - A e|| <= tol ||r||
+ * (the recurrence's residual estimate) or after max_it Arnoldi steps.
+ * Returns 0 converged, 1 not converged; *iters = Arnoldi steps. */
+int oracle_gmres(const og_grid *g, const double *ax, const double *ay, const double *az,
+                 const double *r_in, double *e, double tol, int max_it, int m, int *iters)
+{
+    long n = cell_count(g);
+    size_t bytes = sizeof(double) * (size_t)n;
+    double *b = (double *)malloc(bytes), *w = (double *)malloc(bytes), *res = (double *)malloc(bytes);
+    double *V = (double *)malloc(bytes * (size_t)(m + 1));
+    double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
+    double *cs = (double *)malloc(sizeof(double) * m), *sn = (double *)malloc(sizeof(double) * m);
+    double *gv = (double *)malloc(sizeof(double) * (m + 1)), *y = (double *)malloc(sizeof(double) * m);
+    memcpy(b, r_in, bytes);
+    subtract_constant(g, b, oracle_mean(g, b));
+    memset(e, 0, bytes);
+    double bnorm = oracle_norm2(g, b);
+    int status = 1, it = 0;
+    if (bnorm == 0.0) status = 0;
+    while (status == 1 && it < max_it) {
+        /* res = b - A e */
+        oracle_residual(g, ax, ay, az, b, e, res);
+        double beta = oracle_norm2(g, res);
+        if (beta <= tol * bnorm) { status = 0; break; }
+        for (long c = 0; c < n; c++) V[c] = res[c] / beta;
+        for (int i = 0; i <= m; i++) gv[i] = 0.0;
+        gv[0] = beta;
+        int j = 0;
+        for (; j < m && it < max_it; j++) {
+            double *vj = V + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
+            oracle_apply(g, ax, ay, az, vj, w);
+            for (int i = 0; i <= j; i++) {
+                const double *vi = V + (size_t)i * n;
+                double h = 0.0;
+                for (long c = 0; c < n; c++) h += w[c] * vi[c];
+                H[i * m + j] = h;
+                for (long c = 0; c < n; c++) w[c] -= h * vi[c];
+            }
+            double hn = oracle_norm2(g, w);
+            H[(j + 1) * m + j] = hn;
+            for (long c = 0; c < n; c++) vn[c] = hn > 0.0 ? w[c] / hn : 0.0;
+            /* previous rotations, then a new one that zeroes H[j+1][j] */
+            for (int i = 0; i < j; i++) {
+                double a = H[i * m + j], bb = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[j * m + j], bb = H[(j + 1) * m + j];
+            double den = sqrt(a * a + bb * bb);
+            cs[j] = den > 0.0 ? a / den : 1.0;
+            sn[j] = den > 0.0 ? bb / den : 0.0;
+            H[j * m + j] = den;
+            H[(j + 1) * m + j] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            it++;
+            if (fabs(gv[j + 1]) <= tol * bnorm || hn == 0.0) { j++; break; }
+        }
+        /* y = H(0:j, 0:j)^-1 g(0:j), e += V y */
+        for (int i = j - 1; i >= 0; i--) {
+            double s2 = gv[i];
+            for (int k = i + 1; k < j; k++) s2 -= H[i * m + k] * y[k];
+            y[i] = H[i * m + i] != 0.0 ? s2 / H[i * m + i] : 0.0;
+        }
+        for (int i = 0; i < j; i++) {
+            const double *vi = V + (size_t)i * n;
+            for (long c = 0; c < n; c++) e[c] += y[i] * vi[c];
+        }
+    }
+    if (status == 1) {
+        oracle_residual(g, ax, ay, az, b, e, res);
+        if (oracle_norm2(g, res) <= tol * bnorm) status = 0;
+    }
+    subtract_constant(g, e, oracle_mean(g, e));
+    *iters = it;
+    free(b);
+    free(w);
+    free(res);
+    free(V);
+    free(H);
+    free(cs);
+    free(sn);
+    free(gv);
+    free(y);
+    return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* V-cycle and the outer iteration with the stopping test / Eq. 15            */
 /* ------------------------------------------------------------------------ */
@@ -649,8 +743,13 @@ static void smooth(const og_hier *H, const og_level *L, int sweeps)
 static int vcycle(og_hier *H, int l)
 {
     og_level *L = &H->lev[l];
-    if (l == H->nlev - 1)
-        return oracle_coarse_solve(&L->g, L->a[0], L->a[1], L->a[2], L->b, L->x);
+    if (l == H->nlev - 1) {
+        if (cell_count(&L->g) <= 512)
+            return oracle_coarse_solve(&L->g, L->a[0], L->a[1], L->a[2], L->b, L->x);
+        int its;
+        oracle_gmres(&L->g, L->a[0], L->a[1], L->a[2], L->b, L->x, 1e-13, 2000, 50, &its);
+        return 0;
+    }
     smooth(H, L, H->nu1);
     og_level *C = &H->lev[l + 1];
     oracle_residual(&L->g, L->a[0], L->a[1], L->a[2], L->b, L->x, L->r);

@@ -678,3 +678,45 @@ def test_pcg_converges_on_drop_film(ratio):
     r = oracle.pcg_solve(P.shape, P.bc, faces, P.rhs, tol=1e-10)
     mg = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=1e-10)
     assert r.status == 0 and r.gamma < 0.5 and r.cycles <= mg.cycles
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 item 6: GMRES on the coarsest grid (next rows: coarsest grids above
+# the dense solver's 512 cells)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc", BCS)
+def test_gmres_matches_dense_coarse_solve(bc):
+    shape = (9, 7, 5)
+    rng = np.random.default_rng(41)
+    f = [rng.uniform(0.05, 1.0, size=cells(shape)) for _ in range(3)]
+    r = rng.standard_normal(cells(shape))
+    e, st, its = oracle.gmres(shape, bc, f, r, tol=1e-13, max_it=2000, m=50)
+    want = oracle.coarse_solve(shape, bc, f, r)
+    assert st == 0
+    np.testing.assert_allclose(e, want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+def test_gmres_finite_termination():
+    """Without restarts GMRES is exact after as many steps as the Krylov space
+    has dimensions: 2 x 2 x 2 with alpha = 1 has 3 distinct nonzero eigenvalues."""
+    shape, bc = (2, 2, 2), (0, 0, 0)
+    r = np.random.default_rng(1).standard_normal(cells(shape))
+    e, st, its = oracle.gmres(shape, bc, ones_faces(shape), r, tol=1e-13, max_it=20, m=20)
+    assert st == 0 and its <= 3
+    np.testing.assert_allclose(oracle.apply(shape, bc, ones_faces(shape), e), r - r.mean(), atol=1e-12)
+
+
+@pytest.mark.parametrize("shape,bc", [((9, 9, 9), (0, 0, 0)), ((18, 18, 14), (1, 0, 1))])
+def test_solve_with_gmres_coarsest_matches_dense_direct(shape, bc):
+    """Coarsest grids above 512 cells (9^3 single level; 9 x 9 x 7 under
+    18 x 18 x 14) take the GMRES coarse solve; the result is still p*."""
+    rng = np.random.default_rng(sum(shape))
+    c = rng.uniform(0.3, 0.7, size=3)
+    rho = I.density_field(shape, None, [(tuple(c), 0.3)], 1000.0, eps_cells=1.0)
+    faces = oracle.faces_from_density(shape, bc, rho)
+    b = rng.standard_normal(cells(shape))
+    want = dense_solution(shape, bc, faces, b)
+    got = oracle.solve_exact(shape, bc, faces, b, max_cycles=200)
+    assert got.status in (0, 2)
+    assert np.linalg.norm(got.x - want) <= 1e-11 * np.linalg.norm(want)
