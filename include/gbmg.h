@@ -30,10 +30,13 @@
  * with zero mean.
  *
  * Size rule.  Every axis has n >= 2 cells and the grid fewer than 2^31 cells.
- * All axes are coarsened together while every axis is even and larger than 2;
- * the coarsest grid must have at most MG_MAX_COARSE cells (it is solved
- * exactly).  Every n = m * 2^k with m in {1, 2, 3, 4} qualifies (2, 3, 4, 6, 8,
- * 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, ...).
+ * All axes are coarsened together while every axis is even and larger than 2.
+ * A coarsest grid of at most MG_MAX_COARSE cells is solved exactly (dense
+ * inverse); a larger one, up to MG_MAX_COARSE_GMRES cells, by restarted GMRES
+ * (Sec. 2.3 item 6).  Every n = m * 2^k with m in {1, 2, 3, 4} has an exact
+ * coarsest solve (2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256,
+ * 384, 512, 768, 1024, ...); sizes with a larger odd factor (e.g. 100 = 25 * 4)
+ * take GMRES.
  *
  * Ownership.  The caller owns every buffer it passes.  Device pointers are
  * device memory of the current CUDA device.  A handle owns its hierarchy (all
@@ -90,7 +93,12 @@ extern "C" {
 #define MG_FACE_HARMONIC 0   /* Eqs. 11-12: 2 a_L a_R / (a_L + a_R), a = 1/rho */
 #define MG_FACE_ARITHMETIC 1 /* (a_L + a_R) / 2 */
 
-#define MG_MAX_COARSE 512 /* most cells allowed on the coarsest grid */
+#define MG_MAX_COARSE 512 /* most cells of a coarsest grid solved by the dense inverse */
+#define MG_MAX_COARSE_GMRES 32768 /* most cells of any coarsest grid (GMRES above MG_MAX_COARSE) */
+#define MG_GMRES_RESTART 30 /* Krylov vectors per GMRES cycle on the coarsest grid */
+
+#define MG_COARSE_AUTO 0  /* coarsest solve: dense inverse up to MG_MAX_COARSE cells, else GMRES */
+#define MG_COARSE_GMRES 1 /* coarsest solve: restarted GMRES whatever the size */
 #define MG_STATIC_MAX_CELLS 512 /* most cells of a grid solved by mg_coarse_solve_static */
 #define MG_MAX_LEVELS 16
 
@@ -128,6 +136,9 @@ typedef struct {
     int tiles;         /* launch shapes of the V-cycle kernels: MG_TILES_AUTO (autotuned per
                           level), MG_TILES_ROWS, or a variant 1 .. MG_TILE_VARIANTS - 1 for
                           every level whose rows are a multiple of 4 cells */
+    int coarse_solver;     /* MG_COARSE_AUTO (default) or MG_COARSE_GMRES */
+    int coarse_max_iters;  /* GMRES: most Arnoldi steps per coarsest solve (default 300) */
+    double coarse_tol;     /* GMRES: relative residual of the coarsest solve (default 1e-8); FP64 */
 } mg_params;
 
 typedef struct {

@@ -60,7 +60,7 @@ int make_levels(const mg_grid &g, int n[][3], int *L)
     }
     *L = l;
     const long long nc = (long long)n[l - 1][0] * n[l - 1][1] * n[l - 1][2];
-    return nc <= kMaxCoarse ? MG_OK : MG_EINVAL;
+    return nc <= kMaxCoarseGmres ? MG_OK : MG_EINVAL;
 }
 
 int check_grid(const mg_grid *g)
@@ -88,6 +88,9 @@ int check_params(const mg_params *p)
     if (p->tiles < MG_TILES_AUTO || p->tiles >= MG_TILE_VARIANTS) return MG_EINVAL;
     if (p->prolongation != MG_PROLONG_TRILINEAR && p->prolongation != MG_PROLONG_FLUX) return MG_EINVAL;
     if (p->solver != MG_SOLVER_MG && p->solver != MG_SOLVER_PCG) return MG_EINVAL;
+    if (p->coarse_solver != MG_COARSE_AUTO && p->coarse_solver != MG_COARSE_GMRES) return MG_EINVAL;
+    if (p->coarse_max_iters < 1 || p->coarse_max_iters > 100000) return MG_EINVAL;
+    if (!(p->coarse_tol > 0.0 && p->coarse_tol < 1.0)) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -99,6 +102,8 @@ struct Layout {
     size_t alpha64[MG_MAX_LEVELS], alpha32[MG_MAX_LEVELS];
     size_t G, b0, part, err, state, dstate, dview, dstart, dcview, setup_cv, total;
     size_t pcg[4];
+    bool gmres;
+    size_t gm;
     int nblk0;
 };
 
@@ -121,7 +126,10 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
     }
     const int *nc = lay.n[lay.L - 1];
     const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
-    lay.G = c.take(ncells * ncells * 8);
+    // dense inverse for small coarsest grids, GMRES scratch otherwise
+    lay.gmres = p.coarse_solver == MG_COARSE_GMRES || ncells > (size_t)kMaxCoarse;
+    lay.G = lay.gmres ? 0 : c.take(ncells * ncells * 8);
+    lay.gm = lay.gmres ? c.take((size_t)(kGmresM + 4) * ncells * 8) : 0;
     const size_t N0 = (size_t)g.nx * g.ny * g.nz;
     lay.b0 = c.take(N0 * 8);
     for (int v = 0; v < 4; v++) lay.pcg[v] = p.solver == MG_SOLVER_PCG ? c.take(N0 * 8) : 0;
@@ -311,6 +319,7 @@ int Plan::fill(mg_handle *const *handles, int count)
     tail_smem = 0;
     ntv = 0;
     ncv = 0;
+    cv_dense = cv_gmres = false;
     for (int g = 0; g < G; g++) {
         mg_handle *h = hs[g];
         if (lt[g] >= h->L) continue;
@@ -359,6 +368,12 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.err = h->err + 1;
         v.g = g;
         v.outer = h->L == 1 ? 1 : 0;
+        v.gmres = h->gmres ? 1 : 0;
+        v.gm = h->gm;
+        v.gm_max = h->prm.coarse_max_iters;
+        v.gm_tol = h->prm.coarse_tol;
+        if (h->gmres) cv_gmres = true;
+        else cv_dense = true;
     }
     for (int g = 0; g < G; g++) {
         mg_handle *h = hs[g];
@@ -473,7 +488,8 @@ static void vcycle(Plan &P, Prof &pf, int cycle_in_step, bool last_of_step)
     }
     if (P.ncv) {
         pf.begin(s, MG_K_COARSE, P.Lmax - 1);
-        launch_coarse_solve<T>(P.cv, P.ncv, last_of_step ? P.ov : nullptr, s);
+        if (P.cv_dense) launch_coarse_solve<T>(P.cv, P.ncv, last_of_step ? P.ov : nullptr, s);
+        if (P.cv_gmres) launch_coarse_gmres<T>(P.cv, P.ncv, last_of_step ? P.ov : nullptr, s);
         pf.end(s);
     }
     for (int l = P.Lmax - 2; l >= 0; l--) {
@@ -787,7 +803,7 @@ static int upload_faces(mg_handle *h)
             launch_cell_alpha(c, h->stream);
         }
     }
-    launch_coarse_setup(h->setup_cv, 1, h->stream);
+    if (!h->gmres) launch_coarse_setup(h->setup_cv, 1, h->stream);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -882,7 +898,9 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
         L.alpha32 = lay.alpha32[l] ? (float *)(h->slab + lay.alpha32[l]) : nullptr;
         L.b = h->slab + lay.b[l];
     }
-    h->G = (double *)(h->slab + lay.G);
+    h->gmres = lay.gmres;
+    h->G = lay.gmres ? nullptr : (double *)(h->slab + lay.G);
+    h->gm = lay.gmres ? (double *)(h->slab + lay.gm) : nullptr;
     h->b0 = (double *)(h->slab + lay.b0);
     for (int v = 0; v < 4; v++) h->pcg[v] = lay.pcg[v] ? (double *)(h->slab + lay.pcg[v]) : nullptr;
     h->part = (double *)(h->slab + lay.part);
@@ -971,6 +989,9 @@ int mg_params_default(mg_params *p)
     p->tiles = MG_TILES_AUTO;
     p->prolongation = MG_PROLONG_TRILINEAR;
     p->solver = MG_SOLVER_MG;
+    p->coarse_solver = MG_COARSE_AUTO;
+    p->coarse_max_iters = 300;
+    p->coarse_tol = 1e-8;
     return MG_OK;
 }
 
@@ -1384,9 +1405,18 @@ int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e)
     v.b = r;
     v.st = h->dstate;
     v.err = h->err + 1;
+    v.gmres = h->gmres ? 1 : 0;
+    v.gm = h->gm;
+    v.gm_max = h->prm.coarse_max_iters;
+    v.gm_tol = h->prm.coarse_tol;
     CK(cudaMemcpyAsync(h->dcview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
-    if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, nullptr, h->stream);
-    else launch_coarse_solve<double>(h->dcview, 1, nullptr, h->stream);
+    if (h->gmres) {
+        if (prec == MG_PREC_MIXED) launch_coarse_gmres<float>(h->dcview, 1, nullptr, h->stream);
+        else launch_coarse_gmres<double>(h->dcview, 1, nullptr, h->stream);
+    } else {
+        if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, nullptr, h->stream);
+        else launch_coarse_solve<double>(h->dcview, 1, nullptr, h->stream);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return MG_OK;

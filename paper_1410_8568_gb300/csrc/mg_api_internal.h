@@ -87,6 +87,8 @@ struct mg_handle {
     double *io_rhs = nullptr, *io_p = nullptr, *io_rho = nullptr;  // host-call staging
     signed char tile[3][MG_MAX_LEVELS] = {};  // launch shape per kernel (MG_TILE_*) and level
     double *pcg[4] = {nullptr, nullptr, nullptr, nullptr};  // CG: r, z, d, q (FP64, finest level)
+    bool gmres = false;        // coarsest grid solved by GMRES (no dense inverse)
+    double *gm = nullptr;      // GMRES scratch
 };
 
 namespace gbmg {
@@ -106,6 +108,7 @@ struct Plan {
     Table half[MG_MAX_LEVELS];  // red-black half-sweeps of level l
     CoarseView *cv = nullptr;   // coarsest solves of the grids without a tail
     int ncv = 0;
+    bool cv_dense = false, cv_gmres = false;  // which coarse kernels the cv table needs
     TailView *tv = nullptr;     // bottom-of-cycle blocks of the grids with a tail
     int ntv = 0;
     size_t tail_smem = 0;

@@ -18,6 +18,8 @@ constexpr int kRowsPerBlock = 8;  // one grid row (fixed j, k) per warp
 constexpr int kSeg = 64;          // x extent of a warp's row segment (2 cells per lane)
 constexpr int kCSeg = 32;         // x extent of a warp's coarse row segment (restriction)
 constexpr int kMaxCoarse = 512;   // most cells of the coarsest grid (dense inverse)
+constexpr int kMaxCoarseGmres = 32768;  // most cells of a coarsest grid solved by GMRES
+constexpr int kGmresM = 30;       // Krylov vectors per GMRES cycle
 constexpr int kPart = 4;          // doubles of reduction partials per block
 constexpr int kOuterCap = 608;    // most blocks of one grid in an outer (FP64) launch: 4 per SM
 
@@ -150,6 +152,10 @@ struct CoarseView {
     int *err;            // set-up error flag (non-positive pivot)
     int g;               // index of the grid in its plan
     int outer;           // 1 if this is also the finest level (x += e happens here)
+    int gmres;           // 1: solved by restarted GMRES (G unused)
+    double *gm;          // GMRES scratch: b, e, w, then kGmresM + 1 Krylov vectors (FP64, nc each)
+    int gm_max;          // most Arnoldi steps
+    double gm_tol;       // relative residual
 };
 
 // Bottom of the V-cycle in one block per grid (levels of at most kTailCells

@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__r
                                                            const OuterView *__restrict__ ov)
 {
     const CoarseView &C = cv[blockIdx.x];
-    if (!C.st->active) return;
+    if (C.gmres || !C.st->active) return;  // GMRES grids: k_coarse_gmres
     __shared__ double rb[kMaxCoarse];
     const int n = C.nc;
     const T *b = (const T *)C.b;

@@ -93,6 +93,7 @@ template <class T> void launch_tail(const TailView *, int count, size_t smem, do
                                     int nu2, cudaStream_t);
 template <class T> void launch_apply(const Table &, cudaStream_t);
 template <class T> void launch_coarse_solve(const CoarseView *, int count, const OuterView *ov, cudaStream_t);
+template <class T> void launch_coarse_gmres(const CoarseView *, int count, const OuterView *ov, cudaStream_t);
 void launch_coarse_setup(const CoarseView *, int count, cudaStream_t);
 void launch_faces_from_density(const FaceArgs &, cudaStream_t);
 void launch_scale_faces(const FaceArgs &, cudaStream_t);

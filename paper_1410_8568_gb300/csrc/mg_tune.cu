@@ -48,7 +48,7 @@ namespace gbmg {
 // that of the per-level FP64 kernels spread over all SMs.
 int first_tail_level(const mg_handle *h)
 {
-    if (!h->mixed) return h->L;
+    if (!h->mixed || h->gmres) return h->L;  // the tail solves the coarsest grid with its inverse
     for (int l = 1; l + 1 < h->L && l < MG_MAX_LEVELS; l++)
         if (h->lev[l].N <= kTailCells && h->L - l <= kMaxTail) return l;
     return h->L;

@@ -28,6 +28,8 @@ K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL = range(7
 TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
 PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
 SOLVER_MG, SOLVER_PCG = 0, 1
+COARSE_AUTO, COARSE_GMRES = 0, 1
+MAX_COARSE, MAX_COARSE_GMRES = 512, 32768
 TILE_HALF, TILE_RESTRICT, TILE_PROLONG = 0, 1, 2
 
 
@@ -47,7 +49,8 @@ class Params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("solver", ctypes.c_int), ("prolongation", ctypes.c_int),
-                ("tiles", ctypes.c_int)]
+                ("tiles", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_max_iters", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -151,7 +154,8 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
 
 
 def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
-                inner_cycles=None, tiles=None, prolongation=None, solver=None) -> Params:
+                inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
+                coarse_tol=None, coarse_max_iters=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
@@ -166,6 +170,12 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
         p.prolongation = int(prolongation)
     if solver is not None:
         p.solver = int(solver)
+    if coarse_solver is not None:
+        p.coarse_solver = int(coarse_solver)
+    if coarse_tol is not None:
+        p.coarse_tol = float(coarse_tol)
+    if coarse_max_iters is not None:
+        p.coarse_max_iters = int(coarse_max_iters)
     return p
 
 
@@ -243,7 +253,8 @@ class Solver:
 
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
                  precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
-                 inner_cycles=None, tiles=None, prolongation=None, solver=None):
+                 inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
+                 coarse_tol=None, coarse_max_iters=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -253,7 +264,7 @@ class Solver:
         self.precision = precision
         self.grid = make_grid(self.shape, self.bc, self.length)
         self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles,
-                                  prolongation, solver)
+                                  prolongation, solver, coarse_solver, coarse_tol, coarse_max_iters)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:

@@ -46,9 +46,11 @@ def test_host_only_calls():
     assert (p.nu1, p.nu2, p.omega, p.precision, p.use_graph) == (2, 2, 1.0, gbmg.MIXED, 1)
     est = gbmg.memory_estimate((64, 64, 64), (1, 1, 0))
     assert 64 ** 3 * 52 < est < 64 ** 3 * 70
-    # coarsest grid too large: 2 x 2 x 256 cannot be coarsened to <= 512 cells
+    # a coarsest grid above 512 cells takes GMRES (2 x 2 x 256 cannot be coarsened) ...
+    assert gbmg.memory_estimate((2, 2, 256), (0, 0, 0)) > 0
+    # ... up to 32768 cells
     with pytest.raises(gbmg.MGError) as e:
-        gbmg.memory_estimate((2, 2, 256), (0, 0, 0))
+        gbmg.memory_estimate((2, 2, 16384), (0, 0, 0))
     assert e.value.code == gbmg.EINVAL
     with pytest.raises(gbmg.MGError):
         gbmg.memory_estimate((1, 8, 8), (0, 0, 0))

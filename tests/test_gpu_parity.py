@@ -317,8 +317,8 @@ def test_edge_cases():
     with pytest.raises(gbmg.MGError) as e:
         solver_for(P, bad)
     assert e.value.code == gbmg.EINVAL
-    with pytest.raises(gbmg.MGError):
-        gbmg.Solver((2, 2, 256), (0, 0, 0), faces=[torch.ones(2 * 2 * 256, dtype=torch.float64, device="cuda")] * 3)
+    with pytest.raises(gbmg.MGError):  # coarsest grid above MG_MAX_COARSE_GMRES cells
+        gbmg.Solver((2, 2, 16384), (0, 0, 0), faces=[torch.ones(2 * 2 * 16384, dtype=torch.float64, device="cuda")] * 3)
 
 
 def test_host_entry_points_match_device_path():
