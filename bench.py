@@ -74,6 +74,22 @@ PROLONG = {"trilinear": 0, "flux": 1}
 SOLVER = {"mg": 0, "pcg": 1}
 
 
+def reduce_max(value, dist):
+    """Largest value over the ranks: the job takes as long as its slowest rank."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(world, units_per_rank, total_ms):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / (total_ms / 1000.0)
+
+
 def make_problem(name):
     from paper_1410_8568_gb300 import inputs as I
     w = WORKLOADS[name]
@@ -294,15 +310,12 @@ def run_projection(args, rank, world, local_rank, dist):
             stream.synchronize()
         times = [a.elapsed_time(b) for a, b in ev]
         tot = sum(times)
-        if dist is not None:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = t.item()
+        tot = reduce_max(tot, dist)
         # divergence left in the projected field, relative to the field's before
         div = torch.empty_like(rho)
         S.divergence(u, 1.0, div)
         S.divergence(u0, 1.0, src)
-        res[prec] = dict(value=world * args.steps / (tot / 1000.0), ms=tot / args.steps,
+        res[prec] = dict(value=job_value(world, args.steps, tot), ms=tot / args.steps,
                          p50=statistics.median(times), p99=float(np.percentile(times, 99)), iters=st.iters,
                          div_ratio=(torch.linalg.vector_norm(div) / torch.linalg.vector_norm(src)).item())
         S.close()
@@ -365,10 +378,7 @@ def run_batch(args, rank, world, local_rank, dist):
         if bad:
             raise RuntimeError("batch solve failed: %s" % bad)
         tot = sum(times)
-        if dist is not None:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = t.item()
+        tot = reduce_max(tot, dist)
         errs = []
         if rank == 0:
             # error against the oracle's p* on the 4 smallest grids of the batch
@@ -378,7 +388,7 @@ def run_batch(args, rank, world, local_rank, dist):
                 pstar = oracle.solve_exact(P.shape, P.bc, f, P.rhs).x
                 x = ps[g].cpu().numpy()
                 errs.append(float(np.linalg.norm(x - pstar) / np.linalg.norm(pstar)))
-        res[prec] = dict(ms=tot / args.steps, value=world * 64 * args.steps / (tot / 1000.0),
+        res[prec] = dict(ms=tot / args.steps, value=job_value(world, 64 * args.steps, tot),
                          p50=statistics.median(times), p99=float(np.percentile(times, 99)),
                          iters=[st.iters for st in sts], err=max(errs) if errs else None)
         B.close()
@@ -597,11 +607,8 @@ def main():
         if clocks:
             results["clocks"] = clocks.stop()
         tot = sum(times)
-        if dist is not None:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = t.item()
-        results[prec] = dict(ms=tot / args.steps, value=world * args.steps / (tot / 1000.0),
+        tot = reduce_max(tot, dist)
+        results[prec] = dict(ms=tot / args.steps, value=job_value(world, args.steps, tot),
                              p50=statistics.median(times), p99=float(np.percentile(times, 99)),
                              iters=st.iters, gamma=st.gamma, rel_res=st.rel_res, wall=wall,
                              levels=S.num_levels(), p=p, inner=S.resolved_params()["inner_cycles"])
@@ -621,10 +628,7 @@ def main():
     timed(S, 2, host=True)
     e2e_times, _, _ = timed(S, args.steps, host=True)
     e2e_tot = sum(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = t.item()
+    e2e_tot = reduce_max(e2e_tot, dist)
 
     # roofline of the dominant kernel: finest-level half-sweep, per-launch events
     v0 = S.tile_choice(gbmg.TILE_HALF, 0)
@@ -703,7 +707,7 @@ def main():
                      "p99_ms": f["p99"], "iters": f["iters"], "inner_cycles": f["inner"], "gamma": f["gamma"], "rel_res": f["rel_res"],
                      "err_vs_oracle": errors.get(gbmg.FP64)},
             "mixed_over_fp64": m["value"] / f["value"],
-            "e2e": {"value": world * args.steps / (e2e_tot / 1000.0), "unit": "solves/s",
+            "e2e": {"value": job_value(world, args.steps, e2e_tot), "unit": "solves/s",
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
