@@ -676,6 +676,15 @@ def main():
             dt, r = cpu_oracle_solve(P, faces)
             cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
                    "sample": "1 full FP64 oracle solve of the workload to 1e-10 (%d V(2,2) cycles)" % r.cycles}
+            # the same on one host core: 2 cycles, scaled to the solve's cycles
+            cores = oracle.num_threads()
+            oracle.set_threads(1)
+            t = time.perf_counter()
+            oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=2)
+            dt1 = (time.perf_counter() - t) * r.cycles / 2.0
+            oracle.set_threads(cores)
+            cpu["single_core"] = {"value": 1.0 / dt1, "unit": "solves/s", "ms_per_solve": 1000.0 * dt1,
+                                  "sample": "2 oracle V(2,2) cycles on 1 thread, scaled to %d cycles" % r.cycles}
         else:
             # bounded sample: 2 oracle cycles, scaled by the GPU solve's cycle count
             t = time.perf_counter()

@@ -35,6 +35,8 @@ def lib():
         P = ctypes.POINTER(ctypes.c_double)
         G = ctypes.POINTER(_Grid)
         L.oracle_num_threads.restype = ctypes.c_int
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        L.oracle_set_threads.restype = ctypes.c_int
         L.oracle_faces_from_density.argtypes = [G, P, ctypes.c_int, P, P, P]
         L.oracle_apply.argtypes = [G, P, P, P, P, P]
         L.oracle_residual.argtypes = [G, P, P, P, P, P, P]
@@ -68,6 +70,11 @@ def lib():
 
 def num_threads() -> int:
     return lib().oracle_num_threads()
+
+
+def set_threads(n: int) -> int:
+    """Threads of the following oracle calls; returns the number in effect."""
+    return lib().oracle_set_threads(int(n))
 
 
 def grid(shape, bc, length=(1.0, 1.0, 1.0)) -> _Grid:

@@ -106,6 +106,18 @@ int oracle_num_threads(void)
 #endif
 }
 
+/* Threads of the following calls (n >= 1); returns the number in effect. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Coefficient of the face of cell (i,j,k) on side `side` (-1 low, +1 high) of
  * axis d, and the index of the cell across that face.  Returns 0 for a wall. */
 static double face_coef(const og_grid *g, const double *const a[3], int i, int j, int k,
