@@ -200,9 +200,10 @@ def level_shapes(shape):
     return out
 
 
-def count_launches(shape, iters, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=True, pcg=False):
-    """Kernels of one step: coefficient set-up, prologue, refinement (or CG) steps, epilogue.
-    In FP32 cycles the levels of at most tail_cells cells (below the finest) run in one launch."""
+def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=True, pcg=False):
+    """Kernels of one solve step: coefficient set-up, prologue, refinement (or CG) steps, epilogue.
+    In FP32 cycles the levels of at most tail_cells cells (below the finest) run in one launch;
+    with more than one V-cycle per refinement step each step starts with a step-control kernel."""
     lv = level_shapes(shape)
     L = len(lv)
     lt = next((l for l in range(1, L - 1) if math.prod(lv[l]) <= tail_cells), L) if mixed else L
@@ -212,11 +213,11 @@ def count_launches(shape, iters, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=T
     cycle = normal * (2 * nu1 + 1 + 1 + 2 * nu2) + 1  # half-sweeps, restriction, prolongation; tail or coarsest
     if pcg:
         prologue += inner * cycle + 3  # first preconditioning: V-cycles, z and its sums, direction
-        step = 4 + inner * cycle + 3 + 1  # A d, alpha, update, test; V-cycles, z, beta, direction; loop control
+        per_step = 4 + 3 + 1           # A d, alpha, update, test; z, beta, direction; loop control
     else:
-        step = inner * cycle + 3       # + residual, finalize, loop control
+        per_step = 4 + (1 if inner > 1 else 0)  # p += e, residual, finalize, loop control (+ step control)
     epilogue = 3                       # sum p, mean, p - mean
-    return setup + prologue + (iters // inner) * step + epilogue
+    return setup + prologue + iters * cycle + steps * per_step + epilogue
 
 
 def cpu_oracle_solve(P, faces, tol=TOL):
@@ -611,7 +612,8 @@ def main():
         results[prec] = dict(ms=tot / args.steps, value=job_value(world, args.steps, tot),
                              p50=statistics.median(times), p99=float(np.percentile(times, 99)),
                              iters=st.iters, gamma=st.gamma, rel_res=st.rel_res, wall=wall,
-                             levels=S.num_levels(), p=p, inner=S.resolved_params()["inner_cycles"])
+                             levels=S.num_levels(), p=p, inner=S.resolved_params()["inner_cycles"],
+                             steps=st.steps)
 
     # error of each result against the FP64 oracle's converged solution (small grids only)
     errors = {}
@@ -649,11 +651,13 @@ def main():
     # the other level-0 kernels of the cycle, algorithmic bytes per finest cell:
     # restriction reads x, b, 3 faces (FP32) and writes the coarse b (1/8 cell);
     # prolongation reads and writes x and reads the coarse correction (1/8);
-    # the FP64 residual reads p, b0 and 3 FP64 faces and writes r (FP32)
+    # the FP64 residual reads p, b0 and 3 FP64 faces and writes r (FP32);
+    # the update p += e reads e (FP32) and reads and writes p
     per_kernel = {}
     for name, kind, bpc, bound in (("restrict", gbmg.K_RESTRICT, 20.5, "hbm"),
                                    ("prolong", gbmg.K_PROLONG, 8.5, "hbm"),
-                                   ("residual_fp64", gbmg.K_RESIDUAL, 44.0, "fp64 alu")):
+                                   ("residual_fp64", gbmg.K_RESIDUAL, 44.0, "fp64 alu"),
+                                   ("update_fp64", gbmg.K_UPDATE, 20.0, "hbm")):
         n_k, ms_k = S.profile_read(kind, 0)
         if n_k:
             us = 1000.0 * ms_k / n_k
@@ -696,7 +700,8 @@ def main():
 
     if rank == 0:
         m, f = results[gbmg.MIXED], results[gbmg.FP64]
-        launches = args.steps * count_launches(P.shape, m["iters"], inner=m["inner"], pcg=args.solver == "pcg")
+        launches = args.steps * count_launches(P.shape, m["iters"], m["steps"], inner=m["inner"],
+                                               pcg=args.solver == "pcg")
         line = {
             "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"],
@@ -710,10 +715,11 @@ def main():
                        "l2": "flushed before every step (256 MB write, outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "p50_ms": m["p50"], "p99_ms": m["p99"],
-            "iters": m["iters"], "inner_cycles": m["inner"], "gamma": m["gamma"], "rel_res": m["rel_res"],
+            "iters": m["iters"], "steps": m["steps"], "inner_cycles": m["inner"], "gamma": m["gamma"],
+            "rel_res": m["rel_res"],
             "err_vs_oracle": errors.get(gbmg.MIXED),
             "fp64": {"value": f["value"], "unit": "solves/s", "ms_per_step": f["ms"], "p50_ms": f["p50"],
-                     "p99_ms": f["p99"], "iters": f["iters"], "inner_cycles": f["inner"], "gamma": f["gamma"], "rel_res": f["rel_res"],
+                     "p99_ms": f["p99"], "iters": f["iters"], "steps": f["steps"], "inner_cycles": f["inner"], "gamma": f["gamma"], "rel_res": f["rel_res"],
                      "err_vs_oracle": errors.get(gbmg.FP64)},
             "mixed_over_fp64": m["value"] / f["value"],
             "e2e": {"value": job_value(world, args.steps, e2e_tot), "unit": "solves/s",

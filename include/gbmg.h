@@ -118,8 +118,7 @@ typedef struct {
 typedef struct {
     int nu1, nu2;      /* pre- and post-relaxation sweeps (one sweep = red then black), nu1 >= 1 */
     double omega;      /* SOR factor of the red-black relaxation, 0 < omega < 2 */
-    int max_iters;     /* most V-cycles per solve, rounded up to whole refinement steps
-                          (inner_cycles V-cycles each) */
+    int max_iters;     /* most V-cycles per solve */
     int precision;     /* MG_PREC_FP64 or MG_PREC_MIXED */
     int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
     int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1;
@@ -139,6 +138,10 @@ typedef struct {
     int coarse_solver;     /* MG_COARSE_AUTO (default) or MG_COARSE_GMRES */
     int coarse_max_iters;  /* GMRES: most Arnoldi steps per coarsest solve (default 300) */
     double coarse_tol;     /* GMRES: relative residual of the coarsest solve (default 1e-8); FP64 */
+    int adaptive_cycles;   /* 1 (default): after the first refinement step, each step runs as many
+                              V-cycles (1 .. inner_cycles) as the last step's measured reduction
+                              rate predicts the tolerance needs, with a 10% margin on the rate;
+                              0: always inner_cycles.  Either way a solve stops at max_iters cycles */
 } mg_params;
 
 typedef struct {
@@ -151,6 +154,7 @@ typedef struct {
     double bnorm;       /* ||b - mean(b)||_2 */
     double rhs_mean;    /* mean of the right-hand side that was removed */
     double ms;          /* device time of the solve (stream events), milliseconds */
+    int steps;          /* FP64 refinement steps (residual evaluations after the first) */
 } mg_stats;
 
 typedef struct mg_handle mg_handle;
@@ -377,10 +381,11 @@ int mg_projection_step(mg_handle *h, double *ux, double *uy, double *uz, double 
 #define MG_K_RESTRICT 1
 #define MG_K_PROLONG 2
 #define MG_K_COARSE 3
-#define MG_K_RESIDUAL 4 /* the FP64 outer update + residual + norms */
+#define MG_K_RESIDUAL 4 /* the FP64 residual + norms */
 #define MG_K_OTHER 5
 #define MG_K_TAIL 6 /* the levels of at most 4096 cells and the coarsest solve, one block per grid */
-#define MG_K_KINDS 7
+#define MG_K_UPDATE 7 /* the FP64 update p += e at the end of a refinement step (Sec. 2.3) */
+#define MG_K_KINDS 8
 
 int mg_profile_enable(mg_handle *h, int enable);
 int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double *total_ms);

@@ -91,6 +91,7 @@ int check_params(const mg_params *p)
     if (p->coarse_solver != MG_COARSE_AUTO && p->coarse_solver != MG_COARSE_GMRES) return MG_EINVAL;
     if (p->coarse_max_iters < 1 || p->coarse_max_iters > 100000) return MG_EINVAL;
     if (!(p->coarse_tol > 0.0 && p->coarse_tol < 1.0)) return MG_EINVAL;
+    if (p->adaptive_cycles != 0 && p->adaptive_cycles != 1) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -367,7 +368,6 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.st = h->state;
         v.err = h->err + 1;
         v.g = g;
-        v.outer = h->L == 1 ? 1 : 0;
         v.gmres = h->gmres ? 1 : 0;
         v.gm = h->gm;
         v.gm_max = h->prm.coarse_max_iters;
@@ -397,6 +397,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.d = h->pcg[2];
         v.q = h->pcg[3];
         v.e = h->lev[0].x;
+        v.adaptive = prm.adaptive_cycles;
     }
     CK(cudaMemcpyAsync(mem, stage_h, tables_bytes, cudaMemcpyHostToDevice, stream));
     CK(cudaEventRecord(staged, stream));
@@ -454,70 +455,72 @@ Prof::~Prof()
 
 // ---- the V-cycle and the outer iteration -----------------------------------
 
-// One V(nu1, nu2) cycle over every grid of the plan, red-black half-sweeps in
-// place.  Coarse levels start every cycle from a zero correction (the first
-// red half-sweep takes x = 0).  The finest level starts from zero in the first
-// cycle of a refinement step and from the previous cycle's correction in the
-// next ones.  The last red and black half-sweeps on the finest level in the
-// last cycle of the step add the correction to the FP64 iterate.
+// V-cycle `cyc` (0-based) of a refinement step over every grid of the plan,
+// red-black half-sweeps in place; a grid whose step asks for at most cyc
+// cycles skips every launch of it (in_cycle).  Coarse levels start every cycle
+// from a zero correction (the first red half-sweep takes x = 0).  The finest
+// level starts from zero in the first cycle of a step and from the previous
+// cycle's correction in the next ones.
 template <class T>
-static void vcycle(Plan &P, Prof &pf, int cycle_in_step, bool last_of_step)
+static void vcycle(Plan &P, Prof &pf, int cyc)
 {
     const cudaStream_t s = P.stream;
     const mg_params &q = P.prm;
+    auto at = [cyc](Table t) {
+        t.cyc = cyc;
+        return t;
+    };
     for (int l = 0; l + 1 < P.Lmax; l++) {
-        const Table &H = P.half[l];
+        const Table H = at(P.half[l]);
         if (H.count == 0) continue;
-        const bool zero = !(l == 0 && cycle_in_step > 0);
+        const bool zero = !(l == 0 && cyc > 0);
         for (int it = 0; it < q.nu1; it++) {
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 0, q.omega, (it == 0 && zero) ? kHalfZero : 0, P.ov, s);
+            launch_half<T>(H, 0, q.omega, (it == 0 && zero) ? kHalfZero : 0, s);
             pf.end(s);
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 1, q.omega, 0, P.ov, s);
+            launch_half<T>(H, 1, q.omega, 0, s);
             pf.end(s);
         }
         pf.begin(s, MG_K_RESTRICT, l);
-        launch_restrict<T>(P.rest[l], s);
+        launch_restrict<T>(at(P.rest[l]), s);
         pf.end(s);
     }
     if (P.ntv) {
         pf.begin(s, MG_K_TAIL, 0);
-        launch_tail<T>(P.tv, P.ntv, P.tail_smem, q.omega, q.nu1, q.nu2, s);
+        launch_tail<T>(P.tv, P.ntv, P.tail_smem, q.omega, q.nu1, q.nu2, cyc, s);
         pf.end(s);
     }
     if (P.ncv) {
         pf.begin(s, MG_K_COARSE, P.Lmax - 1);
-        if (P.cv_dense) launch_coarse_solve<T>(P.cv, P.ncv, last_of_step ? P.ov : nullptr, s);
-        if (P.cv_gmres) launch_coarse_gmres<T>(P.cv, P.ncv, last_of_step ? P.ov : nullptr, s);
+        if (P.cv_dense) launch_coarse_solve<T>(P.cv, P.ncv, cyc, s);
+        if (P.cv_gmres) launch_coarse_gmres<T>(P.cv, P.ncv, cyc, s);
         pf.end(s);
     }
     for (int l = P.Lmax - 2; l >= 0; l--) {
-        const Table &H = P.half[l];
+        const Table H = at(P.half[l]);
         if (H.count == 0) continue;
-        const bool outer = l == 0 && last_of_step;
         pf.begin(s, MG_K_PROLONG, l);
-        launch_prolong<T>(P.down[l], P.ov, (outer && q.nu2 == 0) ? 1 : 0, s);
+        launch_prolong<T>(at(P.down[l]), s);
         pf.end(s);
         for (int it = 0; it < q.nu2; it++) {
-            const int fl = (outer && it == q.nu2 - 1) ? kHalfOuter : 0;
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 0, q.omega, fl, P.ov, s);
+            launch_half<T>(H, 0, q.omega, 0, s);
             pf.end(s);
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 1, q.omega, fl, P.ov, s);
+            launch_half<T>(H, 1, q.omega, 0, s);
             pf.end(s);
         }
     }
 }
 
-// Conjugate gradients: z = M r (inner_cycles V-cycles from zero, no update of
+// Conjugate gradients: z = M r (the step's V-cycles from zero, no update of
 // the FP64 iterate), the dot products of z, the new direction.
 template <class T>
 static void pcg_precondition(Plan &P, Prof &pf, int first)
 {
     const cudaStream_t s = P.stream;
-    for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c, false);
+    for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c);
     pf.begin(s, MG_K_OTHER, 0);
     launch_pcg_z<T>(P.ot, s);
     launch_pcg_finalize(P.ot, first ? 0 : 2, s);
@@ -543,11 +546,15 @@ static void prologue(Plan &P, Prof &pf)
     if (P.prm.solver == MG_SOLVER_PCG) pcg_precondition<T>(P, pf, 1);
 }
 
-// One refinement step: inner_cycles V-cycles on A e = r (the first from e = 0,
-// the next ones continuing from the current e), the last one adding e to the
-// FP64 iterate, then the FP64 residual and the stopping test.
+template <class T> static void body_cycles(Plan &P, Prof &pf, int cycles);
+template <class T> static void body_residual(Plan &P, Prof &pf);
+
+// One step of the outer iteration.  Multigrid iteration: up to `cycles`
+// V-cycles on A e = r (the first from e = 0, the next ones continuing from the
+// current e; each grid runs the number its state asks for), p += e in FP64,
+// then the FP64 residual and the stopping test.
 template <class T>
-static void body(Plan &P, Prof &pf)
+static void body(Plan &P, Prof &pf, int cycles)
 {
     const cudaStream_t s = P.stream;
     if (P.prm.solver == MG_SOLVER_PCG) {
@@ -563,7 +570,23 @@ static void body(Plan &P, Prof &pf)
         pcg_precondition<T>(P, pf, 0);
         return;
     }
-    for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c, c == P.prm.inner_cycles - 1);
+    body_cycles<T>(P, pf, cycles);
+    body_residual<T>(P, pf);
+}
+
+template <class T>
+static void body_cycles(Plan &P, Prof &pf, int cycles)
+{
+    for (int c = 0; c < cycles; c++) vcycle<T>(P, pf, c);
+}
+
+template <class T>
+static void body_residual(Plan &P, Prof &pf)
+{
+    const cudaStream_t s = P.stream;
+    pf.begin(s, MG_K_UPDATE, 0);
+    launch_outer_update<T>(P.ot, s);
+    pf.end(s);
     pf.begin(s, MG_K_RESIDUAL, 0);
     launch_residual<T>(P.ot, 0, s);
     pf.end(s);
@@ -608,9 +631,13 @@ static int build_graph(Plan &P)
     prologue<T>(Q, off);
     launch_loop_ctl(cond, Q.ot, cs);
     CK(cudaStreamEndCapture(cs, &pro_g));
-    // loop body
+    // loop body: with a variable number of V-cycles per step (multigrid
+    // iteration, inner_cycles > 1) the body is [step control] -> [switch over
+    // 1 .. inner V-cycles] -> [residual, test, loop control]; else one piece
+    const bool switched = P.prm.solver != MG_SOLVER_PCG && P.prm.inner_cycles > 1;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    body<T>(Q, off);
+    if (switched) body_residual<T>(Q, off);
+    else body<T>(Q, off, P.prm.inner_cycles);
     launch_loop_ctl(cond, Q.ot, cs);
     CK(cudaStreamEndCapture(cs, &body_g));
     // epilogue
@@ -626,7 +653,35 @@ static int build_graph(Plan &P)
     cp.conditional.size = 1;
     CK(cudaGraphAddNode(&n_loop, main_g, &n_pro, nullptr, 1, &cp));
     cudaGraph_t loop_body = cp.conditional.phGraph_out[0];
-    CK(cudaGraphAddChildGraphNode(&n_inner, loop_body, nullptr, 0, body_g));
+    if (switched) {
+        cudaGraphConditionalHandle sw;
+        CK(cudaGraphConditionalHandleCreate(&sw, loop_body, 0, cudaGraphCondAssignDefault));
+        cudaGraph_t ctl_g = nullptr;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        launch_step_ctl(sw, Q.ot, cs);
+        CK(cudaStreamEndCapture(cs, &ctl_g));
+        cudaGraphNode_t n_ctl, n_sw;
+        CK(cudaGraphAddChildGraphNode(&n_ctl, loop_body, nullptr, 0, ctl_g));
+        cudaGraphDestroy(ctl_g);
+        cudaGraphNodeParams sp = {};
+        sp.type = cudaGraphNodeTypeConditional;
+        sp.conditional.handle = sw;
+        sp.conditional.type = cudaGraphCondTypeSwitch;
+        sp.conditional.size = (unsigned int)P.prm.inner_cycles;
+        CK(cudaGraphAddNode(&n_sw, loop_body, &n_ctl, nullptr, 1, &sp));
+        for (int c = 1; c <= P.prm.inner_cycles; c++) {
+            cudaGraph_t cyc_g = nullptr;
+            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            body_cycles<T>(Q, off, c);
+            CK(cudaStreamEndCapture(cs, &cyc_g));
+            cudaGraphNode_t n_c;
+            CK(cudaGraphAddChildGraphNode(&n_c, sp.conditional.phGraph_out[c - 1], nullptr, 0, cyc_g));
+            cudaGraphDestroy(cyc_g);
+        }
+        CK(cudaGraphAddChildGraphNode(&n_inner, loop_body, &n_sw, 1, body_g));
+    } else {
+        CK(cudaGraphAddChildGraphNode(&n_inner, loop_body, nullptr, 0, body_g));
+    }
     CK(cudaGraphAddChildGraphNode(&n_epi, main_g, &n_loop, 1, epi_g));
     cudaGraphDestroy(pro_g);
     cudaGraphDestroy(body_g);
@@ -634,6 +689,16 @@ static int build_graph(Plan &P)
     CK(cudaGraphInstantiate(&P.gexec, main_g, 0));
     P.graph = main_g;
     return MG_OK;
+}
+
+// V-cycles of the next refinement step (host-driven loops, from the states
+// just read back): the most any active grid asks for, as k_step_ctl decides
+static int step_cycles(const Plan &P)
+{
+    int c = 1;
+    for (int g = 0; g < P.G; g++)
+        if (P.st_h[g].active && P.st_h[g].cycles_next > c) c = P.st_h[g].cycles_next;
+    return c;
 }
 
 template <class T>
@@ -661,7 +726,7 @@ static int run_plan_t(Plan &P, Prof &pf, bool use_graph)
             bool any = false;
             for (int g = 0; g < P.G; g++) any |= P.st_h[g].active != 0;
             if (!any) break;
-            body<T>(P, pf);
+            body<T>(P, pf, step_cycles(P));
         }
         epilogue(P, pf);
         CK(cudaEventRecord(P.e1, s));
@@ -700,8 +765,9 @@ int plan_prologue(Plan &P)
 
 int plan_body(Plan &P)
 {
-    if (P.mixed) body<float>(P, g_no_prof);
-    else body<double>(P, g_no_prof);
+    const int c = step_cycles(P);
+    if (P.mixed) body<float>(P, g_no_prof, c);
+    else body<double>(P, g_no_prof, c);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -736,6 +802,7 @@ void fill_stats(const GridState &s, const int herr[2], double ms, mg_stats *o, i
         o->gamma = (s.iters > 0 && s.r0 > 0.0) ? pow(s.rnorm / s.r0, 1.0 / s.iters) : 0.0;
         o->rhs_mean = s.bmean;
         o->ms = ms;
+        o->steps = s.steps;
     }
     *status_out = status;
 }
@@ -915,6 +982,7 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
     GridState ds;
     memset(&ds, 0, sizeof(ds));
     ds.active = 1;
+    ds.cycles_next = 1 << 30;  // unit calls run whatever cycle index they are given
     CK(cudaMemcpy(h->dstate, &ds, sizeof(ds), cudaMemcpyHostToDevice));
     CK(cudaMemset(h->state, 0, sizeof(GridState)));
     CK(cudaMemset(h->err, 0, 16 * sizeof(int)));
@@ -992,6 +1060,7 @@ int mg_params_default(mg_params *p)
     p->coarse_solver = MG_COARSE_AUTO;
     p->coarse_max_iters = 300;
     p->coarse_tol = 1e-8;
+    p->adaptive_cycles = 1;
     return MG_OK;
 }
 
@@ -1350,8 +1419,8 @@ int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int swe
     if (rc) return rc;
     for (int s = 0; s < sweeps; s++) {
         for (int colour = 0; colour < 2; colour++) {
-            if (prec == MG_PREC_MIXED) launch_half<float>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
-            else launch_half<double>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
+            if (prec == MG_PREC_MIXED) launch_half<float>(tb, colour, h->prm.omega, 0, h->stream);
+            else launch_half<double>(tb, colour, h->prm.omega, 0, h->stream);
         }
     }
     CK(cudaGetLastError());
@@ -1379,8 +1448,8 @@ int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x)
     Table tb;
     int rc = unit_view(h, level, prec, x, nullptr, coarse_e, nullptr, &tb, kProlongTiles);
     if (rc) return rc;
-    if (prec == MG_PREC_MIXED) launch_prolong<float>(tb, nullptr, 0, h->stream);
-    else launch_prolong<double>(tb, nullptr, 0, h->stream);
+    if (prec == MG_PREC_MIXED) launch_prolong<float>(tb, h->stream);
+    else launch_prolong<double>(tb, h->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return MG_OK;
@@ -1411,11 +1480,11 @@ int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e)
     v.gm_tol = h->prm.coarse_tol;
     CK(cudaMemcpyAsync(h->dcview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
     if (h->gmres) {
-        if (prec == MG_PREC_MIXED) launch_coarse_gmres<float>(h->dcview, 1, nullptr, h->stream);
-        else launch_coarse_gmres<double>(h->dcview, 1, nullptr, h->stream);
+        if (prec == MG_PREC_MIXED) launch_coarse_gmres<float>(h->dcview, 1, 0, h->stream);
+        else launch_coarse_gmres<double>(h->dcview, 1, 0, h->stream);
     } else {
-        if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, nullptr, h->stream);
-        else launch_coarse_solve<double>(h->dcview, 1, nullptr, h->stream);
+        if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, 0, h->stream);
+        else launch_coarse_solve<double>(h->dcview, 1, 0, h->stream);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));

@@ -36,11 +36,24 @@ struct GridState {
     int iters;      // completed V-cycles
     int status;     // gbmg status code
     int active;     // 1 while the grid is being iterated
+    int cycles_next;  // V-cycles of the next refinement step (1 .. inner)
+    int steps;        // refinement steps done
+    double rprev;     // ||r|| before the last refinement step
     double rz;      // conjugate gradients: r . z of the current step
     double alpha;   //   step length
     double beta;    //   direction update
     double zmean;   //   mean of the preconditioned residual
 };
+
+// A grid takes part in V-cycle `cyc` (0-based) of the current refinement step
+// while it is still iterating and its step asks for more than cyc cycles.  A
+// batch runs as many cycles as its most demanding grid and the others sit the
+// extra ones out, so every grid gets exactly its own arithmetic, alone or
+// batched.
+__device__ __forceinline__ bool in_cycle(const GridState *s, int cyc)
+{
+    return s->active && cyc < s->cycles_next;
+}
 
 // Division by a fixed divisor d >= 1 of numerators n < 2^31 by one multiply
 // and a shift (Granlund & Montgomery, PLDI 1994, round-up variant): with
@@ -137,6 +150,7 @@ struct OuterView {
     // correction (V-cycle precision)
     double *r64, *z, *d, *q;
     const void *e;
+    int adaptive;        // choose the V-cycles of each refinement step from the measured rate
 };
 
 // The coarsest level of one grid.
@@ -151,7 +165,6 @@ struct CoarseView {
     const GridState *st;
     int *err;            // set-up error flag (non-positive pivot)
     int g;               // index of the grid in its plan
-    int outer;           // 1 if this is also the finest level (x += e happens here)
     int gmres;           // 1: solved by restarted GMRES (G unused)
     double *gm;          // GMRES scratch: b, e, w, then kGmresM + 1 Krylov vectors (FP64, nc each)
     int gm_max;          // most Arnoldi steps

@@ -61,11 +61,10 @@ __device__ __forceinline__ double apply_at(const CoarseView &C, const double *__
 }  // namespace
 
 template <class T>
-__global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView *__restrict__ cv, int count,
-                                                                const OuterView *__restrict__ ov)
+__global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView *__restrict__ cv, int cyc)
 {
     const CoarseView &C = cv[blockIdx.x];
-    if (!C.gmres || !C.st->active) return;
+    if (!C.gmres || !in_cycle(C.st, cyc)) return;
     __shared__ double H[(kGmresM + 1) * kGmresM];
     __shared__ double cs[kGmresM], sn[kGmresM], g[kGmresM + 1], y[kGmresM];
     __shared__ double red[32];
@@ -165,21 +164,16 @@ __global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView
     for (int c = tid; c < n; c += nt) s += e[c];
     const double em = block_all_sum(s, red) / n;
     T *x = (T *)C.x;
-    double *pout = (ov != nullptr && C.outer) ? ov[C.g].p : nullptr;
-    for (int c = tid; c < n; c += nt) {
-        const T xn = (T)(e[c] - em);
-        x[c] = xn;
-        if (pout) pout[c] += (double)xn;
-    }
+    for (int c = tid; c < n; c += nt) x[c] = (T)(e[c] - em);
 }
 
 template <class T>
-void launch_coarse_gmres(const CoarseView *cv, int count, const OuterView *ov, cudaStream_t s)
+void launch_coarse_gmres(const CoarseView *cv, int count, int cyc, cudaStream_t s)
 {
-    k_coarse_gmres<T><<<count, kGmresThreads, 0, s>>>(cv, count, ov);
+    k_coarse_gmres<T><<<count, kGmresThreads, 0, s>>>(cv, cyc);
 }
 
-template void launch_coarse_gmres<float>(const CoarseView *, int, const OuterView *, cudaStream_t);
-template void launch_coarse_gmres<double>(const CoarseView *, int, const OuterView *, cudaStream_t);
+template void launch_coarse_gmres<float>(const CoarseView *, int, int, cudaStream_t);
+template void launch_coarse_gmres<double>(const CoarseView *, int, int, cudaStream_t);
 
 }  // namespace gbmg

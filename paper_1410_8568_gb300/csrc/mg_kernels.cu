@@ -123,19 +123,16 @@ struct LoadPlain {
 // steers convergence; the FP64 path divides exactly.
 //
 // flags: kZeroGuess  (red launch) the iterate is zero on entry: red cells get
-//                    omega * (-b / d), black cells 0, so no clearing pass;
-//        kOuter      the relaxed cells' final values are also added to the FP64
-//                    iterate (last red and last black half-sweep of a
-//                    refinement step on the finest level).
-template <class T, bool OUT>
+//                    omega * (-b / d), black cells 0, so no clearing pass.
+// cyc: index of the V-cycle within its refinement step (in_cycle).
+template <class T>
 __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
                                                    const int *__restrict__ start, int count,
-                                                   int colour, T omega, int flags,
-                                                   const OuterView *__restrict__ ov)
+                                                   int colour, T omega, int flags, int cyc)
 {
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
-    if (!L.st->active) return;
+    if (!in_cycle(L.st, cyc)) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], per = L.per;
     T *__restrict__ x = (T *)L.x;
     const T *__restrict__ b = (const T *)L.b;
@@ -143,7 +140,6 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
     const T *__restrict__ wy = (const T *)L.w[1];
     const T *__restrict__ wz = (const T *)L.w[2];
     const bool zero = flags & kZeroGuess;
-    double *__restrict__ pout = OUT ? ov[L.g].p : nullptr;
     const long long sy = nx, sz = (long long)nx * ny;
     const int lb = blockIdx.x - start[e];
 
@@ -170,7 +166,6 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
                 v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
             }
             x[c] = v;
-            if constexpr (OUT) pout[c] += (double)v;
         }
         return;
     }
@@ -184,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
     if (row >= ny * nz) return;
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
-    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, pout);
+    half_quad<T>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero);
 }
 
 // Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64
@@ -204,11 +199,11 @@ int prolong_blocks(const int n[3]) { return half_blocks(n); }
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restrict__ lv,
-                                                       const int *__restrict__ start, int count)
+                                                       const int *__restrict__ start, int count, int cyc)
 {
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
-    if (!L.st->active) return;
+    if (!in_cycle(L.st, cyc)) return;
     const int ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2];
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int lb = blockIdx.x - start[e];
@@ -260,24 +255,20 @@ int restrict_blocks(const int n[3], const int nc[3])
 }
 
 // ---------------------------------------------------------------------------
-// (4) prolongation and correction: x += P e_c.  outer_update: finest level with
-// no post-smoothing, the refinement step ends here, so p += (double) x too.
+// (4) prolongation and correction: x += P e_c
 // ---------------------------------------------------------------------------
 
-template <class T, bool OUT, bool FLUX>
+template <class T, bool FLUX>
 __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
-                                                      const int *__restrict__ start, int count,
-                                                      const OuterView *__restrict__ ov,
-                                                      int outer_update)
+                                                      const int *__restrict__ start, int count, int cyc)
 {
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
-    if (!L.st->active) return;
+    if (!in_cycle(L.st, cyc)) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const T *ec = (const T *)L.xc;
     T *x = (T *)L.x;
     const int lb = blockIdx.x - start[e];
-    double *pout = OUT ? ov[L.g].p : nullptr;
     if ((nx & 3) == 0) {
         const int nq = nx >> 2;
         const int xt_n = (nq + 31) >> 5;
@@ -286,8 +277,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
-        if constexpr (FLUX) prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, pout);
-        else prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, pout);
+        if constexpr (FLUX) prolong_quad_flux<T>(L, row, row % ny, row / ny, qx);
+        else prolong_quad<T>(L, row, row % ny, row / ny, qx);
         return;
     }
     const Tile t = fine_tile(L.n, lb);
@@ -300,7 +291,6 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         const T xn = x[c] + (FLUX ? prolong_at_flux(ec, (const T *)L.ac, L.nc, L.per, i, t.j, t.k)
                                   : prolong_at(ec, L.nc, L.per, i, t.j, t.k));
         x[c] = xn;
-        if constexpr (OUT) pout[c] += (double)xn;
     }
 }
 
@@ -377,12 +367,12 @@ __device__ __forceinline__ T smem_flux(const T *x, const T *wx, const T *wy, con
 
 template <class T>
 __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restrict__ tv, T omega,
-                                                       int nu1, int nu2)
+                                                       int nu1, int nu2, int cyc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = (T *)smem_raw;
     const TailView &V = tv[blockIdx.x];
-    if (!V.st->active) return;
+    if (!in_cycle(V.st, cyc)) return;
     const int nt = V.nt, per = V.per;
     // stage the faces of every tail level but the coarsest (solved with G) and
     // the right-hand side of the first; levels above the coarsest have even
@@ -534,32 +524,25 @@ __global__ void __launch_bounds__(kThreads) k_apply(const LevelView *__restrict_
 // solves A e = b - mean(b) and adds a constant, which the cycle ignores
 // (A 1 = 0) and the final mean removal takes out.  One warp per row of G
 // (rows are contiguous, G is symmetric), lanes split the dot product, fixed
-// shuffle tree.  A grid whose finest level is its coarsest (C.outer) also
-// gets p += (double) e.
+// shuffle tree.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__restrict__ cv,
-                                                           const OuterView *__restrict__ ov)
+__global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__restrict__ cv, int cyc)
 {
     const CoarseView &C = cv[blockIdx.x];
-    if (C.gmres || !C.st->active) return;  // GMRES grids: k_coarse_gmres
+    if (C.gmres || !in_cycle(C.st, cyc)) return;  // GMRES grids: k_coarse_gmres
     __shared__ double rb[kMaxCoarse];
     const int n = C.nc;
     const T *b = (const T *)C.b;
     for (int t = threadIdx.x; t < n; t += blockDim.x) rb[t] = (double)b[t];
     __syncthreads();
     T *x = (T *)C.x;
-    double *pout = (ov != nullptr && C.outer) ? ov[C.g].p : nullptr;
     const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
     for (int t = threadIdx.x >> 5; t < n; t += warps) {
         const double *Gt = C.G + (long long)t * n;
         double s = 0.0;
         for (int u = lane; u < n; u += 32) s += Gt[u] * rb[u];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            const T xn = (T)(-s);
-            x[t] = xn;
-            if (pout) pout[t] += (double)xn;
-        }
+        if (lane == 0) x[t] = (T)(-s);
     }
 }
 
@@ -834,6 +817,9 @@ __global__ void k_begin(const OuterView *__restrict__ ov)
     s->r0 = 0.0;
     s->rnorm = 0.0;
     s->xmean = 0.0;
+    s->cycles_next = O.inner < O.max_iters ? O.inner : O.max_iters;
+    s->steps = 0;
+    s->rprev = 0.0;
 }
 
 // Partial sums of the caller's right-hand side (which = 0, partial slot 3) or
@@ -917,6 +903,29 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
     }
 }
 
+// End of a refinement step: p += (double) e, e the level-0 correction of the
+// step's V-cycles (V-cycle precision Te), for every grid still iterating.
+template <class Te>
+__global__ void __launch_bounds__(kThreads) k_outer_update(const OuterView *__restrict__ ov,
+                                                           const int *__restrict__ start, int count)
+{
+    const int e = find_entry(start, count);
+    const OuterView O = ov[e];
+    if (!O.st->active) return;
+    const int lb = blockIdx.x - start[e];
+    const int ntiles = fine_blocks(O.n);
+    const Te *__restrict__ ev = (const Te *)O.e;
+    for (int tile = lb; tile < ntiles; tile += O.nblk) {
+        const Tile t = fine_tile(O.n, tile);
+        if (!t.ok) continue;
+        const long long rowoff = (long long)O.n[0] * t.row;
+        for (int h = 0; h < 2; h++) {
+            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+            if (i < O.n[0]) O.p[rowoff + i] += (double)ev[rowoff + i];
+        }
+    }
+}
+
 // One block per grid: sum the block partials in a fixed order and update the
 // state.  mode 0: mean of b.  mode 1: after the starting residual.  mode 2:
 // after a cycle (counts it).  mode 3: mean of the final iterate.  Stopping
@@ -943,11 +952,14 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
         return;
     }
     const double rn = sqrt(out[0]);
+    int done = 0;
     if (mode == 1) {
         s->bnorm = sqrt(out[2]);
         s->r0 = rn;
     } else {
-        s->iters += O.inner;
+        done = s->cycles_next;
+        s->iters += done;
+        s->steps += 1;
     }
     s->rnorm = rn;
     if (!isfinite(rn)) {
@@ -960,6 +972,23 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
         s->status = 4;  // MG_ENOTCONV
         s->active = 0;
     }
+    if (s->active) {
+        // V-cycles of the next refinement step: inner, or (adaptive, multigrid
+        // iteration) the number the last step's per-cycle reduction rate g
+        // needs to reach the tolerance, taken with a 10% margin on g
+        int c = O.inner;
+        if (mode == 2 && O.adaptive && !O.r64 && s->rprev > 0.0) {
+            const double g = pow(rn / s->rprev, 1.0 / done);
+            if (g > 0.0 && g < 1.0) {
+                const double ge = fmin(0.95, 1.1 * g);
+                const double need = ceil(log(s->tol * s->bnorm / rn) / log(ge));
+                c = need < 1.0 ? 1 : (need < (double)O.inner ? (int)need : O.inner);
+            }
+        }
+        const int left = s->max_iters - s->iters;  // >= 1 here
+        s->cycles_next = c < left ? c : left;
+    }
+    s->rprev = rn;
 }
 
 // End of a solve: p = p - mean(p) (a zero right-hand side gives p = 0).
@@ -995,6 +1024,19 @@ __global__ void k_loop_ctl(cudaGraphConditionalHandle h, const OuterView *__rest
     cudaGraphSetConditional(h, any);
 }
 
+// Start of a refinement step of a graph-driven solve: the step's V-cycles are
+// the most any active grid of the plan asks for (switch branch c - 1).
+__global__ void k_step_ctl(cudaGraphConditionalHandle h, const OuterView *__restrict__ ov, int count)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int c = 1;
+    for (int g = 0; g < count; g++) {
+        const GridState *s = ov[g].st;
+        if (s->active && s->cycles_next > c) c = s->cycles_next;
+    }
+    cudaGraphSetConditional(h, (unsigned int)(c - 1));
+}
+
 // Copy the state of every grid of a plan into one contiguous array (one
 // device-to-host copy then serves the whole batch).
 __global__ void k_gather_states(const OuterView *__restrict__ ov, int count, GridState *out)
@@ -1011,44 +1053,41 @@ void launch_gather_states(const OuterTable &ot, GridState *out, cudaStream_t s)
     k_gather_states<<<1, 128, 0, s>>>(ot.ov, ot.count, out);
 }
 
+void launch_step_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStream_t s)
+{
+    k_step_ctl<<<1, 32, 0, s>>>(h, ot.ov, ot.count);
+}
 void launch_loop_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStream_t s)
 {
     k_loop_ctl<<<1, 32, 0, s>>>(h, ot.ov, ot.count);
 }
 
 template <class T>
-void launch_half_rows(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
+void launch_half_rows(const Table &tb, int colour, double omega, int flags, cudaStream_t s)
 {
-    if (flags & kOuter)
-        k_half<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, ov);
-    else
-        k_half<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, ov);
+    k_half<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc);
 }
 template <class T>
 void launch_restrict_rows(const Table &tb, cudaStream_t s)
 {
-    k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
+    k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
 }
 template <class T>
-void launch_prolong_rows(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
+void launch_prolong_rows(const Table &tb, cudaStream_t s)
 {
-    if (tb.flux) {
-        if (outer_update) k_prolong<T, true, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
-        else k_prolong<T, false, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
-    } else {
-        if (outer_update) k_prolong<T, true, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
-        else k_prolong<T, false, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, ov, outer_update);
-    }
+    if (tb.flux) k_prolong<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
+    else k_prolong<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
 }
 template <class T>
-void launch_tail(const TailView *tv, int count, size_t smem, double omega, int nu1, int nu2, cudaStream_t s)
+void launch_tail(const TailView *tv, int count, size_t smem, double omega, int nu1, int nu2, int cyc,
+                 cudaStream_t s)
 {
     static size_t attr = 0;  // opt in to more than 48 KB of shared memory when needed
     if (smem > attr) {
         cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_tail<T><<<count, kTailThreads, smem, s>>>(tv, (T)omega, nu1, nu2);
+    k_tail<T><<<count, kTailThreads, smem, s>>>(tv, (T)omega, nu1, nu2, cyc);
 }
 template <class T>
 void launch_apply(const Table &tb, cudaStream_t s)
@@ -1056,9 +1095,9 @@ void launch_apply(const Table &tb, cudaStream_t s)
     k_apply<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
 }
 template <class T>
-void launch_coarse_solve(const CoarseView *cv, int count, const OuterView *ov, cudaStream_t s)
+void launch_coarse_solve(const CoarseView *cv, int count, int cyc, cudaStream_t s)
 {
-    k_coarse_solve<T><<<count, kThreads, 0, s>>>(cv, ov);
+    k_coarse_solve<T><<<count, kThreads, 0, s>>>(cv, cyc);
 }
 void launch_coarse_setup(const CoarseView *cv, int count, cudaStream_t s)
 {
@@ -1104,6 +1143,11 @@ void launch_residual(const OuterTable &ot, int init, cudaStream_t s)
 {
     k_residual<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, init);
 }
+template <class Te>
+void launch_outer_update(const OuterTable &ot, cudaStream_t s)
+{
+    k_outer_update<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+}
 void launch_finalize(const OuterTable &ot, int mode, cudaStream_t s)
 {
     k_finalize<<<ot.count, kThreads, 0, s>>>(ot.ov, mode);
@@ -1113,19 +1157,21 @@ void launch_final(const OuterTable &ot, cudaStream_t s)
     k_final<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
 }
 
-template void launch_half_rows<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
-template void launch_half_rows<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_half_rows<float>(const Table &, int, double, int, cudaStream_t);
+template void launch_half_rows<double>(const Table &, int, double, int, cudaStream_t);
 template void launch_restrict_rows<float>(const Table &, cudaStream_t);
 template void launch_restrict_rows<double>(const Table &, cudaStream_t);
-template void launch_prolong_rows<float>(const Table &, const OuterView *, int, cudaStream_t);
-template void launch_prolong_rows<double>(const Table &, const OuterView *, int, cudaStream_t);
-template void launch_tail<float>(const TailView *, int, size_t, double, int, int, cudaStream_t);
-template void launch_tail<double>(const TailView *, int, size_t, double, int, int, cudaStream_t);
+template void launch_prolong_rows<float>(const Table &, cudaStream_t);
+template void launch_prolong_rows<double>(const Table &, cudaStream_t);
+template void launch_tail<float>(const TailView *, int, size_t, double, int, int, int, cudaStream_t);
+template void launch_tail<double>(const TailView *, int, size_t, double, int, int, int, cudaStream_t);
 template void launch_apply<float>(const Table &, cudaStream_t);
 template void launch_apply<double>(const Table &, cudaStream_t);
-template void launch_coarse_solve<float>(const CoarseView *, int, const OuterView *, cudaStream_t);
-template void launch_coarse_solve<double>(const CoarseView *, int, const OuterView *, cudaStream_t);
+template void launch_coarse_solve<float>(const CoarseView *, int, int, cudaStream_t);
+template void launch_coarse_solve<double>(const CoarseView *, int, int, cudaStream_t);
 template void launch_residual<float>(const OuterTable &, int, cudaStream_t);
 template void launch_residual<double>(const OuterTable &, int, cudaStream_t);
+template void launch_outer_update<float>(const OuterTable &, cudaStream_t);
+template void launch_outer_update<double>(const OuterTable &, cudaStream_t);
 
 }  // namespace gbmg

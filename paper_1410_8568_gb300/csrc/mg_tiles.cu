@@ -15,39 +15,37 @@ namespace gbmg {
 // Block lb of a table entry owns items [lb Q B, (lb + 1) Q B); thread t handles
 // lb Q B + q B + t for q < Q.  Items are numbered row by row, so consecutive
 // threads touch consecutive 16-byte vectors.
-template <class T, int B, int Q, bool OUT>
+template <class T, int B, int Q>
 __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ lv,
                                                  const int *__restrict__ start, int count,
-                                                 int colour, T omega, int flags,
-                                                 const OuterView *__restrict__ ov)
+                                                 int colour, T omega, int flags, int cyc)
 {
     const int e = find_entry(start, count);
     const LevelView &L = lv[e];
-    if (!L.st->active) return;
+    if (!in_cycle(L.st, cyc)) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], nq = nx >> 2;
     const int items = nq * ny * nz;
     const int lb = blockIdx.x - start[e];
     const bool zero = flags & kZeroGuess;
-    double *pout = OUT ? ov[L.g].p : nullptr;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
         const int g = (lb * Q + q) * B + (int)threadIdx.x;
         if (g >= items) return;
         const int row = fdiv(g, L.dq);
         const int k = fdiv(row, L.dy);
-        half_quad<T, OUT>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
+        half_quad<T>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
                      (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
-                     omega, zero, pout);
+                     omega, zero);
     }
 }
 
 template <class T, int B, int Q>
 __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict__ lv,
-                                                     const int *__restrict__ start, int count)
+                                                     const int *__restrict__ start, int count, int cyc)
 {
     const int e = find_entry(start, count);
     const LevelView &L = lv[e];
-    if (!L.st->active) return;
+    if (!in_cycle(L.st, cyc)) return;
     const int np = L.nc[0] >> 1, ncy = L.nc[1];
     const int items = np * ncy * L.nc[2];
     const int lb = blockIdx.x - start[e];
@@ -61,27 +59,24 @@ __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict
     }
 }
 
-template <class T, int B, int Q, bool OUT>
+template <class T, int B, int Q>
 __global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict__ lv,
-                                                    const int *__restrict__ start, int count,
-                                                    const OuterView *__restrict__ ov,
-                                                    int outer_update)
+                                                    const int *__restrict__ start, int count, int cyc)
 {
     // items: coarse cell pairs; each covers a quad of the 2 x 2 fine rows above it
     const int e = find_entry(start, count);
     const LevelView &L = lv[e];
-    if (!L.st->active) return;
+    if (!in_cycle(L.st, cyc)) return;
     const int np = L.nc[0] >> 1, ncy = L.nc[1];
     const int items = np * ncy * L.nc[2];
     const int lb = blockIdx.x - start[e];
-    double *pout = OUT ? ov[L.g].p : nullptr;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
         const int g = (lb * Q + q) * B + (int)threadIdx.x;
         if (g >= items) return;
         const int crow = fdiv(g, L.dp);
         const int K = fdiv(crow, L.dcy);
-        prolong_block<T, OUT>(L, crow - K * ncy, K, g - crow * np, pout);
+        prolong_block<T>(L, crow - K * ncy, K, g - crow * np);
     }
 }
 
@@ -133,19 +128,15 @@ int restrict_blocks_v(const int n[3], const int nc[3], int v)
 }
 
 template <class T>
-void launch_half(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
+void launch_half(const Table &tb, int colour, double omega, int flags, cudaStream_t s)
 {
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        if (flags & kOuter)
-            k_half_flat<T, ts.B, ts.Q, true><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
-                                                                        (T)omega, flags, ov);
-        else
-            k_half_flat<T, ts.B, ts.Q, false><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
-                                                                         (T)omega, flags, ov);
+        k_half_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega,
+                                                              flags, tb.cyc);
     });
-    if (!flat) launch_half_rows<T>(tb, colour, omega, flags, ov, s);
+    if (!flat) launch_half_rows<T>(tb, colour, omega, flags, s);
 }
 
 template <class T>
@@ -154,36 +145,31 @@ void launch_restrict(const Table &tb, cudaStream_t s)
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count);
+        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
     });
     if (!flat) launch_restrict_rows<T>(tb, s);
 }
 
 template <class T>
-void launch_prolong(const Table &tb, const OuterView *ov, int outer_update, cudaStream_t s)
+void launch_prolong(const Table &tb, cudaStream_t s)
 {
     if (tb.blocks == 0) return;
     if (tb.flux) {  // flux-conserving prolongation: row tiles only
-        launch_prolong_rows<T>(tb, ov, outer_update, s);
+        launch_prolong_rows<T>(tb, s);
         return;
     }
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        if (outer_update)
-            k_prolong_flat<T, ts.B, ts.Q, true><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, ov,
-                                                                           outer_update);
-        else
-            k_prolong_flat<T, ts.B, ts.Q, false><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, ov,
-                                                                            outer_update);
+        k_prolong_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
     });
-    if (!flat) launch_prolong_rows<T>(tb, ov, outer_update, s);
+    if (!flat) launch_prolong_rows<T>(tb, s);
 }
 
-template void launch_half<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
-template void launch_half<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_half<float>(const Table &, int, double, int, cudaStream_t);
+template void launch_half<double>(const Table &, int, double, int, cudaStream_t);
 template void launch_restrict<float>(const Table &, cudaStream_t);
 template void launch_restrict<double>(const Table &, cudaStream_t);
-template void launch_prolong<float>(const Table &, const OuterView *, int, cudaStream_t);
-template void launch_prolong<double>(const Table &, const OuterView *, int, cudaStream_t);
+template void launch_prolong<float>(const Table &, cudaStream_t);
+template void launch_prolong<double>(const Table &, cudaStream_t);
 
 }  // namespace gbmg

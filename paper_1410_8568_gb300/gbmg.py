@@ -24,7 +24,7 @@ STATIC_MAX_CELLS = 512
 NEUMANN, PERIODIC = 0, 1
 FP64, MIXED = 0, 1
 HARMONIC, ARITHMETIC = 0, 1
-K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL = range(7)
+K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL, K_UPDATE = range(8)
 TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
 PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
 SOLVER_MG, SOLVER_PCG = 0, 1
@@ -50,13 +50,14 @@ class Params(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("solver", ctypes.c_int), ("prolongation", ctypes.c_int),
                 ("tiles", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_max_iters", ctypes.c_int),
-                ("coarse_tol", ctypes.c_double)]
+                ("coarse_tol", ctypes.c_double), ("adaptive_cycles", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("res0", ctypes.c_double), ("res", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("bnorm", ctypes.c_double), ("rhs_mean", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("bnorm", ctypes.c_double), ("rhs_mean", ctypes.c_double), ("ms", ctypes.c_double),
+                ("steps", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -155,7 +156,7 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
 
 def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
                 inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
-                coarse_tol=None, coarse_max_iters=None) -> Params:
+                coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
@@ -176,6 +177,8 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
         p.coarse_tol = float(coarse_tol)
     if coarse_max_iters is not None:
         p.coarse_max_iters = int(coarse_max_iters)
+    if adaptive_cycles is not None:
+        p.adaptive_cycles = int(adaptive_cycles)
     return p
 
 
@@ -254,7 +257,7 @@ class Solver:
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
                  precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
                  inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
-                 coarse_tol=None, coarse_max_iters=None):
+                 coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -264,7 +267,8 @@ class Solver:
         self.precision = precision
         self.grid = make_grid(self.shape, self.bc, self.length)
         self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles,
-                                  prolongation, solver, coarse_solver, coarse_tol, coarse_max_iters)
+                                  prolongation, solver, coarse_solver, coarse_tol, coarse_max_iters,
+                                  adaptive_cycles)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:

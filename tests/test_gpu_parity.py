@@ -306,11 +306,11 @@ def test_edge_cases():
         # the handle is still usable afterwards
         p5 = torch.zeros_like(b)
         assert S.solve(b, p5).status == gbmg.OK and torch.equal(p5, p1)
-    for max_iters, inner in ((2, 2), (2, 3), (4, 3), (1, 1)):
+    for max_iters, inner in ((2, 2), (2, 3), (4, 3), (1, 1), (5, 2)):
         with solver_for(P, f, max_iters=max_iters, inner_cycles=inner) as S:
             st = S.solve(dev(P.rhs), torch.zeros(cells(P.shape), dtype=torch.float64, device="cuda"))
-            # the solve stops after the first whole refinement step that reaches max_iters
-            assert st.status == gbmg.ENOTCONV and st.iters == inner * -(-max_iters // inner)
+            # the last refinement step is cut to the cycles left: exactly max_iters
+            assert st.status == gbmg.ENOTCONV and st.iters == max_iters
     # invalid coefficients and sizes are refused
     bad = [a.copy() for a in f]
     bad[0][5, 5, 5] = -1.0
@@ -347,12 +347,15 @@ def test_profiling_counts_launches():
         # one launch per colour of each of the nu1 + nu2 sweeps per V-cycle on the finest level
         n, ms = S.profile_read(gbmg.K_SMOOTH, 0)
         assert n == st.iters * 2 * (2 + 2) and ms > 0.0
-        # one FP64 residual per refinement step (inner_cycles V-cycles each) plus the starting one
+        # per refinement step (at most inner_cycles V-cycles each) the FP64
+        # update p += e and the FP64 residual, plus the starting residual
         inner = S.resolved_params()["inner_cycles"]
         assert inner == 3  # the mixed-precision default
         n, ms = S.profile_read(gbmg.K_RESIDUAL, 0)
-        assert st.iters % inner == 0
-        assert n == st.iters // inner + 1 and ms > 0.0
+        assert st.steps >= -(-st.iters // inner)
+        assert n == st.steps + 1 and ms > 0.0
+        n, ms = S.profile_read(gbmg.K_UPDATE, 0)
+        assert n == st.steps and ms > 0.0
 
 
 # ---------------------------------------------------------------------------
@@ -483,3 +486,26 @@ def test_server_results_equal_alone():
         assert rc == gbmg.OK and st.iters == ia
         assert torch.equal(pa, pb)
     assert srv.close() == gbmg.OK
+
+
+@pytest.mark.parametrize("precision", [gbmg.MIXED, gbmg.FP64])
+def test_adaptive_cycles_per_step(precision):
+    """Adaptive steps stop with fewer or as many V-cycles as fixed ones, at the
+    same tolerance, and give the same solution to the oracle's accuracy."""
+    P = I.config2(64)
+    f = oracle.faces_from_density(P.shape, P.bc, P.rho)
+    pstar = exact_solution("cfg2_dropfilm_64", P, f)
+    res = {}
+    for adaptive in (0, 1):
+        with solver_for(P, f, precision=precision, adaptive_cycles=adaptive) as S:
+            inner = S.resolved_params()["inner_cycles"]
+            p = torch.zeros(cells(P.shape), dtype=torch.float64, device="cuda")
+            st = S.solve(dev(P.rhs), p, tol=TOL)
+            assert st.status == gbmg.OK and st.rel_res <= TOL
+            err = np.linalg.norm(host(p) - pstar) / np.linalg.norm(pstar)
+            assert err <= ERR
+            res[adaptive] = st
+    assert res[0].iters % inner == 0 or res[0].iters == 100
+    assert res[1].iters <= res[0].iters
+    print("fixed %d cycles / %d steps, adaptive %d cycles / %d steps" %
+          (res[0].iters, res[0].steps, res[1].iters, res[1].steps))
