@@ -215,7 +215,7 @@ def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, 
         prologue += inner * cycle + 3  # first preconditioning: V-cycles, z and its sums, direction
         per_step = 4 + 3 + 1           # A d, alpha, update, test; z, beta, direction; loop control
     else:
-        per_step = 4 + (1 if inner > 1 else 0)  # p += e, residual, finalize, loop control (+ step control)
+        per_step = 3 + (1 if inner > 1 else 0)  # residual, finalize, loop control (+ step control)
     epilogue = 3                       # sum p, mean, p - mean
     return setup + prologue + iters * cycle + steps * per_step + epilogue
 
@@ -651,13 +651,11 @@ def main():
     # the other level-0 kernels of the cycle, algorithmic bytes per finest cell:
     # restriction reads x, b, 3 faces (FP32) and writes the coarse b (1/8 cell);
     # prolongation reads and writes x and reads the coarse correction (1/8);
-    # the FP64 residual reads p, b0 and 3 FP64 faces and writes r (FP32);
-    # the update p += e reads e (FP32) and reads and writes p
+    # the FP64 residual reads p, b0 and 3 FP64 faces and writes r (FP32)
     per_kernel = {}
     for name, kind, bpc, bound in (("restrict", gbmg.K_RESTRICT, 20.5, "hbm"),
                                    ("prolong", gbmg.K_PROLONG, 8.5, "hbm"),
-                                   ("residual_fp64", gbmg.K_RESIDUAL, 44.0, "fp64 alu"),
-                                   ("update_fp64", gbmg.K_UPDATE, 20.0, "hbm")):
+                                   ("residual_fp64", gbmg.K_RESIDUAL, 44.0, "fp64 alu")):
         n_k, ms_k = S.profile_read(kind, 0)
         if n_k:
             us = 1000.0 * ms_k / n_k

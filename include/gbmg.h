@@ -381,11 +381,10 @@ int mg_projection_step(mg_handle *h, double *ux, double *uy, double *uz, double 
 #define MG_K_RESTRICT 1
 #define MG_K_PROLONG 2
 #define MG_K_COARSE 3
-#define MG_K_RESIDUAL 4 /* the FP64 residual + norms */
+#define MG_K_RESIDUAL 4 /* the FP64 residual + norms (the update p += e is folded into the cycle) */
 #define MG_K_OTHER 5
 #define MG_K_TAIL 6 /* the levels of at most 4096 cells and the coarsest solve, one block per grid */
-#define MG_K_UPDATE 7 /* the FP64 update p += e at the end of a refinement step (Sec. 2.3) */
-#define MG_K_KINDS 8
+#define MG_K_KINDS 7
 
 int mg_profile_enable(mg_handle *h, int enable);
 int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double *total_ms);

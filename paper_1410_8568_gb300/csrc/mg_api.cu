@@ -368,6 +368,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.st = h->state;
         v.err = h->err + 1;
         v.g = g;
+        v.outer = h->L == 1 ? 1 : 0;
         v.gmres = h->gmres ? 1 : 0;
         v.gm = h->gm;
         v.gm_max = h->prm.coarse_max_iters;
@@ -460,9 +461,12 @@ Prof::~Prof()
 // cycles skips every launch of it (in_cycle).  Coarse levels start every cycle
 // from a zero correction (the first red half-sweep takes x = 0).  The finest
 // level starts from zero in the first cycle of a step and from the previous
-// cycle's correction in the next ones.
+// cycle's correction in the next ones.  outer: in the grid's last cycle of the
+// step, the last red and black half-sweeps on the finest level also add the
+// correction to the FP64 iterate (the prolongation does if nu2 = 0, the coarse
+// solve if the grid has one level).
 template <class T>
-static void vcycle(Plan &P, Prof &pf, int cyc)
+static void vcycle(Plan &P, Prof &pf, int cyc, bool outer)
 {
     const cudaStream_t s = P.stream;
     const mg_params &q = P.prm;
@@ -476,10 +480,10 @@ static void vcycle(Plan &P, Prof &pf, int cyc)
         const bool zero = !(l == 0 && cyc > 0);
         for (int it = 0; it < q.nu1; it++) {
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 0, q.omega, (it == 0 && zero) ? kHalfZero : 0, s);
+            launch_half<T>(H, 0, q.omega, (it == 0 && zero) ? kHalfZero : 0, nullptr, s);
             pf.end(s);
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 1, q.omega, 0, s);
+            launch_half<T>(H, 1, q.omega, 0, nullptr, s);
             pf.end(s);
         }
         pf.begin(s, MG_K_RESTRICT, l);
@@ -493,22 +497,24 @@ static void vcycle(Plan &P, Prof &pf, int cyc)
     }
     if (P.ncv) {
         pf.begin(s, MG_K_COARSE, P.Lmax - 1);
-        if (P.cv_dense) launch_coarse_solve<T>(P.cv, P.ncv, cyc, s);
-        if (P.cv_gmres) launch_coarse_gmres<T>(P.cv, P.ncv, cyc, s);
+        if (P.cv_dense) launch_coarse_solve<T>(P.cv, P.ncv, cyc, outer ? P.ov : nullptr, s);
+        if (P.cv_gmres) launch_coarse_gmres<T>(P.cv, P.ncv, cyc, outer ? P.ov : nullptr, s);
         pf.end(s);
     }
     for (int l = P.Lmax - 2; l >= 0; l--) {
         const Table H = at(P.half[l]);
         if (H.count == 0) continue;
+        const bool top = outer && l == 0;
         pf.begin(s, MG_K_PROLONG, l);
-        launch_prolong<T>(at(P.down[l]), s);
+        launch_prolong<T>(at(P.down[l]), (top && q.nu2 == 0) ? P.ov : nullptr, s);
         pf.end(s);
         for (int it = 0; it < q.nu2; it++) {
+            const int fl = (top && it == q.nu2 - 1) ? kHalfOuter : 0;
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 0, q.omega, 0, s);
+            launch_half<T>(H, 0, q.omega, fl, P.ov, s);
             pf.end(s);
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 1, q.omega, 0, s);
+            launch_half<T>(H, 1, q.omega, fl, P.ov, s);
             pf.end(s);
         }
     }
@@ -520,7 +526,7 @@ template <class T>
 static void pcg_precondition(Plan &P, Prof &pf, int first)
 {
     const cudaStream_t s = P.stream;
-    for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c);
+    for (int c = 0; c < P.prm.inner_cycles; c++) vcycle<T>(P, pf, c, false);
     pf.begin(s, MG_K_OTHER, 0);
     launch_pcg_z<T>(P.ot, s);
     launch_pcg_finalize(P.ot, first ? 0 : 2, s);
@@ -551,8 +557,8 @@ template <class T> static void body_residual(Plan &P, Prof &pf);
 
 // One step of the outer iteration.  Multigrid iteration: up to `cycles`
 // V-cycles on A e = r (the first from e = 0, the next ones continuing from the
-// current e; each grid runs the number its state asks for), p += e in FP64,
-// then the FP64 residual and the stopping test.
+// current e; each grid runs the number its state asks for, the last one adding
+// e to the FP64 iterate), then the FP64 residual and the stopping test.
 template <class T>
 static void body(Plan &P, Prof &pf, int cycles)
 {
@@ -577,16 +583,13 @@ static void body(Plan &P, Prof &pf, int cycles)
 template <class T>
 static void body_cycles(Plan &P, Prof &pf, int cycles)
 {
-    for (int c = 0; c < cycles; c++) vcycle<T>(P, pf, c);
+    for (int c = 0; c < cycles; c++) vcycle<T>(P, pf, c, true);
 }
 
 template <class T>
 static void body_residual(Plan &P, Prof &pf)
 {
     const cudaStream_t s = P.stream;
-    pf.begin(s, MG_K_UPDATE, 0);
-    launch_outer_update<T>(P.ot, s);
-    pf.end(s);
     pf.begin(s, MG_K_RESIDUAL, 0);
     launch_residual<T>(P.ot, 0, s);
     pf.end(s);
@@ -1419,8 +1422,8 @@ int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int swe
     if (rc) return rc;
     for (int s = 0; s < sweeps; s++) {
         for (int colour = 0; colour < 2; colour++) {
-            if (prec == MG_PREC_MIXED) launch_half<float>(tb, colour, h->prm.omega, 0, h->stream);
-            else launch_half<double>(tb, colour, h->prm.omega, 0, h->stream);
+            if (prec == MG_PREC_MIXED) launch_half<float>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
+            else launch_half<double>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
         }
     }
     CK(cudaGetLastError());
@@ -1448,8 +1451,8 @@ int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x)
     Table tb;
     int rc = unit_view(h, level, prec, x, nullptr, coarse_e, nullptr, &tb, kProlongTiles);
     if (rc) return rc;
-    if (prec == MG_PREC_MIXED) launch_prolong<float>(tb, h->stream);
-    else launch_prolong<double>(tb, h->stream);
+    if (prec == MG_PREC_MIXED) launch_prolong<float>(tb, nullptr, h->stream);
+    else launch_prolong<double>(tb, nullptr, h->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return MG_OK;
@@ -1480,11 +1483,11 @@ int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e)
     v.gm_tol = h->prm.coarse_tol;
     CK(cudaMemcpyAsync(h->dcview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
     if (h->gmres) {
-        if (prec == MG_PREC_MIXED) launch_coarse_gmres<float>(h->dcview, 1, 0, h->stream);
-        else launch_coarse_gmres<double>(h->dcview, 1, 0, h->stream);
+        if (prec == MG_PREC_MIXED) launch_coarse_gmres<float>(h->dcview, 1, 0, nullptr, h->stream);
+        else launch_coarse_gmres<double>(h->dcview, 1, 0, nullptr, h->stream);
     } else {
-        if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, 0, h->stream);
-        else launch_coarse_solve<double>(h->dcview, 1, 0, h->stream);
+        if (prec == MG_PREC_MIXED) launch_coarse_solve<float>(h->dcview, 1, 0, nullptr, h->stream);
+        else launch_coarse_solve<double>(h->dcview, 1, 0, nullptr, h->stream);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));

@@ -54,6 +54,8 @@ __device__ __forceinline__ bool in_cycle(const GridState *s, int cyc)
 {
     return s->active && cyc < s->cycles_next;
 }
+// V-cycle `cyc` is the last of the grid's current refinement step.
+__device__ __forceinline__ bool last_cycle(const GridState *s, int cyc) { return cyc + 1 == s->cycles_next; }
 
 // Division by a fixed divisor d >= 1 of numerators n < 2^31 by one multiply
 // and a shift (Granlund & Montgomery, PLDI 1994, round-up variant): with
@@ -165,6 +167,7 @@ struct CoarseView {
     const GridState *st;
     int *err;            // set-up error flag (non-positive pivot)
     int g;               // index of the grid in its plan
+    int outer;           // 1 if this is also the finest level (p += e happens here)
     int gmres;           // 1: solved by restarted GMRES (G unused)
     double *gm;          // GMRES scratch: b, e, w, then kGmresM + 1 Krylov vectors (FP64, nc each)
     int gm_max;          // most Arnoldi steps

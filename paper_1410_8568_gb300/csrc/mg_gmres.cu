@@ -61,7 +61,8 @@ __device__ __forceinline__ double apply_at(const CoarseView &C, const double *__
 }  // namespace
 
 template <class T>
-__global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView *__restrict__ cv, int cyc)
+__global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView *__restrict__ cv, int cyc,
+                                                                const OuterView *__restrict__ ov)
 {
     const CoarseView &C = cv[blockIdx.x];
     if (!C.gmres || !in_cycle(C.st, cyc)) return;
@@ -164,16 +165,22 @@ __global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView
     for (int c = tid; c < n; c += nt) s += e[c];
     const double em = block_all_sum(s, red) / n;
     T *x = (T *)C.x;
-    for (int c = tid; c < n; c += nt) x[c] = (T)(e[c] - em);
+    // single-level grid: the last cycle of a refinement step also updates p
+    double *pout = (ov != nullptr && C.outer && last_cycle(C.st, cyc)) ? ov[C.g].p : nullptr;
+    for (int c = tid; c < n; c += nt) {
+        const T xn = (T)(e[c] - em);
+        x[c] = xn;
+        if (pout) pout[c] += (double)xn;
+    }
 }
 
 template <class T>
-void launch_coarse_gmres(const CoarseView *cv, int count, int cyc, cudaStream_t s)
+void launch_coarse_gmres(const CoarseView *cv, int count, int cyc, const OuterView *ov, cudaStream_t s)
 {
-    k_coarse_gmres<T><<<count, kGmresThreads, 0, s>>>(cv, cyc);
+    k_coarse_gmres<T><<<count, kGmresThreads, 0, s>>>(cv, cyc, ov);
 }
 
-template void launch_coarse_gmres<float>(const CoarseView *, int, int, cudaStream_t);
-template void launch_coarse_gmres<double>(const CoarseView *, int, int, cudaStream_t);
+template void launch_coarse_gmres<float>(const CoarseView *, int, int, const OuterView *, cudaStream_t);
+template void launch_coarse_gmres<double>(const CoarseView *, int, int, const OuterView *, cudaStream_t);
 
 }  // namespace gbmg

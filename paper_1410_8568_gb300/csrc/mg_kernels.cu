@@ -123,25 +123,22 @@ struct LoadPlain {
 // steers convergence; the FP64 path divides exactly.
 //
 // flags: kZeroGuess  (red launch) the iterate is zero on entry: red cells get
-//                    omega * (-b / d), black cells 0, so no clearing pass.
+//                    omega * (-b / d), black cells 0, so no clearing pass;
+//        kOuter      (finest level, last post-smoothing sweep of a cycle) a grid
+//                    whose refinement step ends with this cycle also adds the
+//                    relaxed cells' final values to its FP64 iterate.
 // cyc: index of the V-cycle within its refinement step (in_cycle).
-template <class T>
-__global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
-                                                   const int *__restrict__ start, int count,
-                                                   int colour, T omega, int flags, int cyc)
+template <class T, bool OUT>
+__device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour, T omega, bool zero,
+                                          double *__restrict__ pout)
 {
-    const int e = find_entry(start, count);
-    const LevelView L = lv[e];
-    if (!in_cycle(L.st, cyc)) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], per = L.per;
     T *__restrict__ x = (T *)L.x;
     const T *__restrict__ b = (const T *)L.b;
     const T *__restrict__ wx = (const T *)L.w[0];
     const T *__restrict__ wy = (const T *)L.w[1];
     const T *__restrict__ wz = (const T *)L.w[2];
-    const bool zero = flags & kZeroGuess;
     const long long sy = nx, sz = (long long)nx * ny;
-    const int lb = blockIdx.x - start[e];
 
     if ((nx & 3) != 0) {
         // one cell per thread (row tiles of 64 cells per warp, 2 per lane)
@@ -166,6 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
                 v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
             }
             x[c] = v;
+            if constexpr (OUT) pout[c] += (double)v;
         }
         return;
     }
@@ -179,7 +177,29 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
     if (row >= ny * nz) return;
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
-    half_quad<T>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero);
+    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, pout);
+}
+
+// MAYOUT: the launch carries kOuter; the test of the step's last cycle is
+// per grid, so uniform over a block, and picks one of two instances of the body.
+template <class T, bool MAYOUT>
+__global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
+                                                   const int *__restrict__ start, int count,
+                                                   int colour, T omega, int flags, int cyc,
+                                                   const OuterView *__restrict__ ov)
+{
+    const int e = find_entry(start, count);
+    const LevelView L = lv[e];
+    if (!in_cycle(L.st, cyc)) return;
+    const int lb = blockIdx.x - start[e];
+    const bool zero = flags & kZeroGuess;
+    if constexpr (MAYOUT) {
+        if (last_cycle(L.st, cyc)) {
+            half_body<T, true>(L, lb, colour, omega, zero, ov[L.g].p);
+            return;
+        }
+    }
+    half_body<T, false>(L, lb, colour, omega, zero, nullptr);
 }
 
 // Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64
@@ -255,20 +275,18 @@ int restrict_blocks(const int n[3], const int nc[3])
 }
 
 // ---------------------------------------------------------------------------
-// (4) prolongation and correction: x += P e_c
+// (4) prolongation and correction: x += P e_c.  With no post-smoothing the
+// finest level's prolongation ends the cycle, so a launch with MAYOUT adds the
+// result to the FP64 iterate of the grids whose step ends with this cycle
+// (row tiles only: a configuration without post-smoothing is not tuned for).
 // ---------------------------------------------------------------------------
 
-template <class T, bool FLUX>
-__global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
-                                                      const int *__restrict__ start, int count, int cyc)
+template <class T, bool FLUX, bool OUT>
+__device__ __forceinline__ void prolong_body(const LevelView &L, int lb, double *__restrict__ pout)
 {
-    const int e = find_entry(start, count);
-    const LevelView L = lv[e];
-    if (!in_cycle(L.st, cyc)) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const T *ec = (const T *)L.xc;
     T *x = (T *)L.x;
-    const int lb = blockIdx.x - start[e];
     if ((nx & 3) == 0) {
         const int nq = nx >> 2;
         const int xt_n = (nq + 31) >> 5;
@@ -277,8 +295,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
-        if constexpr (FLUX) prolong_quad_flux<T>(L, row, row % ny, row / ny, qx);
-        else prolong_quad<T>(L, row, row % ny, row / ny, qx);
+        if constexpr (FLUX) prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, pout);
+        else prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, pout);
         return;
     }
     const Tile t = fine_tile(L.n, lb);
@@ -291,7 +309,26 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         const T xn = x[c] + (FLUX ? prolong_at_flux(ec, (const T *)L.ac, L.nc, L.per, i, t.j, t.k)
                                   : prolong_at(ec, L.nc, L.per, i, t.j, t.k));
         x[c] = xn;
+        if constexpr (OUT) pout[c] += (double)xn;
     }
+}
+
+template <class T, bool FLUX, bool MAYOUT>
+__global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
+                                                      const int *__restrict__ start, int count, int cyc,
+                                                      const OuterView *__restrict__ ov)
+{
+    const int e = find_entry(start, count);
+    const LevelView L = lv[e];
+    if (!in_cycle(L.st, cyc)) return;
+    const int lb = blockIdx.x - start[e];
+    if constexpr (MAYOUT) {
+        if (last_cycle(L.st, cyc)) {
+            prolong_body<T, FLUX, true>(L, lb, ov[L.g].p);
+            return;
+        }
+    }
+    prolong_body<T, FLUX, false>(L, lb, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -524,9 +561,11 @@ __global__ void __launch_bounds__(kThreads) k_apply(const LevelView *__restrict_
 // solves A e = b - mean(b) and adds a constant, which the cycle ignores
 // (A 1 = 0) and the final mean removal takes out.  One warp per row of G
 // (rows are contiguous, G is symmetric), lanes split the dot product, fixed
-// shuffle tree.
+// shuffle tree.  A grid whose finest level is its coarsest (C.outer) adds e
+// to its FP64 iterate in the last cycle of a refinement step (ov non-null).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__restrict__ cv, int cyc)
+__global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__restrict__ cv, int cyc,
+                                                           const OuterView *__restrict__ ov)
 {
     const CoarseView &C = cv[blockIdx.x];
     if (C.gmres || !in_cycle(C.st, cyc)) return;  // GMRES grids: k_coarse_gmres
@@ -536,13 +575,18 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__r
     for (int t = threadIdx.x; t < n; t += blockDim.x) rb[t] = (double)b[t];
     __syncthreads();
     T *x = (T *)C.x;
+    double *pout = (ov != nullptr && C.outer && last_cycle(C.st, cyc)) ? ov[C.g].p : nullptr;
     const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
     for (int t = threadIdx.x >> 5; t < n; t += warps) {
         const double *Gt = C.G + (long long)t * n;
         double s = 0.0;
         for (int u = lane; u < n; u += 32) s += Gt[u] * rb[u];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[t] = (T)(-s);
+        if (lane == 0) {
+            const T xn = (T)(-s);
+            x[t] = xn;
+            if (pout) pout[t] += (double)xn;
+        }
     }
 }
 
@@ -903,29 +947,6 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
     }
 }
 
-// End of a refinement step: p += (double) e, e the level-0 correction of the
-// step's V-cycles (V-cycle precision Te), for every grid still iterating.
-template <class Te>
-__global__ void __launch_bounds__(kThreads) k_outer_update(const OuterView *__restrict__ ov,
-                                                           const int *__restrict__ start, int count)
-{
-    const int e = find_entry(start, count);
-    const OuterView O = ov[e];
-    if (!O.st->active) return;
-    const int lb = blockIdx.x - start[e];
-    const int ntiles = fine_blocks(O.n);
-    const Te *__restrict__ ev = (const Te *)O.e;
-    for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile);
-        if (!t.ok) continue;
-        const long long rowoff = (long long)O.n[0] * t.row;
-        for (int h = 0; h < 2; h++) {
-            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
-            if (i < O.n[0]) O.p[rowoff + i] += (double)ev[rowoff + i];
-        }
-    }
-}
-
 // One block per grid: sum the block partials in a fixed order and update the
 // state.  mode 0: mean of b.  mode 1: after the starting residual.  mode 2:
 // after a cycle (counts it).  mode 3: mean of the final iterate.  Stopping
@@ -1063,9 +1084,13 @@ void launch_loop_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStr
 }
 
 template <class T>
-void launch_half_rows(const Table &tb, int colour, double omega, int flags, cudaStream_t s)
+void launch_half_rows(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
-    k_half<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc);
+    if (flags & kOuter)
+        k_half<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc, ov);
+    else
+        k_half<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc,
+                                                        nullptr);
 }
 template <class T>
 void launch_restrict_rows(const Table &tb, cudaStream_t s)
@@ -1073,10 +1098,16 @@ void launch_restrict_rows(const Table &tb, cudaStream_t s)
     k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
 }
 template <class T>
-void launch_prolong_rows(const Table &tb, cudaStream_t s)
+void launch_prolong_rows(const Table &tb, const OuterView *ov, cudaStream_t s)
 {
-    if (tb.flux) k_prolong<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
-    else k_prolong<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
+    const int c = tb.cyc;
+    if (tb.flux) {
+        if (ov) k_prolong<T, true, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov);
+        else k_prolong<T, true, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr);
+    } else {
+        if (ov) k_prolong<T, false, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov);
+        else k_prolong<T, false, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr);
+    }
 }
 template <class T>
 void launch_tail(const TailView *tv, int count, size_t smem, double omega, int nu1, int nu2, int cyc,
@@ -1095,9 +1126,9 @@ void launch_apply(const Table &tb, cudaStream_t s)
     k_apply<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
 }
 template <class T>
-void launch_coarse_solve(const CoarseView *cv, int count, int cyc, cudaStream_t s)
+void launch_coarse_solve(const CoarseView *cv, int count, int cyc, const OuterView *ov, cudaStream_t s)
 {
-    k_coarse_solve<T><<<count, kThreads, 0, s>>>(cv, cyc);
+    k_coarse_solve<T><<<count, kThreads, 0, s>>>(cv, cyc, ov);
 }
 void launch_coarse_setup(const CoarseView *cv, int count, cudaStream_t s)
 {
@@ -1143,11 +1174,6 @@ void launch_residual(const OuterTable &ot, int init, cudaStream_t s)
 {
     k_residual<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, init);
 }
-template <class Te>
-void launch_outer_update(const OuterTable &ot, cudaStream_t s)
-{
-    k_outer_update<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
-}
 void launch_finalize(const OuterTable &ot, int mode, cudaStream_t s)
 {
     k_finalize<<<ot.count, kThreads, 0, s>>>(ot.ov, mode);
@@ -1157,21 +1183,19 @@ void launch_final(const OuterTable &ot, cudaStream_t s)
     k_final<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
 }
 
-template void launch_half_rows<float>(const Table &, int, double, int, cudaStream_t);
-template void launch_half_rows<double>(const Table &, int, double, int, cudaStream_t);
+template void launch_half_rows<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_half_rows<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
 template void launch_restrict_rows<float>(const Table &, cudaStream_t);
 template void launch_restrict_rows<double>(const Table &, cudaStream_t);
-template void launch_prolong_rows<float>(const Table &, cudaStream_t);
-template void launch_prolong_rows<double>(const Table &, cudaStream_t);
+template void launch_prolong_rows<float>(const Table &, const OuterView *, cudaStream_t);
+template void launch_prolong_rows<double>(const Table &, const OuterView *, cudaStream_t);
 template void launch_tail<float>(const TailView *, int, size_t, double, int, int, int, cudaStream_t);
 template void launch_tail<double>(const TailView *, int, size_t, double, int, int, int, cudaStream_t);
 template void launch_apply<float>(const Table &, cudaStream_t);
 template void launch_apply<double>(const Table &, cudaStream_t);
-template void launch_coarse_solve<float>(const CoarseView *, int, int, cudaStream_t);
-template void launch_coarse_solve<double>(const CoarseView *, int, int, cudaStream_t);
+template void launch_coarse_solve<float>(const CoarseView *, int, int, const OuterView *, cudaStream_t);
+template void launch_coarse_solve<double>(const CoarseView *, int, int, const OuterView *, cudaStream_t);
 template void launch_residual<float>(const OuterTable &, int, cudaStream_t);
 template void launch_residual<double>(const OuterTable &, int, cudaStream_t);
-template void launch_outer_update<float>(const OuterTable &, cudaStream_t);
-template void launch_outer_update<double>(const OuterTable &, cudaStream_t);
 
 }  // namespace gbmg

@@ -68,8 +68,10 @@ struct CoarsenArgs {
     float *wc32[3];
 };
 
-// red-black half-sweep of one colour; flags: 1 zero initial iterate (red launch)
-constexpr int kHalfZero = 1;
+// red-black half-sweep of one colour; flags: 1 zero initial iterate (red
+// launch), 4 the grids whose refinement step ends with this cycle add the
+// relaxed values to their FP64 iterate (finest level, last post-sweep)
+constexpr int kHalfZero = 1, kHalfOuter = 4;
 int half_sweep_blocks(const int n[3]);
 int restrict_blocks(const int n[3], const int nc[3]);
 int prolong_blocks(const int n[3]);
@@ -79,19 +81,25 @@ int half_sweep_blocks_v(const int n[3], int v);
 int restrict_blocks_v(const int n[3], const int nc[3], int v);
 int prolong_blocks_v(const int n[3], const int nc[3], int v);
 // launchers that dispatch on Table::variant (mg_tiles.cu) ...
-template <class T> void launch_half(const Table &, int colour, double omega, int flags, cudaStream_t);
+// ov: the plan's outer views where the launch may update the FP64 iterate
+// (kHalfOuter; prolongation and coarse solve of the finest level), else null
+template <class T> void launch_half(const Table &, int colour, double omega, int flags,
+                                    const OuterView *ov, cudaStream_t);
 template <class T> void launch_restrict(const Table &, cudaStream_t);
-template <class T> void launch_prolong(const Table &, cudaStream_t);
+template <class T> void launch_prolong(const Table &, const OuterView *ov, cudaStream_t);
 // ... and the row-tiled kernels they fall back to (mg_kernels.cu)
-template <class T> void launch_half_rows(const Table &, int colour, double omega, int flags, cudaStream_t);
+template <class T> void launch_half_rows(const Table &, int colour, double omega, int flags,
+                                         const OuterView *ov, cudaStream_t);
 template <class T> void launch_restrict_rows(const Table &, cudaStream_t);
-template <class T> void launch_prolong_rows(const Table &, cudaStream_t);
+template <class T> void launch_prolong_rows(const Table &, const OuterView *ov, cudaStream_t);
 // V-cycle stages below the row-tiled levels; cyc as Table::cyc
 template <class T> void launch_tail(const TailView *, int count, size_t smem, double omega, int nu1,
                                     int nu2, int cyc, cudaStream_t);
 template <class T> void launch_apply(const Table &, cudaStream_t);
-template <class T> void launch_coarse_solve(const CoarseView *, int count, int cyc, cudaStream_t);
-template <class T> void launch_coarse_gmres(const CoarseView *, int count, int cyc, cudaStream_t);
+template <class T> void launch_coarse_solve(const CoarseView *, int count, int cyc, const OuterView *ov,
+                                            cudaStream_t);
+template <class T> void launch_coarse_gmres(const CoarseView *, int count, int cyc, const OuterView *ov,
+                                            cudaStream_t);
 void launch_coarse_setup(const CoarseView *, int count, cudaStream_t);
 void launch_faces_from_density(const FaceArgs &, cudaStream_t);
 void launch_scale_faces(const FaceArgs &, cudaStream_t);
@@ -102,7 +110,6 @@ void launch_project(const ProjArgs &, cudaStream_t);
 void launch_begin(const OuterView *, int count, cudaStream_t);
 void launch_sum(const OuterTable &, int which, cudaStream_t);
 template <class Te> void launch_residual(const OuterTable &, int init, cudaStream_t);
-template <class Te> void launch_outer_update(const OuterTable &, cudaStream_t);
 void launch_finalize(const OuterTable &, int mode, cudaStream_t);
 void launch_final(const OuterTable &, cudaStream_t);
 void launch_gather_states(const OuterTable &, GridState *out, cudaStream_t);

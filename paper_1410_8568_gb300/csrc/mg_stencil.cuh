@@ -69,9 +69,10 @@ __device__ __forceinline__ T relax_div(T num, T den)
     else return num / den;
 }
 
-// zero flag of the half-sweep: the iterate is zero on entry (first red launch)
-constexpr int kZeroGuess = 1;
-
+// half-sweep flags: the iterate is zero on entry (first red launch); the
+// launch may add its relaxed values to the FP64 iterate (level 0, last
+// post-smoothing sweep, done by the grids whose step ends with this cycle)
+constexpr int kZeroGuess = 1, kOuter = 4;
 
 // Relaxation of the cells of colour `colour` in the aligned quad (4 qx .. 4 qx + 3,
 // j, k) of row `row` = j + ny k.  The two cells of the colour are p0 = 4 qx + par
@@ -101,10 +102,14 @@ __device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn
     return d > T(0) ? xc + omega * relax_div(f - bc, d) : xc;
 }
 
-template <class T>
+// OUT: also add the relaxed values to the FP64 iterate pout (a compile-time
+// choice: a per-thread run-time test would leave predicated FP64 instructions
+// in every launch, and FP64 throughput on this GPU is a small fraction of
+// FP32's; kernels that may update pick one of the two instances per block).
+template <class T, bool OUT>
 __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T *wy, const T *wz,
                                           int nx, int ny, int nz, int per, int row, int j, int k,
-                                          int qx, int colour, T omega, bool zero)
+                                          int qx, int colour, T omega, bool zero, double *pout)
 {
     // cell indices fit in 32 bits: a grid has fewer than 2^31 cells
     const int sy = nx, sz = nx * ny;
@@ -166,6 +171,10 @@ __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T
     out.v[2] = par ? xq.v[2] : v1;
     out.v[3] = par ? v1 : xq.v[3];
     stq(x + c, out);
+    if constexpr (OUT) {
+        pout[c0] += (double)v0;
+        pout[c0 + 2] += (double)v1;
+    }
 }
 
 // Coarse partner of fine index i along an axis of nc coarse cells: the coarse
@@ -336,9 +345,10 @@ __device__ __forceinline__ void lin_x(const T *__restrict__ er, int Im, int I0, 
 }
 
 // x += P e_c on the aligned quad (4 qx .. 4 qx + 3, j, k) of row `row`: same
-// rounding order as prolong_at.
-template <class T>
-__device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j, int k, int qx)
+// rounding order as prolong_at.  OUT: also p += x in FP64 (see half_quad).
+template <class T, bool OUT>
+__device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j, int k, int qx,
+                                             double *__restrict__ pout)
 {
     const int nx = L.n[0], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
     const T *__restrict__ ec = (const T *)L.xc;
@@ -357,6 +367,7 @@ __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j,
 #pragma unroll
     for (int u = 0; u < 4; u++) {
         xq.v[u] += lin(lin(a00[u], a10[u]), lin(a01[u], a11[u]));
+        if constexpr (OUT) pout[c + u] += (double)xq.v[u];
     }
     stq(x + c, xq);
 }
@@ -364,8 +375,9 @@ __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j,
 // Flux-conserving x += P e_c on the aligned quad (4 qx .. 4 qx + 3, j, k): the
 // quad's 4 cells share the coarse x set {Im, I0, I0 + 1, Ip} on the 4 coarse
 // rows (J0 or its partner, K0 or its partner).
-template <class T>
-__device__ __forceinline__ void prolong_quad_flux(const LevelView &L, int row, int j, int k, int qx)
+template <class T, bool OUT>
+__device__ __forceinline__ void prolong_quad_flux(const LevelView &L, int row, int j, int k, int qx,
+                                                  double *__restrict__ pout)
 {
     const int nx = L.n[0], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
     const T *__restrict__ ec = (const T *)L.xc;
@@ -401,6 +413,7 @@ __device__ __forceinline__ void prolong_quad_flux(const LevelView &L, int row, i
             a[q] = av[r][m];
         }
         xq.v[u] += flux_corner_mean(e, a);
+        if constexpr (OUT) pout[c + u] += (double)xq.v[u];
     }
     stq(x + c, xq);
 }

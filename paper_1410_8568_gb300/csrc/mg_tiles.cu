@@ -15,28 +15,43 @@ namespace gbmg {
 // Block lb of a table entry owns items [lb Q B, (lb + 1) Q B); thread t handles
 // lb Q B + q B + t for q < Q.  Items are numbered row by row, so consecutive
 // threads touch consecutive 16-byte vectors.
-template <class T, int B, int Q>
-__global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ lv,
-                                                 const int *__restrict__ start, int count,
-                                                 int colour, T omega, int flags, int cyc)
+template <class T, int B, int Q, bool OUT>
+__device__ __forceinline__ void half_flat_body(const LevelView &L, int lb, int colour, T omega, bool zero,
+                                               double *pout)
 {
-    const int e = find_entry(start, count);
-    const LevelView &L = lv[e];
-    if (!in_cycle(L.st, cyc)) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], nq = nx >> 2;
     const int items = nq * ny * nz;
-    const int lb = blockIdx.x - start[e];
-    const bool zero = flags & kZeroGuess;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
         const int g = (lb * Q + q) * B + (int)threadIdx.x;
         if (g >= items) return;
         const int row = fdiv(g, L.dq);
         const int k = fdiv(row, L.dy);
-        half_quad<T>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
-                     (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
-                     omega, zero);
+        half_quad<T, OUT>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
+                          (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
+                          omega, zero, pout);
     }
+}
+
+// MAYOUT: the launch carries kOuter (see k_half)
+template <class T, int B, int Q, bool MAYOUT>
+__global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ lv,
+                                                 const int *__restrict__ start, int count,
+                                                 int colour, T omega, int flags, int cyc,
+                                                 const OuterView *__restrict__ ov)
+{
+    const int e = find_entry(start, count);
+    const LevelView &L = lv[e];
+    if (!in_cycle(L.st, cyc)) return;
+    const int lb = blockIdx.x - start[e];
+    const bool zero = flags & kZeroGuess;
+    if constexpr (MAYOUT) {
+        if (last_cycle(L.st, cyc)) {
+            half_flat_body<T, B, Q, true>(L, lb, colour, omega, zero, ov[L.g].p);
+            return;
+        }
+    }
+    half_flat_body<T, B, Q, false>(L, lb, colour, omega, zero, nullptr);
 }
 
 template <class T, int B, int Q>
@@ -128,15 +143,19 @@ int restrict_blocks_v(const int n[3], const int nc[3], int v)
 }
 
 template <class T>
-void launch_half(const Table &tb, int colour, double omega, int flags, cudaStream_t s)
+void launch_half(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_half_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega,
-                                                              flags, tb.cyc);
+        if (flags & kOuter)
+            k_half_flat<T, ts.B, ts.Q, true><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
+                                                                        (T)omega, flags, tb.cyc, ov);
+        else
+            k_half_flat<T, ts.B, ts.Q, false><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
+                                                                         (T)omega, flags, tb.cyc, nullptr);
     });
-    if (!flat) launch_half_rows<T>(tb, colour, omega, flags, s);
+    if (!flat) launch_half_rows<T>(tb, colour, omega, flags, ov, s);
 }
 
 template <class T>
@@ -151,25 +170,25 @@ void launch_restrict(const Table &tb, cudaStream_t s)
 }
 
 template <class T>
-void launch_prolong(const Table &tb, cudaStream_t s)
+void launch_prolong(const Table &tb, const OuterView *ov, cudaStream_t s)
 {
     if (tb.blocks == 0) return;
-    if (tb.flux) {  // flux-conserving prolongation: row tiles only
-        launch_prolong_rows<T>(tb, s);
+    if (tb.flux || ov) {  // flux-conserving prolongation, or the FP64 update: row tiles only
+        launch_prolong_rows<T>(tb, ov, s);
         return;
     }
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
         k_prolong_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
     });
-    if (!flat) launch_prolong_rows<T>(tb, s);
+    if (!flat) launch_prolong_rows<T>(tb, nullptr, s);
 }
 
-template void launch_half<float>(const Table &, int, double, int, cudaStream_t);
-template void launch_half<double>(const Table &, int, double, int, cudaStream_t);
+template void launch_half<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
+template void launch_half<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
 template void launch_restrict<float>(const Table &, cudaStream_t);
 template void launch_restrict<double>(const Table &, cudaStream_t);
-template void launch_prolong<float>(const Table &, cudaStream_t);
-template void launch_prolong<double>(const Table &, cudaStream_t);
+template void launch_prolong<float>(const Table &, const OuterView *, cudaStream_t);
+template void launch_prolong<double>(const Table &, const OuterView *, cudaStream_t);
 
 }  // namespace gbmg

@@ -148,8 +148,8 @@ int time_shape(mg_handle *h, int kind, int l, int v, float *ms)
     Table tb{h->dview, h->dstart, 1, blocks, v};
     auto run = [&](int i) {
         if (kind == MG_TILE_RESTRICT) launch_restrict<T>(tb, s);
-        else if (kind == MG_TILE_PROLONG) launch_prolong<T>(tb, s);
-        else launch_half<T>(tb, i & 1, 1.0, 0, s);
+        else if (kind == MG_TILE_PROLONG) launch_prolong<T>(tb, nullptr, s);
+        else launch_half<T>(tb, i & 1, 1.0, 0, nullptr, s);
     };
     cudaEvent_t e0, e1;
     TK(cudaEventCreate(&e0));

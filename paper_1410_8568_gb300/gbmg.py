@@ -24,7 +24,7 @@ STATIC_MAX_CELLS = 512
 NEUMANN, PERIODIC = 0, 1
 FP64, MIXED = 0, 1
 HARMONIC, ARITHMETIC = 0, 1
-K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL, K_UPDATE = range(8)
+K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL = range(7)
 TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
 PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
 SOLVER_MG, SOLVER_PCG = 0, 1

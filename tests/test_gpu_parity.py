@@ -347,15 +347,13 @@ def test_profiling_counts_launches():
         # one launch per colour of each of the nu1 + nu2 sweeps per V-cycle on the finest level
         n, ms = S.profile_read(gbmg.K_SMOOTH, 0)
         assert n == st.iters * 2 * (2 + 2) and ms > 0.0
-        # per refinement step (at most inner_cycles V-cycles each) the FP64
-        # update p += e and the FP64 residual, plus the starting residual
+        # one FP64 residual per refinement step (at most inner_cycles V-cycles
+        # each) plus the starting one
         inner = S.resolved_params()["inner_cycles"]
         assert inner == 3  # the mixed-precision default
         n, ms = S.profile_read(gbmg.K_RESIDUAL, 0)
         assert st.steps >= -(-st.iters // inner)
         assert n == st.steps + 1 and ms > 0.0
-        n, ms = S.profile_read(gbmg.K_UPDATE, 0)
-        assert n == st.steps and ms > 0.0
 
 
 # ---------------------------------------------------------------------------
