@@ -46,13 +46,19 @@ struct GridState {
 };
 
 // A grid takes part in V-cycle `cyc` (0-based) of the current refinement step
-// while it is still iterating and its step asks for more than cyc cycles.  A
-// batch runs as many cycles as its most demanding grid and the others sit the
-// extra ones out, so every grid gets exactly its own arithmetic, alone or
-// batched.
-__device__ __forceinline__ bool in_cycle(const GridState *s, int cyc)
+// while its step asks for more than cyc cycles.  A batch runs as many cycles as
+// its most demanding grid and the others sit the extra ones out, so every grid
+// gets exactly its own arithmetic, alone or batched.  A grid that stopped has
+// cycles_next = 0 (every kernel that clears `active` also clears it), so the
+// test is one load at the head of every V-cycle kernel.
+__device__ __forceinline__ bool in_cycle(const GridState *s, int cyc) { return cyc < s->cycles_next; }
+
+// Stop a grid's iteration with the given status.
+__device__ __forceinline__ void stop_grid(GridState *s, int status)
 {
-    return s->active && cyc < s->cycles_next;
+    s->status = status;
+    s->active = 0;
+    s->cycles_next = 0;
 }
 // V-cycle `cyc` is the last of the grid's current refinement step.
 __device__ __forceinline__ bool last_cycle(const GridState *s, int cyc) { return cyc + 1 == s->cycles_next; }

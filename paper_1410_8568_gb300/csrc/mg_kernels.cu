@@ -983,16 +983,9 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
         s->steps += 1;
     }
     s->rnorm = rn;
-    if (!isfinite(rn)) {
-        s->status = 5;  // MG_EDIVERGED
-        s->active = 0;
-    } else if (s->bnorm == 0.0 || rn <= s->tol * s->bnorm) {
-        s->status = 0;
-        s->active = 0;
-    } else if (s->iters >= s->max_iters) {
-        s->status = 4;  // MG_ENOTCONV
-        s->active = 0;
-    }
+    if (!isfinite(rn)) stop_grid(s, 5);                                      // MG_EDIVERGED
+    else if (s->bnorm == 0.0 || rn <= s->tol * s->bnorm) stop_grid(s, 0);   // converged
+    else if (s->iters >= s->max_iters) stop_grid(s, 4);                      // MG_ENOTCONV
     if (s->active) {
         // V-cycles of the next refinement step: inner, or (adaptive, multigrid
         // iteration) the number the last step's per-cycle reduction rate g

@@ -145,8 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_finalize(const OuterView *__re
         const double dq = out[0];
         const double a = s->rz / dq;
         if (!(dq < 0.0) || !isfinite(a)) {
-            s->status = 5;  // MG_EDIVERGED
-            s->active = 0;
+            stop_grid(s, 5);  // MG_EDIVERGED
             return;
         }
         s->alpha = a;
@@ -155,10 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_finalize(const OuterView *__re
     s->beta = mode == 0 ? 0.0 : -s->alpha * out[0] / s->rz;
     s->rz = out[1];
     s->zmean = out[2] / N;
-    if (!isfinite(s->beta) || !isfinite(s->rz)) {
-        s->status = 5;
-        s->active = 0;
-    }
+    if (!isfinite(s->beta) || !isfinite(s->rz)) stop_grid(s, 5);
 }
 
 void launch_pcg_matvec(const OuterTable &ot, cudaStream_t s)
