@@ -103,6 +103,8 @@ struct Layout {
     size_t alpha64[MG_MAX_LEVELS], alpha32[MG_MAX_LEVELS];
     size_t G, b0, part, err, state, dstate, dview, dstart, dcview, setup_cv, total;
     size_t pcg[4];
+    size_t xp3[3], xb[2], wlo[3];  // extended-precision outer iteration
+    bool xp;
     bool gmres;
     size_t gm;
     int nblk0;
@@ -134,6 +136,10 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
     const size_t N0 = (size_t)g.nx * g.ny * g.nz;
     lay.b0 = c.take(N0 * 8);
     for (int v = 0; v < 4; v++) lay.pcg[v] = p.solver == MG_SOLVER_PCG ? c.take(N0 * 8) : 0;
+    lay.xp = mixed && p.solver == MG_SOLVER_MG;
+    for (int v = 0; v < 3; v++) lay.xp3[v] = lay.xp ? c.take(N0 * 4) : 0;
+    for (int v = 0; v < 2; v++) lay.xb[v] = lay.xp ? c.take(N0 * 4) : 0;
+    for (int v = 0; v < 3; v++) lay.wlo[v] = lay.xp ? c.take(N0 * 4) : 0;
     const int n0[3] = {g.nx, g.ny, g.nz};
     lay.nblk0 = outer_blocks(n0);
     lay.part = c.take((size_t)lay.nblk0 * kPart * 8);
@@ -233,6 +239,7 @@ int Plan::fill(mg_handle *const *handles, int count)
     hs.assign(handles, handles + count);
     G = count;
     mixed = hs[0]->mixed;
+    xp = hs[0]->xp;
     stream = hs[0]->stream;
     prm = hs[0]->prm;
     Lmax = 0;
@@ -399,6 +406,15 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.q = h->pcg[3];
         v.e = h->lev[0].x;
         v.adaptive = prm.adaptive_cycles;
+        v.xp = h->xp ? 1 : 0;
+        v.xq = make_fastdiv(v.n[0] >= 4 ? (unsigned)(v.n[0] >> 2) : 1u);
+        v.xy = make_fastdiv((unsigned)v.n[1]);
+        for (int q = 0; q < 3; q++) {
+            v.xp3[q] = h->xp3[q];
+            v.w32[q] = h->xp ? h->lev[0].w32[q] : nullptr;
+            v.wlo[q] = h->wlo[q];
+        }
+        for (int q = 0; q < 2; q++) v.xb[q] = h->xb[q];
     }
     CK(cudaMemcpyAsync(mem, stage_h, tables_bytes, cudaMemcpyHostToDevice, stream));
     CK(cudaEventRecord(staged, stream));
@@ -543,9 +559,22 @@ static void prologue(Plan &P, Prof &pf)
     launch_sum(P.ot, 0, s);
     launch_finalize(P.ot, 0, s);
     pf.end(s);
-    pf.begin(s, MG_K_RESIDUAL, 0);
-    launch_residual<T>(P.ot, 1, s);
-    pf.end(s);
+    if (P.xp) {
+        // extended precision: b - mean b and its norm (FP64), the scale, the
+        // float forms of b and p, the starting residual in FP32 arithmetic
+        pf.begin(s, MG_K_OTHER, 0);
+        launch_xp_b0(P.ot, s);
+        launch_finalize(P.ot, 4, s);
+        launch_xp_prepare(P.ot, s);
+        pf.end(s);
+        pf.begin(s, MG_K_RESIDUAL, 0);
+        launch_residual_xp(P.ot, s);
+        pf.end(s);
+    } else {
+        pf.begin(s, MG_K_RESIDUAL, 0);
+        launch_residual<T>(P.ot, 1, s);
+        pf.end(s);
+    }
     pf.begin(s, MG_K_OTHER, 0);
     launch_finalize(P.ot, 1, s);
     pf.end(s);
@@ -591,7 +620,8 @@ static void body_residual(Plan &P, Prof &pf)
 {
     const cudaStream_t s = P.stream;
     pf.begin(s, MG_K_RESIDUAL, 0);
-    launch_residual<T>(P.ot, 0, s);
+    if (P.xp) launch_residual_xp(P.ot, s);
+    else launch_residual<T>(P.ot, 0, s);
     pf.end(s);
     pf.begin(s, MG_K_OTHER, 0);
     launch_finalize(P.ot, 2, s);
@@ -891,6 +921,7 @@ int gbmg::set_faces_impl(mg_handle *h, const double *ax, const double *ay, const
         a.scale[d] = 1.0 / (h->lev[0].h[d] * h->lev[0].h[d]);
         a.out64[d] = h->lev[0].w64[d];
         a.out32[d] = h->mixed ? h->lev[0].w32[d] : nullptr;
+        a.out32lo[d] = h->wlo[d];
     }
     a.per = h->per;
     a.err = h->err;
@@ -909,6 +940,7 @@ static int set_density_impl(mg_handle *h, const double *rho, int mode)
         a.scale[d] = 1.0 / (h->lev[0].h[d] * h->lev[0].h[d]);
         a.out64[d] = h->lev[0].w64[d];
         a.out32[d] = h->mixed ? h->lev[0].w32[d] : nullptr;
+        a.out32lo[d] = h->wlo[d];
     }
     a.per = h->per;
     a.mode = mode;
@@ -973,6 +1005,10 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
     h->gm = lay.gmres ? (double *)(h->slab + lay.gm) : nullptr;
     h->b0 = (double *)(h->slab + lay.b0);
     for (int v = 0; v < 4; v++) h->pcg[v] = lay.pcg[v] ? (double *)(h->slab + lay.pcg[v]) : nullptr;
+    h->xp = lay.xp;
+    for (int v = 0; v < 3; v++) h->xp3[v] = lay.xp ? (float *)(h->slab + lay.xp3[v]) : nullptr;
+    for (int v = 0; v < 2; v++) h->xb[v] = lay.xp ? (float *)(h->slab + lay.xb[v]) : nullptr;
+    for (int v = 0; v < 3; v++) h->wlo[v] = lay.xp ? (float *)(h->slab + lay.wlo[v]) : nullptr;
     h->part = (double *)(h->slab + lay.part);
     h->nblk0 = lay.nblk0;
     h->err = (int *)(h->slab + lay.err);

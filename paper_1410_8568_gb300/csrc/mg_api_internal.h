@@ -89,6 +89,12 @@ struct mg_handle {
     double *pcg[4] = {nullptr, nullptr, nullptr, nullptr};  // CG: r, z, d, q (FP64, finest level)
     bool gmres = false;        // coarsest grid solved by GMRES (no dense inverse)
     double *gm = nullptr;      // GMRES scratch
+    // extended-precision outer iteration (mixed precision, multigrid iteration):
+    // three-float iterate, float-pair right-hand side, low parts of the level-0 faces
+    bool xp = false;
+    float *xp3[3] = {nullptr, nullptr, nullptr};
+    float *xb[2] = {nullptr, nullptr};
+    float *wlo[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace gbmg {
@@ -99,6 +105,7 @@ struct Plan {
     int G = 0;
     int Lmax = 0;
     bool mixed = true;
+    bool xp = false;  // extended-precision outer iteration (every handle of a plan shares its params)
     mg_params prm;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;

@@ -43,6 +43,7 @@ struct GridState {
     double alpha;   //   step length
     double beta;    //   direction update
     double zmean;   //   mean of the preconditioned residual
+    double xscale;  // extended-precision outer iteration: internal iterate = p * xscale (a power of 2)
 };
 
 // A grid takes part in V-cycle `cyc` (0-based) of the current refinement step
@@ -159,7 +160,30 @@ struct OuterView {
     double *r64, *z, *d, *q;
     const void *e;
     int adaptive;        // choose the V-cycles of each refinement step from the measured rate
+    // extended-precision outer iteration (mixed-precision multigrid iteration,
+    // mg_xprec.cuh): iterate p * xscale = xp[0] + xp[1] + xp[2], right-hand
+    // side (b - mean b) * xscale = xb[0] + xb[1], level-0 faces w32[d] + wlo[d]
+    int xp;
+    FastDiv xq, xy;      // division by the quads per row n[0] / 4 and by n[1]
+    float *xp3[3];
+    float *xb[2];
+    const float *w32[3];
+    const float *wlo[3];
 };
+
+// Where a kernel adds the final correction of a refinement step: the FP64
+// iterate (FP64 cycles) or the three-float iterate (FP32 cycles).
+struct OuterOut {
+    double *p;
+    float *t[3];
+};
+__device__ __forceinline__ OuterOut outer_out(const OuterView &O)
+{
+    OuterOut o;
+    o.p = O.p;
+    for (int q = 0; q < 3; q++) o.t[q] = O.xp3[q];
+    return o;
+}
 
 // The coarsest level of one grid.
 struct CoarseView {

@@ -11,6 +11,7 @@
 // after gm_max Arnoldi steps; e is returned with zero mean.  Every dot product
 // is a fixed-order block reduction, so the result is deterministic.
 #include "mg_kernels.h"
+#include "mg_stencil.cuh"
 
 #include <math.h>
 
@@ -166,11 +167,12 @@ __global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView
     const double em = block_all_sum(s, red) / n;
     T *x = (T *)C.x;
     // single-level grid: the last cycle of a refinement step also updates p
-    double *pout = (ov != nullptr && C.outer && last_cycle(C.st, cyc)) ? ov[C.g].p : nullptr;
+    const bool out = ov != nullptr && C.outer && last_cycle(C.st, cyc);
+    const OuterOut po = out ? outer_out(ov[C.g]) : OuterOut{};
     for (int c = tid; c < n; c += nt) {
         const T xn = (T)(e[c] - em);
         x[c] = xn;
-        if (pout) pout[c] += (double)xn;
+        if (out) add_outer<T>(po, c, xn);
     }
 }
 

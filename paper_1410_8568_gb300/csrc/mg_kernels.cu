@@ -130,7 +130,7 @@ struct LoadPlain {
 // cyc: index of the V-cycle within its refinement step (in_cycle).
 template <class T, bool OUT>
 __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour, T omega, bool zero,
-                                          double *__restrict__ pout)
+                                          const OuterOut &po)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], per = L.per;
     T *__restrict__ x = (T *)L.x;
@@ -163,7 +163,7 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
                 v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
             }
             x[c] = v;
-            if constexpr (OUT) pout[c] += (double)v;
+            if constexpr (OUT) add_outer<T>(po, (int)c, v);
         }
         return;
     }
@@ -177,7 +177,7 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
     if (row >= ny * nz) return;
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
-    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, pout);
+    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, po);
 }
 
 // MAYOUT: the launch carries kOuter; the test of the step's last cycle is
@@ -195,11 +195,11 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
     const bool zero = flags & kZeroGuess;
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
-            half_body<T, true>(L, lb, colour, omega, zero, ov[L.g].p);
+            half_body<T, true>(L, lb, colour, omega, zero, outer_out(ov[L.g]));
             return;
         }
     }
-    half_body<T, false>(L, lb, colour, omega, zero, nullptr);
+    half_body<T, false>(L, lb, colour, omega, zero, OuterOut{});
 }
 
 // Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64
@@ -282,7 +282,7 @@ int restrict_blocks(const int n[3], const int nc[3])
 // ---------------------------------------------------------------------------
 
 template <class T, bool FLUX, bool OUT>
-__device__ __forceinline__ void prolong_body(const LevelView &L, int lb, double *__restrict__ pout)
+__device__ __forceinline__ void prolong_body(const LevelView &L, int lb, const OuterOut &po)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const T *ec = (const T *)L.xc;
@@ -295,8 +295,8 @@ __device__ __forceinline__ void prolong_body(const LevelView &L, int lb, double 
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
-        if constexpr (FLUX) prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, pout);
-        else prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, pout);
+        if constexpr (FLUX) prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, po);
+        else prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, po);
         return;
     }
     const Tile t = fine_tile(L.n, lb);
@@ -309,7 +309,7 @@ __device__ __forceinline__ void prolong_body(const LevelView &L, int lb, double 
         const T xn = x[c] + (FLUX ? prolong_at_flux(ec, (const T *)L.ac, L.nc, L.per, i, t.j, t.k)
                                   : prolong_at(ec, L.nc, L.per, i, t.j, t.k));
         x[c] = xn;
-        if constexpr (OUT) pout[c] += (double)xn;
+        if constexpr (OUT) add_outer<T>(po, (int)c, xn);
     }
 }
 
@@ -324,11 +324,11 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
     const int lb = blockIdx.x - start[e];
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
-            prolong_body<T, FLUX, true>(L, lb, ov[L.g].p);
+            prolong_body<T, FLUX, true>(L, lb, outer_out(ov[L.g]));
             return;
         }
     }
-    prolong_body<T, FLUX, false>(L, lb, nullptr);
+    prolong_body<T, FLUX, false>(L, lb, OuterOut{});
 }
 
 // ---------------------------------------------------------------------------
@@ -575,7 +575,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__r
     for (int t = threadIdx.x; t < n; t += blockDim.x) rb[t] = (double)b[t];
     __syncthreads();
     T *x = (T *)C.x;
-    double *pout = (ov != nullptr && C.outer && last_cycle(C.st, cyc)) ? ov[C.g].p : nullptr;
+    const bool out = ov != nullptr && C.outer && last_cycle(C.st, cyc);
+    const OuterOut po = out ? outer_out(ov[C.g]) : OuterOut{};
     const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
     for (int t = threadIdx.x >> 5; t < n; t += warps) {
         const double *Gt = C.G + (long long)t * n;
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__r
         if (lane == 0) {
             const T xn = (T)(-s);
             x[t] = xn;
-            if (pout) pout[t] += (double)xn;
+            if (out) add_outer<T>(po, t, xn);
         }
     }
 }
@@ -705,6 +706,7 @@ __global__ void __launch_bounds__(kThreads) k_faces_from_density(FaceArgs a)
             v *= a.scale[d];
             if (a.out64[d]) a.out64[d][c] = v;
             if (a.out32[d]) a.out32[d][c] = (float)v;
+            if (a.out32lo[d]) a.out32lo[d][c] = (float)(v - (double)(float)v);
         }
         if (!ok && a.err) *a.err = 1;
     }
@@ -728,6 +730,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_faces(FaceArgs a)
             }
             a.out64[d][c] = v;
             if (a.out32[d]) a.out32[d][c] = (float)v;
+            if (a.out32lo[d]) a.out32lo[d][c] = (float)(v - (double)(float)v);
         }
     }
 }
@@ -863,6 +866,7 @@ __global__ void k_begin(const OuterView *__restrict__ ov)
     s->xmean = 0.0;
     s->cycles_next = O.inner < O.max_iters ? O.inner : O.max_iters;
     s->steps = 0;
+    s->xscale = 1.0;
     s->rprev = 0.0;
 }
 
@@ -876,6 +880,9 @@ __global__ void __launch_bounds__(kThreads) k_sum(const OuterView *__restrict__ 
     const int lb = blockIdx.x - start[e];
     const int ntiles = fine_blocks(O.n);
     const double *src = which == 0 ? O.b : O.p;
+    // end of an extended-precision solve that took a step: the iterate is the
+    // three-float one (summed in its internal scale)
+    const bool conv = which == 1 && xp_live(O);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
         const Tile t = fine_tile(O.n, tile);
@@ -883,13 +890,246 @@ __global__ void __launch_bounds__(kThreads) k_sum(const OuterView *__restrict__ 
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {
             const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
-            if (i < O.n[0]) v[0] += src[rowoff + i];
+            if (i >= O.n[0]) continue;
+            const long long c = rowoff + i;
+            if (conv) {
+                v[0] += ((double)O.xp3[0][c] + (double)O.xp3[1][c]) + (double)O.xp3[2][c];
+            } else {
+                v[0] += src[c];
+            }
         }
     }
     double out[4];
     block_sum4(v, out);
     if (threadIdx.x == 0) O.part[kPart * lb + (which == 0 ? 3 : 1)] = out[0];
 }
+
+// ---- extended-precision outer iteration (mixed-precision multigrid) --------
+//
+// The FP64 prologue reduces the right-hand side; the refinement loop itself
+// runs in FP32 arithmetic on the three-float iterate (mg_xprec.cuh); the
+// epilogue converts back.  Internal quantities are scaled by xscale = 2^-k,
+// k chosen from the right-hand side's rms, so that the float components stay
+// far from the FP32 exponent limits whatever the scale of the problem.
+
+// Split an FP64 value into floats: v = h + m (+ z): exact for z (the 53-bit
+// significand fits 72 bits), to 2^-48 |v| for the pair.
+__device__ __forceinline__ void split3(double v, float &h, float &m, float &z)
+{
+    h = (float)v;
+    const double r = v - (double)h;
+    m = (float)r;
+    z = (float)(r - (double)m);
+}
+
+// b0 = b - mean(b) in FP64 and the partial sums of ||b0||^2 (slot 2).
+__global__ void __launch_bounds__(kThreads) k_xp_b0(const OuterView *__restrict__ ov,
+                                                    const int *__restrict__ start, int count)
+{
+    const int e = find_entry(start, count);
+    const OuterView O = ov[e];
+    if (!O.st->active) return;
+    const int lb = blockIdx.x - start[e];
+    const int ntiles = fine_blocks(O.n);
+    const double m = O.st->bmean;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int tile = lb; tile < ntiles; tile += O.nblk) {
+        const Tile t = fine_tile(O.n, tile);
+        if (!t.ok) continue;
+        const long long rowoff = (long long)O.n[0] * t.row;
+        for (int h = 0; h < 2; h++) {
+            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+            if (i >= O.n[0]) continue;
+            const double bc = O.b[rowoff + i] - m;
+            O.b0[rowoff + i] = bc;
+            v[2] += bc * bc;
+        }
+    }
+    double out[4];
+    block_sum4(v, out);
+    if (threadIdx.x == 0) O.part[kPart * lb + 2] = out[2];
+}
+
+// Scaled right-hand side and iterate in their float forms.
+__global__ void __launch_bounds__(kThreads) k_xp_prepare(const OuterView *__restrict__ ov,
+                                                         const int *__restrict__ start, int count)
+{
+    const int e = find_entry(start, count);
+    const OuterView O = ov[e];
+    if (!O.st->active) return;
+    const int lb = blockIdx.x - start[e];
+    const int ntiles = fine_blocks(O.n);
+    const double sc = O.st->xscale;
+    for (int tile = lb; tile < ntiles; tile += O.nblk) {
+        const Tile t = fine_tile(O.n, tile);
+        if (!t.ok) continue;
+        const long long rowoff = (long long)O.n[0] * t.row;
+        for (int h = 0; h < 2; h++) {
+            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+            if (i >= O.n[0]) continue;
+            const long long c = rowoff + i;
+            float z;
+            split3(O.b0[c] * sc, O.xb[0][c], O.xb[1][c], z);
+            split3(O.p[c] * sc, O.xp3[0][c], O.xp3[1][c], O.xp3[2][c]);
+        }
+    }
+}
+
+// One face of the residual: (F0, F1) += w (p_nb - p_c), w = w0 + w1
+#define XP_FACE(NB, W0, W1)                                                                    \
+    do {                                                                                       \
+        const int nb_ = (NB);                                                                  \
+        float l_;                                                                              \
+        const float h_ = triple_diff(P0[nb_], P1[nb_], P2[nb_], a0, a1, a2, l_);               \
+        pair_fma_acc(F0, F1, h_, l_, (W0), (W1));                                              \
+    } while (0)
+
+// r = (b - mean b) - A p in the three-float arithmetic, scaled: the V-cycle's
+// FP32 right-hand side, and the partial sums of ||r||^2 (slot 0, accumulated
+// from the rounded r as in the FP64 kernel).  Every cell sums its faces in the
+// order of flux64 (x low, x high, y low, y high, z low, z high).  Rows of a
+// multiple of 4 cells: a thread takes an aligned quad, loads every operand as
+// 16-byte vectors and treats wall faces as faces of zero weight (the stored
+// low wall face is 0; its neighbour index is the cell itself), so the loads
+// carry no branches; the zero terms leave the sums unchanged.  Other rows: one
+// cell at a time, wall faces skipped.
+__global__ void __launch_bounds__(kThreads) k_residual_xp(const OuterView *__restrict__ ov,
+                                                          const int *__restrict__ start, int count)
+{
+    const int e = find_entry(start, count);
+    const OuterView &O = ov[e];
+    if (!O.st->active) return;
+    const int lb = blockIdx.x - start[e];
+    const int nx = O.n[0], ny = O.n[1], nz = O.n[2], per = O.per, nblk = O.nblk;
+    const int sy = nx, sz = nx * ny;  // grids have fewer than 2^31 cells
+    const float *__restrict__ P0 = O.xp3[0];
+    const float *__restrict__ P1 = O.xp3[1];
+    const float *__restrict__ P2 = O.xp3[2];
+    const float *__restrict__ wx = O.w32[0];
+    const float *__restrict__ wy = O.w32[1];
+    const float *__restrict__ wz = O.w32[2];
+    const float *__restrict__ lx = O.wlo[0];
+    const float *__restrict__ ly = O.wlo[1];
+    const float *__restrict__ lz = O.wlo[2];
+    const float *__restrict__ B0 = O.xb[0];
+    const float *__restrict__ B1 = O.xb[1];
+    float *__restrict__ r = (float *)O.r;
+    float racc = 0.f;
+    if ((nx & 3) == 0) {
+        const int nq = nx >> 2, items = nq * ny * nz;
+        const FastDiv dq = O.xq, dy = O.xy;
+        for (int g = lb * kThreads + (int)threadIdx.x; g < items; g += nblk * kThreads) {
+            const int row = fdiv(g, dq);
+            const int k = fdiv(row, dy), j = row - k * ny;
+            const int i0 = (g - row * nq) << 2;
+            const int c = row * nx + i0;
+            const bool has_e = i0 + 4 < nx || (per & 1);
+            const int cw = i0 > 0 ? c - 1 : ((per & 1) ? c + nx - 1 : c);
+            const int ce = i0 + 4 < nx ? c + 4 : ((per & 1) ? c + 4 - nx : c + 3);
+            const bool has_n = j + 1 < ny || (per & 2), has_t = k + 1 < nz || (per & 4);
+            const int ds = j > 0 ? -sy : ((per & 2) ? sy * (ny - 1) : 0);
+            const int dn = j + 1 < ny ? sy : ((per & 2) ? -sy * (ny - 1) : 0);
+            const int db = k > 0 ? -sz : ((per & 4) ? sz * (nz - 1) : 0);
+            const int dt = k + 1 < nz ? sz : ((per & 4) ? -sz * (nz - 1) : 0);
+            const float4 A0 = *(const float4 *)(P0 + c), A1 = *(const float4 *)(P1 + c),
+                         A2 = *(const float4 *)(P2 + c);
+            const float a0[4] = {A0.x, A0.y, A0.z, A0.w}, a1[4] = {A1.x, A1.y, A1.z, A1.w},
+                        a2[4] = {A2.x, A2.y, A2.z, A2.w};
+            float F0[4] = {0.f, 0.f, 0.f, 0.f}, F1[4] = {0.f, 0.f, 0.f, 0.f};
+            auto term = [&](int u, float n0, float n1, float n2, float w0, float w1) {
+                float l;
+                const float h = triple_diff(n0, n1, n2, a0[u], a1[u], a2[u], l);
+                pair_fma_acc(F0[u], F1[u], h, l, w0, w1);
+            };
+            {
+                const float4 X0 = *(const float4 *)(wx + c), X1 = *(const float4 *)(lx + c);
+                const float x0[5] = {X0.x, X0.y, X0.z, X0.w, has_e ? wx[ce] : 0.f};
+                const float x1[5] = {X1.x, X1.y, X1.z, X1.w, has_e ? lx[ce] : 0.f};
+                const float w0v = P0[cw], w1v = P1[cw], w2v = P2[cw];
+                const float e0v = P0[ce], e1v = P1[ce], e2v = P2[ce];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (u == 0) term(0, w0v, w1v, w2v, x0[0], x1[0]);
+                    else term(u, a0[u - 1], a1[u - 1], a2[u - 1], x0[u], x1[u]);
+                    if (u == 3) term(3, e0v, e1v, e2v, x0[4], x1[4]);
+                    else term(u, a0[u + 1], a1[u + 1], a2[u + 1], x0[u + 1], x1[u + 1]);
+                }
+            }
+            auto axis = [&](int dlo, int dhi, bool has_hi, const float *w, const float *wl) {
+                const float4 L0 = *(const float4 *)(P0 + c + dlo), L1 = *(const float4 *)(P1 + c + dlo),
+                             L2 = *(const float4 *)(P2 + c + dlo);
+                const float4 H0 = *(const float4 *)(P0 + c + dhi), H1 = *(const float4 *)(P1 + c + dhi),
+                             H2 = *(const float4 *)(P2 + c + dhi);
+                const float4 WL0 = *(const float4 *)(w + c), WL1 = *(const float4 *)(wl + c);
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 WH0 = has_hi ? *(const float4 *)(w + c + dhi) : z4;
+                const float4 WH1 = has_hi ? *(const float4 *)(wl + c + dhi) : z4;
+                const float l0[4] = {L0.x, L0.y, L0.z, L0.w}, l1[4] = {L1.x, L1.y, L1.z, L1.w},
+                            l2[4] = {L2.x, L2.y, L2.z, L2.w};
+                const float h0[4] = {H0.x, H0.y, H0.z, H0.w}, h1[4] = {H1.x, H1.y, H1.z, H1.w},
+                            h2[4] = {H2.x, H2.y, H2.z, H2.w};
+                const float wl0[4] = {WL0.x, WL0.y, WL0.z, WL0.w}, wl1[4] = {WL1.x, WL1.y, WL1.z, WL1.w};
+                const float wh0[4] = {WH0.x, WH0.y, WH0.z, WH0.w}, wh1[4] = {WH1.x, WH1.y, WH1.z, WH1.w};
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    term(u, l0[u], l1[u], l2[u], wl0[u], wl1[u]);
+                    term(u, h0[u], h1[u], h2[u], wh0[u], wh1[u]);
+                }
+            };
+            axis(ds, dn, has_n, wy, ly);
+            axis(db, dt, has_t, wz, lz);
+            const float4 Q0 = *(const float4 *)(B0 + c), Q1 = *(const float4 *)(B1 + c);
+            const float q0[4] = {Q0.x, Q0.y, Q0.z, Q0.w}, q1[4] = {Q1.x, Q1.y, Q1.z, Q1.w};
+            float rq[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                float tt;
+                const float hh = two_diff(q0[u], F0[u], tt);
+                rq[u] = __fadd_rn(hh, __fadd_rn(tt, __fsub_rn(q1[u], F1[u])));
+                racc = __fmaf_rn(rq[u], rq[u], racc);
+            }
+            *(float4 *)(r + c) = make_float4(rq[0], rq[1], rq[2], rq[3]);
+        }
+    } else {
+        const int n3[3] = {nx, ny, nz};
+        const int ntiles = fine_blocks(n3);
+        for (int tile = lb; tile < ntiles; tile += nblk) {
+            const Tile t = fine_tile(n3, tile);
+            if (!t.ok) continue;
+            const int rowoff = nx * t.row;
+            const int j = t.j, k = t.k;
+            for (int h = 0; h < 2; h++) {
+                const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+                if (i >= nx) continue;
+                const int c = rowoff + i;
+                const float a0 = P0[c], a1 = P1[c], a2 = P2[c];
+                float F0 = 0.f, F1 = 0.f;
+                if (i > 0) XP_FACE(c - 1, wx[c], lx[c]);
+                else if (per & 1) XP_FACE(c + nx - 1, wx[c], lx[c]);
+                if (i + 1 < nx) XP_FACE(c + 1, wx[c + 1], lx[c + 1]);
+                else if (per & 1) XP_FACE(c + 1 - nx, wx[c + 1 - nx], lx[c + 1 - nx]);
+                if (j > 0) XP_FACE(c - sy, wy[c], ly[c]);
+                else if (per & 2) XP_FACE(c + sy * (ny - 1), wy[c], ly[c]);
+                if (j + 1 < ny) XP_FACE(c + sy, wy[c + sy], ly[c + sy]);
+                else if (per & 2) XP_FACE(c - sy * (ny - 1), wy[c - sy * (ny - 1)], ly[c - sy * (ny - 1)]);
+                if (k > 0) XP_FACE(c - sz, wz[c], lz[c]);
+                else if (per & 4) XP_FACE(c + sz * (nz - 1), wz[c], lz[c]);
+                if (k + 1 < nz) XP_FACE(c + sz, wz[c + sz], lz[c + sz]);
+                else if (per & 4) XP_FACE(c - sz * (nz - 1), wz[c - sz * (nz - 1)], lz[c - sz * (nz - 1)]);
+                float tt;
+                const float hh = two_diff(B0[c], F0, tt);
+                const float rc = __fadd_rn(hh, __fadd_rn(tt, __fsub_rn(B1[c], F1)));
+                r[c] = rc;
+                racc = __fmaf_rn(rc, rc, racc);
+            }
+        }
+    }
+    double v[4] = {(double)racc, 0.0, 0.0, 0.0};
+    double out[4];
+    block_sum4(v, out);
+    if (threadIdx.x == 0) O.part[kPart * lb + 0] = out[0];
+}
+#undef XP_FACE
 
 // Outer residual r = (b - mean b) - A p in FP64, handed to the V-cycle in its
 // precision Te.  init = 1 (start of a solve): also stores b0 = b - mean(b) and
@@ -949,7 +1189,8 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
 
 // One block per grid: sum the block partials in a fixed order and update the
 // state.  mode 0: mean of b.  mode 1: after the starting residual.  mode 2:
-// after a cycle (counts it).  mode 3: mean of the final iterate.  Stopping
+// after a cycle (counts it).  mode 3: mean of the final iterate.  mode 4
+// (extended precision): ||b - mean b|| and the internal scale.  Stopping
 // test: ||r|| <= tol ||b||; NaN/Inf residual = diverged; max_iters reached =
 // not converged.
 __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restrict__ ov, int mode)
@@ -972,10 +1213,21 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
         s->xmean = out[1] / N;
         return;
     }
-    const double rn = sqrt(out[0]);
+    if (mode == 4) {
+        // extended precision: ||b - mean b|| and the internal scale 2^-k,
+        // 2^k near the rms of b - mean b (k kept inside the FP32 exponent range)
+        s->bnorm = sqrt(out[2]);
+        const double rms = s->bnorm / sqrt(N);
+        int k = (rms > 0.0 && isfinite(rms)) ? ilogb(rms) : 0;
+        k = k < -100 ? -100 : (k > 100 ? 100 : k);
+        s->xscale = ldexp(1.0, -k);
+        return;
+    }
+    // extended precision: the partials are of the scaled residual
+    const double rn = O.xp ? sqrt(out[0]) / s->xscale : sqrt(out[0]);
     int done = 0;
     if (mode == 1) {
-        s->bnorm = sqrt(out[2]);
+        if (!O.xp) s->bnorm = sqrt(out[2]);
         s->r0 = rn;
     } else {
         done = s->cycles_next;
@@ -1005,7 +1257,10 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
     s->rprev = rn;
 }
 
-// End of a solve: p = p - mean(p) (a zero right-hand side gives p = 0).
+// End of a solve: p = p - mean(p) (a zero right-hand side gives p = 0).  After
+// an extended-precision solve p = ((p0 - mean) + p1 + p2) / xscale from the
+// three-float iterate: the mean leaves the leading component first, so a
+// constant carried by the iterate costs no accuracy in the FP64 result.
 __global__ void __launch_bounds__(kThreads) k_final(const OuterView *__restrict__ ov,
                                                     const int *__restrict__ start, int count)
 {
@@ -1016,13 +1271,21 @@ __global__ void __launch_bounds__(kThreads) k_final(const OuterView *__restrict_
     const int ntiles = fine_blocks(O.n);
     const double m = s->xmean;
     const bool zero = s->bnorm == 0.0;
+    const bool conv = xp_live(O);
+    const double inv = conv ? 1.0 / s->xscale : 1.0;  // a power of 2: exact
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
         const Tile t = fine_tile(O.n, tile);
         if (!t.ok) continue;
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {
             const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
-            if (i < O.n[0]) O.p[rowoff + i] = zero ? 0.0 : O.p[rowoff + i] - m;
+            if (i >= O.n[0]) continue;
+            const long long c = rowoff + i;
+            double v;
+            if (zero) v = 0.0;
+            else if (conv) v = ((((double)O.xp3[0][c] - m) + (double)O.xp3[1][c]) + (double)O.xp3[2][c]) * inv;
+            else v = O.p[c] - m;
+            O.p[c] = v;
         }
     }
 }
@@ -1166,6 +1429,18 @@ template <class Te>
 void launch_residual(const OuterTable &ot, int init, cudaStream_t s)
 {
     k_residual<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, init);
+}
+void launch_xp_b0(const OuterTable &ot, cudaStream_t s)
+{
+    k_xp_b0<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+}
+void launch_xp_prepare(const OuterTable &ot, cudaStream_t s)
+{
+    k_xp_prepare<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+}
+void launch_residual_xp(const OuterTable &ot, cudaStream_t s)
+{
+    k_residual_xp<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
 }
 void launch_finalize(const OuterTable &ot, int mode, cudaStream_t s)
 {

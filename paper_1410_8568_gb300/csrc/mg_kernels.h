@@ -33,7 +33,8 @@ struct FaceArgs {
     const double *in[3];     // caller faces (scale_faces)
     double scale[3];         // 1 for raw alpha, 1/h_d^2 for level-0 coefficients
     double *out64[3];
-    float *out32[3];         // optional FP32 copy
+    float *out32[3];         // optional FP32 copy (round to nearest)
+    float *out32lo[3];       // optional: out64 - out32 rounded to FP32 (float-pair faces)
     int *err;                // set to 1 on a non-positive / non-finite value
 };
 
@@ -110,6 +111,11 @@ void launch_project(const ProjArgs &, cudaStream_t);
 void launch_begin(const OuterView *, int count, cudaStream_t);
 void launch_sum(const OuterTable &, int which, cudaStream_t);
 template <class Te> void launch_residual(const OuterTable &, int init, cudaStream_t);
+// extended-precision outer iteration (mixed-precision multigrid iteration):
+// b - mean b and its norm; the scaled float forms of b and p; the residual
+void launch_xp_b0(const OuterTable &, cudaStream_t);
+void launch_xp_prepare(const OuterTable &, cudaStream_t);
+void launch_residual_xp(const OuterTable &, cudaStream_t);
 void launch_finalize(const OuterTable &, int mode, cudaStream_t);
 void launch_final(const OuterTable &, cudaStream_t);
 void launch_gather_states(const OuterTable &, GridState *out, cudaStream_t);

@@ -32,6 +32,10 @@ __device__ __forceinline__ void block_sum4(double v[4], double *out)
     }
 }
 
+// The grid's iterate lives in the three-float form: an extended-precision
+// solve that took at least one refinement step.
+__device__ __forceinline__ bool xp_live(const OuterView &O) { return O.xp && O.st->steps > 0; }
+
 // Row-tile coordinates of this thread for a fine launch (2 cells per lane).
 struct Tile {
     int row, j, k, xbase;

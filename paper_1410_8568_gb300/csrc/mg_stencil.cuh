@@ -9,6 +9,7 @@
 #pragma once
 
 #include "mg_device.cuh"
+#include "mg_xprec.cuh"
 
 namespace gbmg {
 
@@ -102,14 +103,60 @@ __device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn
     return d > T(0) ? xc + omega * relax_div(f - bc, d) : xc;
 }
 
-// OUT: also add the relaxed values to the FP64 iterate pout (a compile-time
-// choice: a per-thread run-time test would leave predicated FP64 instructions
-// in every launch, and FP64 throughput on this GPU is a small fraction of
-// FP32's; kernels that may update pick one of the two instances per block).
+// Add the final correction v of cell c of a refinement step to the outer
+// iterate: p += v in FP64 (FP64 cycles) or the exact three-float update
+// (FP32 cycles, mg_xprec.cuh).
+template <class T>
+__device__ __forceinline__ void add_outer(const OuterOut &o, int c, T v)
+{
+    if constexpr (sizeof(T) == 8) {
+        o.p[c] += v;
+    } else {
+        float a = o.t[0][c], m = o.t[1][c], z = o.t[2][c];
+        triple_add(a, m, z, v);
+        o.t[0][c] = a;
+        o.t[1][c] = m;
+        o.t[2][c] = z;
+    }
+}
+
+// The same for the cells of an aligned quad at c (4 | c) selected by `sel`
+// (bit u: cell c + u), with the three-float components moved as 16-byte vectors.
+template <class T>
+__device__ __forceinline__ void add_outer_quad(const OuterOut &o, int c, const T v[4], int sel)
+{
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (sel >> u & 1) o.p[c + u] += v[u];
+    } else {
+        float4 a = *(const float4 *)(o.t[0] + c), m = *(const float4 *)(o.t[1] + c),
+               z = *(const float4 *)(o.t[2] + c);
+        float *pa = &a.x, *pm = &m.x, *pz = &z.x;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            float a1 = pa[u], m1 = pm[u], z1 = pz[u];
+            triple_add(a1, m1, z1, v[u]);
+            const bool on = sel >> u & 1;
+            pa[u] = on ? a1 : pa[u];
+            pm[u] = on ? m1 : pm[u];
+            pz[u] = on ? z1 : pz[u];
+        }
+        *(float4 *)(o.t[0] + c) = a;
+        *(float4 *)(o.t[1] + c) = m;
+        *(float4 *)(o.t[2] + c) = z;
+    }
+}
+
+// OUT: also add the relaxed values to the outer iterate (add_outer; a
+// compile-time choice: a per-thread run-time test would leave predicated
+// update instructions in every launch, FP64 ones in the FP64 case, whose
+// throughput on this GPU is a small fraction of FP32's; kernels that may
+// update pick one of the two instances per block).
 template <class T, bool OUT>
 __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T *wy, const T *wz,
                                           int nx, int ny, int nz, int per, int row, int j, int k,
-                                          int qx, int colour, T omega, bool zero, double *pout)
+                                          int qx, int colour, T omega, bool zero, const OuterOut &po)
 {
     // cell indices fit in 32 bits: a grid has fewer than 2^31 cells
     const int sy = nx, sz = nx * ny;
@@ -172,8 +219,8 @@ __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T
     out.v[3] = par ? v1 : xq.v[3];
     stq(x + c, out);
     if constexpr (OUT) {
-        pout[c0] += (double)v0;
-        pout[c0 + 2] += (double)v1;
+        const T vv[4] = {v0, v0, v1, v1};
+        add_outer_quad<T>(po, c, vv, par ? 0xA : 0x5);
     }
 }
 
@@ -345,10 +392,11 @@ __device__ __forceinline__ void lin_x(const T *__restrict__ er, int Im, int I0, 
 }
 
 // x += P e_c on the aligned quad (4 qx .. 4 qx + 3, j, k) of row `row`: same
-// rounding order as prolong_at.  OUT: also p += x in FP64 (see half_quad).
+// rounding order as prolong_at.  OUT: also add x to the outer iterate (see
+// half_quad).
 template <class T, bool OUT>
 __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j, int k, int qx,
-                                             double *__restrict__ pout)
+                                             const OuterOut &po)
 {
     const int nx = L.n[0], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
     const T *__restrict__ ec = (const T *)L.xc;
@@ -367,9 +415,9 @@ __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j,
 #pragma unroll
     for (int u = 0; u < 4; u++) {
         xq.v[u] += lin(lin(a00[u], a10[u]), lin(a01[u], a11[u]));
-        if constexpr (OUT) pout[c + u] += (double)xq.v[u];
     }
     stq(x + c, xq);
+    if constexpr (OUT) add_outer_quad<T>(po, c, xq.v, 0xF);
 }
 
 // Flux-conserving x += P e_c on the aligned quad (4 qx .. 4 qx + 3, j, k): the
@@ -377,7 +425,7 @@ __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j,
 // rows (J0 or its partner, K0 or its partner).
 template <class T, bool OUT>
 __device__ __forceinline__ void prolong_quad_flux(const LevelView &L, int row, int j, int k, int qx,
-                                                  double *__restrict__ pout)
+                                                  const OuterOut &po)
 {
     const int nx = L.n[0], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
     const T *__restrict__ ec = (const T *)L.xc;
@@ -413,9 +461,9 @@ __device__ __forceinline__ void prolong_quad_flux(const LevelView &L, int row, i
             a[q] = av[r][m];
         }
         xq.v[u] += flux_corner_mean(e, a);
-        if constexpr (OUT) pout[c + u] += (double)xq.v[u];
     }
     stq(x + c, xq);
+    if constexpr (OUT) add_outer_quad<T>(po, c, xq.v, 0xF);
 }
 
 // x += P e_c on the 2 x 2 fine rows (2J + dy, 2K + dz) above coarse row (J, K),

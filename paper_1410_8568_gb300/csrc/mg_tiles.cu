@@ -17,7 +17,7 @@ namespace gbmg {
 // threads touch consecutive 16-byte vectors.
 template <class T, int B, int Q, bool OUT>
 __device__ __forceinline__ void half_flat_body(const LevelView &L, int lb, int colour, T omega, bool zero,
-                                               double *pout)
+                                               const OuterOut &po)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], nq = nx >> 2;
     const int items = nq * ny * nz;
@@ -29,7 +29,7 @@ __device__ __forceinline__ void half_flat_body(const LevelView &L, int lb, int c
         const int k = fdiv(row, L.dy);
         half_quad<T, OUT>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
                           (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
-                          omega, zero, pout);
+                          omega, zero, po);
     }
 }
 
@@ -47,11 +47,11 @@ __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ l
     const bool zero = flags & kZeroGuess;
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
-            half_flat_body<T, B, Q, true>(L, lb, colour, omega, zero, ov[L.g].p);
+            half_flat_body<T, B, Q, true>(L, lb, colour, omega, zero, outer_out(ov[L.g]));
             return;
         }
     }
-    half_flat_body<T, B, Q, false>(L, lb, colour, omega, zero, nullptr);
+    half_flat_body<T, B, Q, false>(L, lb, colour, omega, zero, OuterOut{});
 }
 
 template <class T, int B, int Q>

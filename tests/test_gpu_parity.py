@@ -507,3 +507,46 @@ def test_adaptive_cycles_per_step(precision):
     assert res[1].iters <= res[0].iters
     print("fixed %d cycles / %d steps, adaptive %d cycles / %d steps" %
           (res[0].iters, res[0].steps, res[1].iters, res[1].steps))
+
+
+@pytest.mark.parametrize("precision", [gbmg.MIXED, gbmg.FP64])
+def test_scaled_rhs_and_offset_iterate(precision):
+    """The outer iteration is invariant to the scale of the problem and to a
+    constant in the iterate.  A right-hand side scaled by 2^+-100 gives the
+    scaled solution bit for bit (the mixed-precision outer iteration works on
+    a power-of-two scaled copy); a scale of 1e-30 or 1e30 gives the scaled
+    solution to the spec accuracy; a warm start carrying a constant
+    converges to the same zero-mean solution: 1e4 times the solution's size
+    for the three-float iterate of the mixed-precision outer iteration, 10
+    times for the FP64 iterate (each FP64 update rounds at 2^-53 of the
+    constant, which at 1e4 leaves a residual near 1e-9 of the right-hand side)."""
+    P = I.config2(48)
+    f = oracle.faces_from_density(P.shape, P.bc, P.rho)
+    pstar = exact_solution("cfg2_dropfilm_48", P, f)
+    with solver_for(P, f, precision=precision) as S:
+        b = dev(P.rhs)
+        p = torch.zeros_like(b)
+        st = S.solve(b, p, tol=TOL)
+        assert st.status == gbmg.OK
+        for m in (-100, 100):
+            s = math.ldexp(1.0, m)
+            ps = torch.zeros_like(b)
+            sts = S.solve(b * s, ps, tol=TOL)
+            assert sts.status == gbmg.OK and sts.iters == st.iters
+            assert torch.equal(ps, p * s)
+        for s in (1e-30, 1e30):
+            ps = torch.zeros_like(b)
+            sts = S.solve(b * s, ps, tol=TOL)
+            assert sts.status == gbmg.OK and sts.rel_res <= TOL
+            err = np.linalg.norm(host(ps) / s - pstar) / np.linalg.norm(pstar)
+            assert err <= ERR, (s, err)
+        c = (1e4 if precision == gbmg.MIXED else 10.0) * np.abs(pstar).max()
+        po = torch.full_like(b, c)
+        sto = S.solve(b, po, tol=TOL)
+        assert sto.status == gbmg.OK
+        x = host(po)
+        bp = P.rhs - P.rhs.mean()
+        rel = np.linalg.norm(oracle.residual(P.shape, P.bc, f, bp, x)) / np.linalg.norm(bp)
+        err = np.linalg.norm(x - pstar) / np.linalg.norm(pstar)
+        print("offset warm start: iters=%d rel_res=%.2e (oracle %.2e) err=%.2e" % (sto.iters, sto.rel_res, rel, err))
+        assert rel <= 1.05 * TOL and err <= ERR
