@@ -478,9 +478,9 @@ Prof::~Prof()
 // from a zero correction (the first red half-sweep takes x = 0).  The finest
 // level starts from zero in the first cycle of a step and from the previous
 // cycle's correction in the next ones.  outer: in the grid's last cycle of the
-// step, the last red and black half-sweeps on the finest level also add the
-// correction to the FP64 iterate (the prolongation does if nu2 = 0, the coarse
-// solve if the grid has one level).
+// step, the last black half-sweep on the finest level also adds the correction
+// (both colours) to the outer iterate (the prolongation does if nu2 = 0, the
+// coarse solve if the grid has one level).
 template <class T>
 static void vcycle(Plan &P, Prof &pf, int cyc, bool outer)
 {
@@ -525,9 +525,10 @@ static void vcycle(Plan &P, Prof &pf, int cyc, bool outer)
         launch_prolong<T>(at(P.down[l]), (top && q.nu2 == 0) ? P.ov : nullptr, s);
         pf.end(s);
         for (int it = 0; it < q.nu2; it++) {
+            // the last black half-sweep adds both colours' final values
             const int fl = (top && it == q.nu2 - 1) ? kHalfOuter : 0;
             pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 0, q.omega, fl, P.ov, s);
+            launch_half<T>(H, 0, q.omega, 0, nullptr, s);
             pf.end(s);
             pf.begin(s, MG_K_SMOOTH, l);
             launch_half<T>(H, 1, q.omega, fl, P.ov, s);

@@ -124,9 +124,10 @@ struct LoadPlain {
 //
 // flags: kZeroGuess  (red launch) the iterate is zero on entry: red cells get
 //                    omega * (-b / d), black cells 0, so no clearing pass;
-//        kOuter      (finest level, last post-smoothing sweep of a cycle) a grid
+//        kOuter      (finest level, last black half-sweep of a cycle) a grid
 //                    whose refinement step ends with this cycle also adds the
-//                    relaxed cells' final values to its FP64 iterate.
+//                    final values of every cell (both colours) to its outer
+//                    iterate.
 // cyc: index of the V-cycle within its refinement step (in_cycle).
 template <class T, bool OUT>
 __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour, T omega, bool zero,
@@ -149,6 +150,9 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
             const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
             if (i >= nx || ((i + t.j + t.k) & 1) != colour) {
                 if (zero && i < nx) x[(long long)nx * t.row + i] = T(0);
+                // the other colour's final value (the launch leaves it as it is)
+                if constexpr (OUT)
+                    if (i < nx) add_outer<T>(po, (int)((long long)nx * t.row + i), x[(long long)nx * t.row + i]);
                 continue;
             }
             const long long c = (long long)nx * t.row + i;
@@ -681,29 +685,49 @@ __global__ void __launch_bounds__(1024) k_coarse_setup(const CoarseView *__restr
 // and coarse faces
 // ---------------------------------------------------------------------------
 
+// 1 / x in FP64 by Newton-Raphson iteration on f(y) = 1/y - x, y <- y + y (1 - x y),
+// from the FP32 reciprocal of x (relative error about 2^-23).  Each step squares
+// the relative error and the last one rounds once, so two steps end within
+// about one ulp of the quotient (Markstein, IBM J. Res. Dev. 34, 1990).  FP64
+// division is a long instruction sequence on this GPU's slow FP64 pipe; the
+// Newton form is 4 fused multiply-adds.  Arguments outside the FP32 range
+// divide exactly.
+__device__ __forceinline__ double recip_nr(double x)
+{
+    const float xf = (float)x;
+    if (!(fabsf(xf) > 1e-37f && fabsf(xf) < 1e37f)) return 1.0 / x;
+    double y = (double)__frcp_rn(xf);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
 __global__ void __launch_bounds__(kThreads) k_faces_from_density(FaceArgs a)
 {
     const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const int i = c % a.n[0];
-        const int rest = c / a.n[0];
-        const int j = rest % a.n[1];
-        const int k = rest / a.n[1];
+        const int rest = fdiv(c, a.dx);
+        const int i = c - rest * a.n[0];
+        const int k = fdiv(rest, a.dy);
+        const int j = rest - k * a.n[1];
         const int q[3] = {i, j, k};
-        const long long stride[3] = {1, a.n[0], (long long)a.n[0] * a.n[1]};
+        const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
         const double rho_c = a.rho[c];
         bool ok = rho_c > 0.0 && isfinite(rho_c);
+        const double inv_c = a.mode == 0 ? 0.0 : recip_nr(rho_c);
+#pragma unroll
         for (int d = 0; d < 3; d++) {
             double v;
             if (q[d] == 0 && !(a.per >> d & 1)) {
                 v = 0.0;  // Neumann wall
             } else {
-                const long long l = q[d] > 0 ? c - stride[d] : c + stride[d] * (a.n[d] - 1);
+                const int l = q[d] > 0 ? c - stride[d] : c + stride[d] * (a.n[d] - 1);
                 const double rho_l = a.rho[l];
                 // Eqs. 11-12 with alpha = 1/rho: 2 a_l a_c / (a_l + a_c) = 2 / (rho_l + rho_c)
-                v = a.mode == 0 ? 2.0 / (rho_l + rho_c) : 0.5 * (1.0 / rho_l + 1.0 / rho_c);
+                v = a.mode == 0 ? (2.0 * a.scale[d]) * recip_nr(rho_l + rho_c)
+                                : (0.5 * a.scale[d]) * (recip_nr(rho_l) + inv_c);
             }
-            v *= a.scale[d];
             if (a.out64[d]) a.out64[d][c] = v;
             if (a.out32[d]) a.out32[d][c] = (float)v;
             if (a.out32lo[d]) a.out32lo[d][c] = (float)(v - (double)(float)v);
@@ -1398,7 +1422,10 @@ static int cells_grid(long long N)
 }
 void launch_faces_from_density(const FaceArgs &a, cudaStream_t s)
 {
-    k_faces_from_density<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+    FaceArgs b = a;
+    b.dx = make_fastdiv((unsigned)a.n[0]);
+    b.dy = make_fastdiv((unsigned)a.n[1]);
+    k_faces_from_density<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(b);
 }
 void launch_scale_faces(const FaceArgs &a, cudaStream_t s)
 {

@@ -35,6 +35,7 @@ struct FaceArgs {
     double *out64[3];
     float *out32[3];         // optional FP32 copy (round to nearest)
     float *out32lo[3];       // optional: out64 - out32 rounded to FP32 (float-pair faces)
+    FastDiv dx, dy;          // division by n[0], n[1] (set by the launcher)
     int *err;                // set to 1 on a non-positive / non-finite value
 };
 

@@ -148,11 +148,13 @@ __device__ __forceinline__ void add_outer_quad(const OuterOut &o, int c, const T
     }
 }
 
-// OUT: also add the relaxed values to the outer iterate (add_outer; a
-// compile-time choice: a per-thread run-time test would leave predicated
-// update instructions in every launch, FP64 ones in the FP64 case, whose
-// throughput on this GPU is a small fraction of FP32's; kernels that may
-// update pick one of the two instances per block).
+// OUT (the last black half-sweep of a cycle): also add the quad's final
+// values to the outer iterate, the relaxed cells and the other colour's cells,
+// which that half-sweep does not change (add_outer; a compile-time choice: a
+// per-thread run-time test would leave predicated update instructions in every
+// launch, FP64 ones in the FP64 case, whose throughput on this GPU is a small
+// fraction of FP32's; kernels that may update pick one of the two instances
+// per block).
 template <class T, bool OUT>
 __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T *wy, const T *wz,
                                           int nx, int ny, int nz, int per, int row, int j, int k,
@@ -218,10 +220,7 @@ __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T
     out.v[2] = par ? xq.v[2] : v1;
     out.v[3] = par ? v1 : xq.v[3];
     stq(x + c, out);
-    if constexpr (OUT) {
-        const T vv[4] = {v0, v0, v1, v1};
-        add_outer_quad<T>(po, c, vv, par ? 0xA : 0x5);
-    }
+    if constexpr (OUT) add_outer_quad<T>(po, c, out.v, 0xF);
 }
 
 // Coarse partner of fine index i along an axis of nc coarse cells: the coarse
