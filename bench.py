@@ -200,7 +200,8 @@ def level_shapes(shape):
     return out
 
 
-def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=True, pcg=False):
+def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=True, pcg=False,
+                   xp=False):
     """Kernels of one solve step: coefficient set-up, prologue, refinement (or CG) steps, epilogue.
     In FP32 cycles the levels of at most tail_cells cells (below the finest) run in one launch;
     with more than one V-cycle per refinement step each step starts with a step-control kernel."""
@@ -210,6 +211,8 @@ def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, 
     normal = lt if lt < L else L - 1
     setup = 1 + (L - 1) + 1            # faces from density, coarsening per level, coarsest inverse
     prologue = 6                       # begin, sum b, mean, residual, finalize, loop control
+    if not pcg:
+        prologue += 2 + (1 if xp else 0)  # b - mean b, its norm (+ float forms of b and p)
     cycle = normal * (2 * nu1 + 1 + 1 + 2 * nu2) + 1  # half-sweeps, restriction, prolongation; tail or coarsest
     if pcg:
         prologue += inner * cycle + 3  # first preconditioning: V-cycles, z and its sums, direction
@@ -587,18 +590,23 @@ def main():
         times = [a.elapsed_time(b) for a, b in ev]
         return times, st, p
 
+    # the headline (FP32 cycles in the FP64 outer iteration), the FP64 path, and
+    # the extended-precision outer iteration (multigrid iteration only)
+    modes = [("mixed", gbmg.MIXED, gbmg.OUTER_FP64), ("fp64", gbmg.FP64, gbmg.OUTER_FP64)]
+    if args.solver == "mg":
+        modes.append(("mixed_xp", gbmg.MIXED, gbmg.OUTER_XP))
     results = {}
     solvers = {}
-    for prec in (gbmg.MIXED, gbmg.FP64):
+    for key, prec, outer in modes:
         with torch.cuda.stream(stream):
-            solvers[prec] = gbmg.Solver(P.shape, P.bc, rho=rho, precision=prec, stream=stream,
-                                        prolongation=PROLONG[args.prolongation], solver=SOLVER[args.solver])
-        S = solvers[prec]
+            solvers[key] = gbmg.Solver(P.shape, P.bc, rho=rho, precision=prec, stream=stream, outer=outer,
+                                       prolongation=PROLONG[args.prolongation], solver=SOLVER[args.solver])
+        S = solvers[key]
         timed(S, args.warmup)
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks = ClockSampler(local_rank) if prec == gbmg.MIXED else None
+        clocks = ClockSampler(local_rank) if key == "mixed" else None
         if clocks:
             clocks.start()
         t0 = time.perf_counter()
@@ -609,11 +617,21 @@ def main():
             results["clocks"] = clocks.stop()
         tot = sum(times)
         tot = reduce_max(tot, dist)
-        results[prec] = dict(ms=tot / args.steps, value=job_value(world, args.steps, tot),
-                             p50=statistics.median(times), p99=float(np.percentile(times, 99)),
-                             iters=st.iters, gamma=st.gamma, rel_res=st.rel_res, wall=wall,
-                             levels=S.num_levels(), p=p, inner=S.resolved_params()["inner_cycles"],
-                             steps=st.steps)
+        results[key] = dict(ms=tot / args.steps, value=job_value(world, args.steps, tot),
+                            p50=statistics.median(times), p99=float(np.percentile(times, 99)),
+                            iters=st.iters, gamma=st.gamma, rel_res=st.rel_res, wall=wall,
+                            levels=S.num_levels(), p=p, inner=S.resolved_params()["inner_cycles"],
+                            steps=st.steps)
+        if key == "mixed_xp":
+            # its residual kernel, per-launch events
+            S.profile(True)
+            timed(S, 3)
+            n_x, ms_x = S.profile_read(gbmg.K_RESIDUAL, 0)
+            S.profile(False)
+            results[key]["residual_avg_launch_us"] = 1000.0 * ms_x / max(1, n_x)
+        if key != "mixed":
+            S.close()  # frees its hierarchy before the next one is built
+            del solvers[key]
 
     # error of each result against the FP64 oracle's converged solution (small grids only)
     errors = {}
@@ -621,12 +639,13 @@ def main():
         import oracle
         faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
         pstar = oracle.solve_exact(P.shape, P.bc, faces, P.rhs).x
-        for prec in (gbmg.MIXED, gbmg.FP64):
-            x = results[prec]["p"].cpu().numpy()
-            errors[prec] = float(np.linalg.norm(x - pstar) / np.linalg.norm(pstar))
+        for key in results:
+            if key != "clocks":
+                x = results[key]["p"].cpu().numpy()
+                errors[key] = float(np.linalg.norm(x - pstar) / np.linalg.norm(pstar))
 
     # end to end through the host entry point (pinned buffers, copies inside)
-    S = solvers[gbmg.MIXED]
+    S = solvers["mixed"]
     timed(S, 2, host=True)
     e2e_times, _, _ = timed(S, args.steps, host=True)
     e2e_tot = sum(e2e_times)
@@ -691,13 +710,13 @@ def main():
             # bounded sample: 2 oracle cycles, scaled by the GPU solve's cycle count
             t = time.perf_counter()
             r = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=2)
-            dt = (time.perf_counter() - t) * results[gbmg.FP64]["iters"] / 2.0
+            dt = (time.perf_counter() - t) * results["fp64"]["iters"] / 2.0
             cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
                    "sample": "2 FP64 oracle V(2,2) cycles of the workload, scaled to %d cycles per solve" %
-                             results[gbmg.FP64]["iters"]}
+                             results["fp64"]["iters"]}
 
     if rank == 0:
-        m, f = results[gbmg.MIXED], results[gbmg.FP64]
+        m, f = results["mixed"], results["fp64"]
         launches = args.steps * count_launches(P.shape, m["iters"], m["steps"], inner=m["inner"],
                                                pcg=args.solver == "pcg")
         line = {
@@ -715,11 +734,21 @@ def main():
             "p50_ms": m["p50"], "p99_ms": m["p99"],
             "iters": m["iters"], "steps": m["steps"], "inner_cycles": m["inner"], "gamma": m["gamma"],
             "rel_res": m["rel_res"],
-            "err_vs_oracle": errors.get(gbmg.MIXED),
+            "err_vs_oracle": errors.get("mixed"),
             "fp64": {"value": f["value"], "unit": "solves/s", "ms_per_step": f["ms"], "p50_ms": f["p50"],
                      "p99_ms": f["p99"], "iters": f["iters"], "steps": f["steps"], "inner_cycles": f["inner"], "gamma": f["gamma"], "rel_res": f["rel_res"],
-                     "err_vs_oracle": errors.get(gbmg.FP64)},
+                     "err_vs_oracle": errors.get("fp64")},
             "mixed_over_fp64": m["value"] / f["value"],
+            "mixed_xp": None if "mixed_xp" not in results else {
+                "precision": "FP32 V(2,2) cycles in the extended-precision outer iteration (three-float "
+                             "iterate, float-pair faces and b, error-free FP32 residual; FP64 only in "
+                             "the set-up and final conversion)",
+                "value": results["mixed_xp"]["value"], "unit": "solves/s", "ms_per_step": results["mixed_xp"]["ms"],
+                "p50_ms": results["mixed_xp"]["p50"], "p99_ms": results["mixed_xp"]["p99"],
+                "iters": results["mixed_xp"]["iters"], "steps": results["mixed_xp"]["steps"],
+                "rel_res": results["mixed_xp"]["rel_res"], "err_vs_oracle": errors.get("mixed_xp"),
+                "residual_avg_launch_us": results["mixed_xp"]["residual_avg_launch_us"],
+                "over_mixed": results["mixed_xp"]["value"] / m["value"]},
             "e2e": {"value": job_value(world, args.steps, e2e_tot), "unit": "solves/s",
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

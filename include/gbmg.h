@@ -99,6 +99,13 @@ extern "C" {
 
 #define MG_COARSE_AUTO 0  /* coarsest solve: dense inverse up to MG_MAX_COARSE cells, else GMRES */
 #define MG_COARSE_GMRES 1 /* coarsest solve: restarted GMRES whatever the size */
+/* outer iteration of the mixed-precision multigrid iteration (mg_params.outer) */
+#define MG_OUTER_FP64 0 /* FP64 residual and FP64 update p += e (Sec. 2.3 with FP32 V-cycles) */
+#define MG_OUTER_XP 1   /* the same steps in extended precision from FP32 arithmetic: p held as a
+                           sum of three floats (72 bits), b and the finest faces as float pairs,
+                           the residual by error-free transformations with exact face differences
+                           (about 2^-48 relative per term, FP64: 2^-53); FP64 only in the set-up
+                           of a solve and its final conversion.  Ignored for FP64 cycles and CG */
 #define MG_STATIC_MAX_CELLS 512 /* most cells of a grid solved by mg_coarse_solve_static */
 #define MG_MAX_LEVELS 16
 
@@ -121,8 +128,8 @@ typedef struct {
     int max_iters;     /* most V-cycles per solve */
     int precision;     /* MG_PREC_FP64 or MG_PREC_MIXED */
     int use_graph;     /* 1: run each solve as one CUDA-graph launch; 0: host-driven loop */
-    int inner_cycles;  /* V-cycles per FP64 refinement step (residual evaluation), >= 1;
-                          0 (default) = 3 in MIXED precision, 2 in FP64, 1 with MG_SOLVER_PCG */
+    int inner_cycles;  /* most V-cycles per FP64 refinement step (residual evaluation), >= 1;
+                          0 (default) = 6 in MIXED precision, 8 in FP64, 1 with MG_SOLVER_PCG */
     int solver;        /* MG_SOLVER_MG (default) or MG_SOLVER_PCG: FP64 conjugate gradients on -A,
                           each step preconditioned by inner_cycles V-cycles from zero (in the
                           V-cycle precision), the preconditioned residual projected to zero mean;
@@ -142,6 +149,7 @@ typedef struct {
                               V-cycles (1 .. inner_cycles) as the last step's measured reduction
                               rate predicts the tolerance needs, with a 10% margin on the rate;
                               0: always inner_cycles.  Either way a solve stops at max_iters cycles */
+    int outer;             /* MG_OUTER_FP64 (default) or MG_OUTER_XP */
 } mg_params;
 
 typedef struct {

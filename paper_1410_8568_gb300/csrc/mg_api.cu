@@ -92,6 +92,7 @@ int check_params(const mg_params *p)
     if (p->coarse_max_iters < 1 || p->coarse_max_iters > 100000) return MG_EINVAL;
     if (!(p->coarse_tol > 0.0 && p->coarse_tol < 1.0)) return MG_EINVAL;
     if (p->adaptive_cycles != 0 && p->adaptive_cycles != 1) return MG_EINVAL;
+    if (p->outer != MG_OUTER_FP64 && p->outer != MG_OUTER_XP) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -136,7 +137,7 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
     const size_t N0 = (size_t)g.nx * g.ny * g.nz;
     lay.b0 = c.take(N0 * 8);
     for (int v = 0; v < 4; v++) lay.pcg[v] = p.solver == MG_SOLVER_PCG ? c.take(N0 * 8) : 0;
-    lay.xp = mixed && p.solver == MG_SOLVER_MG;
+    lay.xp = mixed && p.solver == MG_SOLVER_MG && p.outer == MG_OUTER_XP;
     for (int v = 0; v < 3; v++) lay.xp3[v] = lay.xp ? c.take(N0 * 4) : 0;
     for (int v = 0; v < 2; v++) lay.xb[v] = lay.xp ? c.take(N0 * 4) : 0;
     for (int v = 0; v < 3; v++) lay.wlo[v] = lay.xp ? c.take(N0 * 4) : 0;
@@ -560,20 +561,22 @@ static void prologue(Plan &P, Prof &pf)
     launch_sum(P.ot, 0, s);
     launch_finalize(P.ot, 0, s);
     pf.end(s);
-    if (P.xp) {
-        // extended precision: b - mean b and its norm (FP64), the scale, the
-        // float forms of b and p, the starting residual in FP32 arithmetic
-        pf.begin(s, MG_K_OTHER, 0);
-        launch_xp_b0(P.ot, s);
-        launch_finalize(P.ot, 4, s);
-        launch_xp_prepare(P.ot, s);
-        pf.end(s);
-        pf.begin(s, MG_K_RESIDUAL, 0);
-        launch_residual_xp(P.ot, s);
-        pf.end(s);
-    } else {
+    if (P.prm.solver == MG_SOLVER_PCG) {
         pf.begin(s, MG_K_RESIDUAL, 0);
         launch_residual<T>(P.ot, 1, s);
+        pf.end(s);
+    } else {
+        // multigrid iteration: b - mean b and its norm (FP64) set the power-of-2
+        // scale the cycles work in; then the starting residual, FP64 or (extended
+        // precision) from the float forms of b and p
+        pf.begin(s, MG_K_OTHER, 0);
+        launch_center_rhs(P.ot, s);
+        launch_finalize(P.ot, 4, s);
+        if (P.xp) launch_xp_prepare(P.ot, s);
+        pf.end(s);
+        pf.begin(s, MG_K_RESIDUAL, 0);
+        if (P.xp) launch_residual_xp(P.ot, s);
+        else launch_residual<T>(P.ot, 0, s);
         pf.end(s);
     }
     pf.begin(s, MG_K_OTHER, 0);
@@ -962,11 +965,13 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
     if (params) prm = *params;
     rc = check_params(&prm);
     if (rc) return rc;
-    // V-cycles per FP64 residual: FP32 cycles are cheap next to the FP64
-    // residual pass (FP64 arithmetic is slow on this GPU), so mixed precision
-    // takes 3; FP64 cycles cost as much as the pass, 2 balances them
+    // most V-cycles per FP64 residual: the residual pass is bound by the FP64
+    // pipe, slow on this GPU, so fewer passes pay; the adaptive step length
+    // trims the steps that need fewer cycles.  FP32 cycles stop gaining within a
+    // step near a 1e-5 reduction (their rounding), about 6 cycles at the rates
+    // of the drop/film fields; FP64 cycles have no such limit
     if (prm.inner_cycles == 0)
-        prm.inner_cycles = prm.solver == MG_SOLVER_PCG ? 1 : prm.precision == MG_PREC_MIXED ? 3 : 2;
+        prm.inner_cycles = prm.solver == MG_SOLVER_PCG ? 1 : prm.precision == MG_PREC_MIXED ? 6 : 8;
     Layout lay;
     rc = plan_layout(*grid, prm, lay);
     if (rc) return rc;
@@ -1101,6 +1106,7 @@ int mg_params_default(mg_params *p)
     p->coarse_max_iters = 300;
     p->coarse_tol = 1e-8;
     p->adaptive_cycles = 1;
+    p->outer = MG_OUTER_FP64;
     return MG_OK;
 }
 

@@ -43,7 +43,8 @@ struct GridState {
     double alpha;   //   step length
     double beta;    //   direction update
     double zmean;   //   mean of the preconditioned residual
-    double xscale;  // extended-precision outer iteration: internal iterate = p * xscale (a power of 2)
+    double xscale;  // multigrid iteration: the cycles see r * xscale, a power of 2 near 1 / rms(b - mean b)
+    double xinv;    //   1 / xscale
 };
 
 // A grid takes part in V-cycle `cyc` (0-based) of the current refinement step
@@ -176,12 +177,14 @@ struct OuterView {
 struct OuterOut {
     double *p;
     float *t[3];
+    double inv;  // FP64 iterate: p += e * inv (the cycles work in the scaled units)
 };
 __device__ __forceinline__ OuterOut outer_out(const OuterView &O)
 {
     OuterOut o;
     o.p = O.p;
     for (int q = 0; q < 3; q++) o.t[q] = O.xp3[q];
+    o.inv = O.st->xinv;
     return o;
 }
 

@@ -891,6 +891,7 @@ __global__ void k_begin(const OuterView *__restrict__ ov)
     s->cycles_next = O.inner < O.max_iters ? O.inner : O.max_iters;
     s->steps = 0;
     s->xscale = 1.0;
+    s->xinv = 1.0;
     s->rprev = 0.0;
 }
 
@@ -947,7 +948,7 @@ __device__ __forceinline__ void split3(double v, float &h, float &m, float &z)
 }
 
 // b0 = b - mean(b) in FP64 and the partial sums of ||b0||^2 (slot 2).
-__global__ void __launch_bounds__(kThreads) k_xp_b0(const OuterView *__restrict__ ov,
+__global__ void __launch_bounds__(kThreads) k_center_rhs(const OuterView *__restrict__ ov,
                                                     const int *__restrict__ start, int count)
 {
     const int e = find_entry(start, count);
@@ -1156,11 +1157,12 @@ __global__ void __launch_bounds__(kThreads) k_residual_xp(const OuterView *__res
 #undef XP_FACE
 
 // Outer residual r = (b - mean b) - A p in FP64, handed to the V-cycle in its
-// precision Te.  init = 1 (start of a solve): also stores b0 = b - mean(b) and
-// the partial sums of ||b0||^2 (slot 2), all FP64.  ||r||^2 goes to slot 0; in
-// the refinement steps it is accumulated from the rounded r handed to the
-// cycle (a norm only steers the stopping test, so its own rounding at 1e-7
-// relative is immaterial).
+// precision Te, scaled by xscale (a power of 2; 1 for CG).  init = 1 (start of
+// a CG solve): also stores b0 = b - mean(b) and the partial sums of ||b0||^2
+// (slot 2), all FP64.  ||r||^2 goes to slot 0; after the first CG residual it
+// is accumulated from the rounded, scaled r handed to the cycle (a norm only
+// steers the stopping test, so its own rounding at 1e-7 relative is
+// immaterial, and the scale keeps FP32 squares inside the FP32 range).
 template <class Te>
 __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restrict__ ov,
                                                        const int *__restrict__ start, int count,
@@ -1174,7 +1176,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
     const int ntiles = fine_blocks(O.n);
     const int nx = O.n[0];
     Te *r = (Te *)O.r;
-    const double m = s->bmean;
+    const double m = s->bmean, sc = s->xscale;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     Te racc = Te(0);
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
@@ -1195,7 +1197,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
                 bc = O.b0[c];
             }
             const double rc = bc - f;
-            const Te rt = (Te)rc;
+            const Te rt = (Te)(rc * sc);
             r[c] = rt;
             if (O.r64) O.r64[c] = rc;  // conjugate gradients keep the FP64 residual
             if (init) v[0] += rc * rc;
@@ -1214,7 +1216,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
 // One block per grid: sum the block partials in a fixed order and update the
 // state.  mode 0: mean of b.  mode 1: after the starting residual.  mode 2:
 // after a cycle (counts it).  mode 3: mean of the final iterate.  mode 4
-// (extended precision): ||b - mean b|| and the internal scale.  Stopping
+// (multigrid iteration): ||b - mean b|| and the scale of the cycles.  Stopping
 // test: ||r|| <= tol ||b||; NaN/Inf residual = diverged; max_iters reached =
 // not converged.
 __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restrict__ ov, int mode)
@@ -1245,13 +1247,14 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
         int k = (rms > 0.0 && isfinite(rms)) ? ilogb(rms) : 0;
         k = k < -100 ? -100 : (k > 100 ? 100 : k);
         s->xscale = ldexp(1.0, -k);
+        s->xinv = ldexp(1.0, k);
         return;
     }
-    // extended precision: the partials are of the scaled residual
-    const double rn = O.xp ? sqrt(out[0]) / s->xscale : sqrt(out[0]);
+    // the partials are of the scaled residual (xscale = 1 for CG)
+    const double rn = sqrt(out[0]) * s->xinv;
     int done = 0;
     if (mode == 1) {
-        if (!O.xp) s->bnorm = sqrt(out[2]);
+        if (O.r64) s->bnorm = sqrt(out[2]);  // CG: the starting residual kernel also reduced b
         s->r0 = rn;
     } else {
         done = s->cycles_next;
@@ -1457,9 +1460,9 @@ void launch_residual(const OuterTable &ot, int init, cudaStream_t s)
 {
     k_residual<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, init);
 }
-void launch_xp_b0(const OuterTable &ot, cudaStream_t s)
+void launch_center_rhs(const OuterTable &ot, cudaStream_t s)
 {
-    k_xp_b0<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    k_center_rhs<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
 }
 void launch_xp_prepare(const OuterTable &ot, cudaStream_t s)
 {

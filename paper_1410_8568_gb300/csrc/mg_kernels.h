@@ -112,9 +112,9 @@ void launch_project(const ProjArgs &, cudaStream_t);
 void launch_begin(const OuterView *, int count, cudaStream_t);
 void launch_sum(const OuterTable &, int which, cudaStream_t);
 template <class Te> void launch_residual(const OuterTable &, int init, cudaStream_t);
-// extended-precision outer iteration (mixed-precision multigrid iteration):
-// b - mean b and its norm; the scaled float forms of b and p; the residual
-void launch_xp_b0(const OuterTable &, cudaStream_t);
+// multigrid iteration: b - mean b and its norm (sets the cycles' scale);
+// extended-precision outer iteration: the scaled float forms of b and p, the residual
+void launch_center_rhs(const OuterTable &, cudaStream_t);
 void launch_xp_prepare(const OuterTable &, cudaStream_t);
 void launch_residual_xp(const OuterTable &, cudaStream_t);
 void launch_finalize(const OuterTable &, int mode, cudaStream_t);

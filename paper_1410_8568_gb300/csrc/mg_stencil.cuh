@@ -104,20 +104,23 @@ __device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn
 }
 
 // Add the final correction v of cell c of a refinement step to the outer
-// iterate: p += v in FP64 (FP64 cycles) or the exact three-float update
-// (FP32 cycles, mg_xprec.cuh).
+// iterate: p += v / xscale in FP64 (the scale a power of 2, so exact), or the
+// exact three-float update in the scaled units (FP32 cycles with the
+// extended-precision outer iteration, mg_xprec.cuh; o.t set).
 template <class T>
 __device__ __forceinline__ void add_outer(const OuterOut &o, int c, T v)
 {
-    if constexpr (sizeof(T) == 8) {
-        o.p[c] += v;
-    } else {
-        float a = o.t[0][c], m = o.t[1][c], z = o.t[2][c];
-        triple_add(a, m, z, v);
-        o.t[0][c] = a;
-        o.t[1][c] = m;
-        o.t[2][c] = z;
+    if constexpr (sizeof(T) == 4) {
+        if (o.t[0] != nullptr) {
+            float a = o.t[0][c], m = o.t[1][c], z = o.t[2][c];
+            triple_add(a, m, z, v);
+            o.t[0][c] = a;
+            o.t[1][c] = m;
+            o.t[2][c] = z;
+            return;
+        }
     }
+    o.p[c] += (double)v * o.inv;
 }
 
 // The same for the cells of an aligned quad at c (4 | c) selected by `sel`
@@ -125,10 +128,10 @@ __device__ __forceinline__ void add_outer(const OuterOut &o, int c, T v)
 template <class T>
 __device__ __forceinline__ void add_outer_quad(const OuterOut &o, int c, const T v[4], int sel)
 {
-    if constexpr (sizeof(T) == 8) {
+    if (sizeof(T) == 8 || o.t[0] == nullptr) {
 #pragma unroll
         for (int u = 0; u < 4; u++)
-            if (sel >> u & 1) o.p[c + u] += v[u];
+            if (sel >> u & 1) o.p[c + u] += (double)v[u] * o.inv;
     } else {
         float4 a = *(const float4 *)(o.t[0] + c), m = *(const float4 *)(o.t[1] + c),
                z = *(const float4 *)(o.t[2] + c);

@@ -29,6 +29,7 @@ TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
 PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
 SOLVER_MG, SOLVER_PCG = 0, 1
 COARSE_AUTO, COARSE_GMRES = 0, 1
+OUTER_FP64, OUTER_XP = 0, 1
 MAX_COARSE, MAX_COARSE_GMRES = 512, 32768
 TILE_HALF, TILE_RESTRICT, TILE_PROLONG = 0, 1, 2
 
@@ -50,7 +51,7 @@ class Params(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("solver", ctypes.c_int), ("prolongation", ctypes.c_int),
                 ("tiles", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_max_iters", ctypes.c_int),
-                ("coarse_tol", ctypes.c_double), ("adaptive_cycles", ctypes.c_int)]
+                ("coarse_tol", ctypes.c_double), ("adaptive_cycles", ctypes.c_int), ("outer", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -156,7 +157,7 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
 
 def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
                 inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
-                coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None) -> Params:
+                coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None, outer=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
@@ -179,6 +180,8 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
         p.coarse_max_iters = int(coarse_max_iters)
     if adaptive_cycles is not None:
         p.adaptive_cycles = int(adaptive_cycles)
+    if outer is not None:
+        p.outer = int(outer)
     return p
 
 
@@ -257,7 +260,7 @@ class Solver:
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
                  precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
                  inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
-                 coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None):
+                 coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None, outer=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -268,7 +271,7 @@ class Solver:
         self.grid = make_grid(self.shape, self.bc, self.length)
         self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles,
                                   prolongation, solver, coarse_solver, coarse_tol, coarse_max_iters,
-                                  adaptive_cycles)
+                                  adaptive_cycles, outer)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:
@@ -460,9 +463,9 @@ def coarse_solve_static(shape, bc, faces, r, e, length=(1.0, 1.0, 1.0), stream=N
                                         _ptr(e, n, d), _stream(stream))
 
 
-def memory_estimate(shape, bc, precision=MIXED, length=(1.0, 1.0, 1.0)) -> int:
+def memory_estimate(shape, bc, precision=MIXED, length=(1.0, 1.0, 1.0), outer=None) -> int:
     g = make_grid(shape, bc, length)
-    p = make_params(precision)
+    p = make_params(precision, outer=outer)
     v = ctypes.c_size_t()
     check(lib().mg_memory_estimate(ctypes.byref(g), ctypes.byref(p), ctypes.byref(v)), "mg_memory_estimate")
     return v.value
@@ -507,8 +510,9 @@ class Server:
     """Continuous-batching request loop (mg_server_*)."""
 
     def __init__(self, hbm_budget_bytes, max_slots=16, precision=MIXED, max_iters=100, stream=None,
-                 solver=None, prolongation=None):
-        self.params = make_params(precision, max_iters=max_iters, solver=solver, prolongation=prolongation)
+                 solver=None, prolongation=None, outer=None):
+        self.params = make_params(precision, max_iters=max_iters, solver=solver, prolongation=prolongation,
+                                  outer=outer)
         self._s = ctypes.c_void_p()
         st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
         check(lib().mg_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(self.params), st,

@@ -45,10 +45,16 @@ def test_host_only_calls():
     assert L.mg_params_default(ctypes.byref(p)) == 0
     assert (p.nu1, p.nu2, p.omega, p.precision, p.use_graph) == (2, 2, 1.0, gbmg.MIXED, 1)
     # mixed precision, multigrid iteration: about 58 B per finest cell for the
-    # levels and the FP64 outer iteration, plus 32 B for the extended-precision
-    # outer iteration (three-float iterate, float-pair b, low parts of the faces)
+    # levels and the FP64 outer iteration ...
     est = gbmg.memory_estimate((64, 64, 64), (1, 1, 0))
-    assert 64 ** 3 * 84 < est < 64 ** 3 * 100
+    assert 64 ** 3 * 52 < est < 64 ** 3 * 70
+    # ... plus 32 B for the extended-precision outer iteration (three-float
+    # iterate, float-pair b, low parts of the finest faces)
+    est_xp = gbmg.memory_estimate((64, 64, 64), (1, 1, 0), outer=gbmg.OUTER_XP)
+    assert est_xp - est == 64 ** 3 * 32
+    with pytest.raises(gbmg.MGError) as e:
+        gbmg.memory_estimate((64, 64, 64), (1, 1, 0), outer=2)
+    assert e.value.code == gbmg.EINVAL
     # FP64 cycles keep the FP64 outer iteration only
     est64 = gbmg.memory_estimate((64, 64, 64), (1, 1, 0), precision=gbmg.FP64)
     assert 64 ** 3 * 50 < est64 < 64 ** 3 * 70

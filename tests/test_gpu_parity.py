@@ -215,13 +215,19 @@ def exact_solution(name, P, faces):
     return _exact_cache[name]
 
 
-@pytest.mark.parametrize("precision", [gbmg.FP64, gbmg.MIXED])
+# (V-cycle precision, outer iteration): FP64 throughout; FP32 cycles in the FP64
+# outer iteration; FP32 cycles in the extended-precision outer iteration
+MODES = [(gbmg.FP64, gbmg.OUTER_FP64), (gbmg.MIXED, gbmg.OUTER_FP64), (gbmg.MIXED, gbmg.OUTER_XP)]
+MODE_IDS = ["fp64", "mixed", "mixed_xp"]
+
+
+@pytest.mark.parametrize("precision,outer", MODES, ids=MODE_IDS)
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
-def test_solve_matches_oracle(name, make, precision):
+def test_solve_matches_oracle(name, make, precision, outer):
     P = make()
     f = oracle.faces_from_density(P.shape, P.bc, P.rho)
     pstar = exact_solution(name, P, f)
-    with solver_for(P, f, precision=precision) as S:
+    with solver_for(P, f, precision=precision, outer=outer) as S:
         b = dev(P.rhs)
         p = torch.zeros_like(b)
         st = S.solve(b, p, tol=TOL)
@@ -255,17 +261,18 @@ def test_graph_and_host_loop_are_bitwise_equal():
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
 
 
-def test_batch_is_bitwise_equal_to_alone():
+@pytest.mark.parametrize("outer", [gbmg.OUTER_FP64, gbmg.OUTER_XP], ids=["fp64_outer", "xp_outer"])
+def test_batch_is_bitwise_equal_to_alone(outer):
     probs = I.config4_batch(6, edges=(32, 48, 64))
     faces = [oracle.faces_from_density(P.shape, P.bc, P.rho) for P in probs]
     alone = []
     for P, f in zip(probs, faces):
-        with solver_for(P, f) as S:
+        with solver_for(P, f, outer=outer) as S:
             p = torch.zeros(cells(P.shape), dtype=torch.float64, device="cuda")
             st = S.solve(dev(P.rhs), p, tol=TOL)
             assert st.status == gbmg.OK
             alone.append((p, st.iters))
-    solvers = [solver_for(P, f) for P, f in zip(probs, faces)]
+    solvers = [solver_for(P, f, outer=outer) for P, f in zip(probs, faces)]
     B = gbmg.Batch(solvers)
     rhs = [dev(P.rhs) for P in probs]
     ps = [torch.zeros_like(r) for r in rhs]
@@ -350,7 +357,7 @@ def test_profiling_counts_launches():
         # one FP64 residual per refinement step (at most inner_cycles V-cycles
         # each) plus the starting one
         inner = S.resolved_params()["inner_cycles"]
-        assert inner == 3  # the mixed-precision default
+        assert inner == 6  # the mixed-precision default
         n, ms = S.profile_read(gbmg.K_RESIDUAL, 0)
         assert st.steps >= -(-st.iters // inner)
         assert n == st.steps + 1 and ms > 0.0
@@ -365,15 +372,15 @@ def test_full_size_drop_film_128():
     f = oracle.faces_from_density(P.shape, P.bc, P.rho)
     pstar = oracle.solve_exact(P.shape, P.bc, f, P.rhs).x
     bp = P.rhs - P.rhs.mean()
-    for precision in (gbmg.MIXED, gbmg.FP64):
-        with solver_for(P, f, precision=precision) as S:
+    for (precision, outer), mid in zip(MODES, MODE_IDS):
+        with solver_for(P, f, precision=precision, outer=outer) as S:
             p = torch.zeros(cells(P.shape), dtype=torch.float64, device="cuda")
             st = S.solve(dev(P.rhs), p, tol=TOL)
             assert st.status == gbmg.OK
             x = host(p)
             rel = np.linalg.norm(oracle.residual(P.shape, P.bc, f, bp, x)) / np.linalg.norm(bp)
             err = np.linalg.norm(x - pstar) / np.linalg.norm(pstar)
-            print("128^3 drop/film prec=%d iters=%d gamma=%.3f rel=%.2e err=%.2e" % (precision, st.iters, st.gamma, rel, err))
+            print("128^3 drop/film %s iters=%d gamma=%.3f rel=%.2e err=%.2e" % (mid, st.iters, st.gamma, rel, err))
             assert rel <= 1.05 * TOL and err <= ERR
 
 
@@ -430,32 +437,34 @@ def test_full_size_layered_density_512():
     b = (mode[None] * dev(g)[:, None, None]).contiguous()
     del mode
     rho = dev(rho_z)[:, None, None].expand(n, n, n).contiguous()
-    with gbmg.Solver(shape, I.DROP_FILM_BC, rho=rho, precision=gbmg.MIXED) as S:
-        del rho
-        p = torch.zeros_like(b)
-        st = S.solve(b, p, tol=TOL)
-        assert st.status == gbmg.OK
-        err = (torch.linalg.vector_norm(p - p_exact) / torch.linalg.vector_norm(p_exact)).item()
-        print("layered 512^3 iters=%d gamma=%.3f err=%.2e" % (st.iters, st.gamma, err))
-        assert err <= ERR
+    for outer in (gbmg.OUTER_FP64, gbmg.OUTER_XP):
+        with gbmg.Solver(shape, I.DROP_FILM_BC, rho=rho, precision=gbmg.MIXED, outer=outer) as S:
+            p = torch.zeros_like(b)
+            st = S.solve(b, p, tol=TOL)
+            assert st.status == gbmg.OK
+            err = (torch.linalg.vector_norm(p - p_exact) / torch.linalg.vector_norm(p_exact)).item()
+            print("layered 512^3 outer=%d iters=%d gamma=%.3f err=%.2e" % (outer, st.iters, st.gamma, err))
+            assert err <= ERR
+            del p
 
 
 # ---------------------------------------------------------------------------
 # serving: continuous batching gives each request its solo result
 # ---------------------------------------------------------------------------
 
-def test_server_results_equal_alone():
+@pytest.mark.parametrize("outer", [gbmg.OUTER_FP64, gbmg.OUTER_XP], ids=["fp64_outer", "xp_outer"])
+def test_server_results_equal_alone(outer):
     import time
     probs = [I.config2(32), I.config1(48), I.config2(64), I.config1(32, ratio=10.0), I.config2(48), I.config1(64)]
     faces = [oracle.faces_from_density(P.shape, P.bc, P.rho) for P in probs]
     alone = []
     for P, f in zip(probs, faces):
-        with solver_for(P, f) as S:
+        with solver_for(P, f, outer=outer) as S:
             p = torch.zeros(cells(P.shape), dtype=torch.float64, device="cuda")
             st = S.solve(dev(P.rhs), p, tol=TOL)
             alone.append((p, st.iters))
     torch.cuda.synchronize()
-    srv = gbmg.Server(hbm_budget_bytes=256 << 20, max_slots=3)
+    srv = gbmg.Server(hbm_budget_bytes=256 << 20, max_slots=3, outer=outer)
     tickets, outs = [], []
     for q, (P, f) in enumerate(zip(probs, faces)):
         fd = [dev(a) for a in f]
@@ -509,21 +518,22 @@ def test_adaptive_cycles_per_step(precision):
           (res[0].iters, res[0].steps, res[1].iters, res[1].steps))
 
 
-@pytest.mark.parametrize("precision", [gbmg.MIXED, gbmg.FP64])
-def test_scaled_rhs_and_offset_iterate(precision):
+@pytest.mark.parametrize("precision,outer", MODES, ids=MODE_IDS)
+def test_scaled_rhs_and_offset_iterate(precision, outer):
     """The outer iteration is invariant to the scale of the problem and to a
     constant in the iterate.  A right-hand side scaled by 2^+-100 gives the
-    scaled solution bit for bit (the mixed-precision outer iteration works on
-    a power-of-two scaled copy); a scale of 1e-30 or 1e30 gives the scaled
-    solution to the spec accuracy; a warm start carrying a constant
-    converges to the same zero-mean solution: 1e4 times the solution's size
-    for the three-float iterate of the mixed-precision outer iteration, 10
-    times for the FP64 iterate (each FP64 update rounds at 2^-53 of the
-    constant, which at 1e4 leaves a residual near 1e-9 of the right-hand side)."""
+    scaled solution bit for bit (the multigrid iteration runs on a copy scaled
+    by a power of two taken from the right-hand side, so the FP32 cycles see
+    the same numbers); a scale of 1e-30 or 1e30 gives the scaled solution to
+    1e-8; a warm start carrying a constant converges to the same zero-mean
+    solution: 1e4 times the solution's size for the three-float iterate of the
+    extended-precision outer iteration, 10 times for the FP64 iterate (each
+    FP64 update rounds at 2^-53 of the constant, which at 1e4 leaves a residual
+    near 1e-9 of the right-hand side)."""
     P = I.config2(48)
     f = oracle.faces_from_density(P.shape, P.bc, P.rho)
     pstar = exact_solution("cfg2_dropfilm_48", P, f)
-    with solver_for(P, f, precision=precision) as S:
+    with solver_for(P, f, precision=precision, outer=outer) as S:
         b = dev(P.rhs)
         p = torch.zeros_like(b)
         st = S.solve(b, p, tol=TOL)
@@ -540,7 +550,7 @@ def test_scaled_rhs_and_offset_iterate(precision):
             assert sts.status == gbmg.OK and sts.rel_res <= TOL
             err = np.linalg.norm(host(ps) / s - pstar) / np.linalg.norm(pstar)
             assert err <= ERR, (s, err)
-        c = (1e4 if precision == gbmg.MIXED else 10.0) * np.abs(pstar).max()
+        c = (1e4 if outer == gbmg.OUTER_XP else 10.0) * np.abs(pstar).max()
         po = torch.full_like(b, c)
         sto = S.solve(b, po, tol=TOL)
         assert sto.status == gbmg.OK
