@@ -623,9 +623,17 @@ def main():
                             levels=S.num_levels(), p=p, inner=S.resolved_params()["inner_cycles"],
                             steps=st.steps)
         if key == "mixed_xp":
-            # its residual kernel, per-launch events
+            # its residual kernel, per-launch events (NVTX range for a profiler:
+            # ncu --nvtx --nvtx-include "profile_pass_xp/")
             S.profile(True)
+            try:
+                torch.cuda.nvtx.range_push("profile_pass_xp")
+                nvtx_xp = True
+            except (RuntimeError, AttributeError):
+                nvtx_xp = False
             timed(S, 3)
+            if nvtx_xp:
+                torch.cuda.nvtx.range_pop()
             n_x, ms_x = S.profile_read(gbmg.K_RESIDUAL, 0)
             S.profile(False)
             results[key]["residual_avg_launch_us"] = 1000.0 * ms_x / max(1, n_x)
