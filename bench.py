@@ -647,6 +647,7 @@ def main():
         import oracle
         faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
         pstar = oracle.solve_exact(P.shape, P.bc, faces, P.rhs).x
+        torch.cuda.synchronize()
         for key in results:
             if key != "clocks":
                 x = results[key]["p"].cpu().numpy()
