@@ -213,7 +213,9 @@ def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, 
     prologue = 6                       # begin, sum b, mean, residual, finalize, loop control
     if not pcg:
         prologue += 2 + (1 if xp else 0)  # b - mean b, its norm (+ float forms of b and p)
-    cycle = normal * (2 * nu1 + 1 + 1 + 2 * nu2) + 1  # half-sweeps, restriction, prolongation; tail or coarsest
+    # half-sweeps, restriction, prolongation per regular level (below the finest the
+    # restriction into a level does its zero-start red half-sweep); tail or coarsest
+    cycle = normal * (2 * nu1 + 1 + 1 + 2 * nu2) - (normal - 1) + 1
     if pcg:
         prologue += inner * cycle + 3  # first preconditioning: V-cycles, z and its sums, direction
         per_step = 4 + 3 + 1           # A d, alpha, update, test; z, beta, direction; loop control

@@ -302,6 +302,10 @@ int Plan::fill(mg_handle *const *handles, int count)
             v.g = g;
             v.st = h->state;
             v.ac = mixed ? (const void *)C.alpha32 : (const void *)C.alpha64;
+            // the next level has its own half-sweeps (neither a tail level nor
+            // the coarsest): its zero-start red half-sweep rides on this restriction
+            v.zr = (l + 1 < lt[g] && l + 2 < h->L) ? 1 : 0;
+            for (int d = 0; d < 3; d++) v.wc[d] = mixed ? (const void *)C.w32[d] : (const void *)C.w64[d];
             fill_fastdiv(v);
             sf.push_back(sf.back() + prolong_blocks_v(F.n, C.n, var[MG_TILE_PROLONG]));
             sc.push_back(sc.back() + restrict_blocks_v(F.n, C.n, var[MG_TILE_RESTRICT]));
@@ -476,7 +480,8 @@ Prof::~Prof()
 // V-cycle `cyc` (0-based) of a refinement step over every grid of the plan,
 // red-black half-sweeps in place; a grid whose step asks for at most cyc
 // cycles skips every launch of it (in_cycle).  Coarse levels start every cycle
-// from a zero correction (the first red half-sweep takes x = 0).  The finest
+// from a zero correction: their first red half-sweep, which reads only b and
+// the faces, is done by the restriction that produces b.  The finest
 // level starts from zero in the first cycle of a step and from the previous
 // cycle's correction in the next ones.  outer: in the grid's last cycle of the
 // step, the last black half-sweep on the finest level also adds the correction
@@ -496,15 +501,19 @@ static void vcycle(Plan &P, Prof &pf, int cyc, bool outer)
         if (H.count == 0) continue;
         const bool zero = !(l == 0 && cyc > 0);
         for (int it = 0; it < q.nu1; it++) {
-            pf.begin(s, MG_K_SMOOTH, l);
-            launch_half<T>(H, 0, q.omega, (it == 0 && zero) ? kHalfZero : 0, nullptr, s);
-            pf.end(s);
+            // below the finest level the restriction into this level already
+            // did the zero-start red half-sweep of every grid in this table
+            if (!(it == 0 && l > 0)) {
+                pf.begin(s, MG_K_SMOOTH, l);
+                launch_half<T>(H, 0, q.omega, (it == 0 && zero) ? kHalfZero : 0, nullptr, s);
+                pf.end(s);
+            }
             pf.begin(s, MG_K_SMOOTH, l);
             launch_half<T>(H, 1, q.omega, 0, nullptr, s);
             pf.end(s);
         }
         pf.begin(s, MG_K_RESTRICT, l);
-        launch_restrict<T>(at(P.rest[l]), s);
+        launch_restrict<T>(at(P.rest[l]), q.omega, s);
         pf.end(s);
     }
     if (P.ntv) {
@@ -1481,8 +1490,8 @@ int mg_restrict_residual(mg_handle *h, int level, int prec, const void *b, const
     Table tb;
     int rc = unit_view(h, level, prec, x, (void *)b, nullptr, coarse_b, &tb, kCoarseTiles);
     if (rc) return rc;
-    if (prec == MG_PREC_MIXED) launch_restrict<float>(tb, h->stream);
-    else launch_restrict<double>(tb, h->stream);
+    if (prec == MG_PREC_MIXED) launch_restrict<float>(tb, h->prm.omega, h->stream);
+    else launch_restrict<double>(tb, h->prm.omega, h->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return MG_OK;

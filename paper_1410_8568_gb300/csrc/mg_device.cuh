@@ -138,6 +138,10 @@ struct LevelView {
     // coarse cell pairs per coarse row nc[0]/2, coarse rows per plane nc[1]
     FastDiv dq, dy, dp, dcy;
     const void *ac;  // cell coefficients of the next coarser level (flux-conserving prolongation)
+    // restriction: also give the next coarser level its first (zero-start) red
+    // half-sweep, from the restricted right-hand side and that level's faces wc
+    int zr;
+    const void *wc[3];
 };
 
 // The finest level of one grid for the FP64 outer iteration.

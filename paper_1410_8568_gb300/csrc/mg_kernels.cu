@@ -223,7 +223,8 @@ int prolong_blocks(const int n[3]) { return half_blocks(n); }
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restrict__ lv,
-                                                       const int *__restrict__ start, int count, int cyc)
+                                                       const int *__restrict__ start, int count, int cyc,
+                                                       T omega)
 {
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
         if (crow >= ncy * ncz) return;
         const int P = (xt << 5) + (threadIdx.x & 31);
         if (P >= np) return;
-        restrict_pair<T>(L, crow, crow % ncy, crow / ncy, P);
+        restrict_pair<T>(L, crow, crow % ncy, crow / ncy, P, omega);
         return;
     }
     const int xt_n = coarse_xtiles(ncx);
@@ -267,7 +268,9 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
                 stencil(wx, wy, wz, LoadPlain<T>{x}, nx, ny, nz, L.per, i, j, k, c, x[c], d, f);
                 s += b[c] - f;
             }
-    ((T *)L.bc)[I + (long long)ncx * crow] = s * T(0.125);
+    const T bcv = s * T(0.125);
+    ((T *)L.bc)[I + (long long)ncx * crow] = bcv;
+    if (L.zr) ((T *)L.xc)[I + (long long)ncx * crow] = zero_start_red<T>(L, I, J, K, bcv, omega);
 }
 
 // Blocks of a restriction launch over the coarse level of `n`.
@@ -1376,9 +1379,9 @@ void launch_half_rows(const Table &tb, int colour, double omega, int flags, cons
                                                         nullptr);
 }
 template <class T>
-void launch_restrict_rows(const Table &tb, cudaStream_t s)
+void launch_restrict_rows(const Table &tb, double omega, cudaStream_t s)
 {
-    k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
+    k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega);
 }
 template <class T>
 void launch_prolong_rows(const Table &tb, const OuterView *ov, cudaStream_t s)
@@ -1483,8 +1486,8 @@ void launch_final(const OuterTable &ot, cudaStream_t s)
 
 template void launch_half_rows<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
 template void launch_half_rows<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
-template void launch_restrict_rows<float>(const Table &, cudaStream_t);
-template void launch_restrict_rows<double>(const Table &, cudaStream_t);
+template void launch_restrict_rows<float>(const Table &, double, cudaStream_t);
+template void launch_restrict_rows<double>(const Table &, double, cudaStream_t);
 template void launch_prolong_rows<float>(const Table &, const OuterView *, cudaStream_t);
 template void launch_prolong_rows<double>(const Table &, const OuterView *, cudaStream_t);
 template void launch_tail<float>(const TailView *, int, size_t, double, int, int, int, cudaStream_t);

@@ -87,12 +87,13 @@ int prolong_blocks_v(const int n[3], const int nc[3], int v);
 // (kHalfOuter; prolongation and coarse solve of the finest level), else null
 template <class T> void launch_half(const Table &, int colour, double omega, int flags,
                                     const OuterView *ov, cudaStream_t);
-template <class T> void launch_restrict(const Table &, cudaStream_t);
+// restriction; omega: the coarse level's zero-start red half-sweep where the view asks (zr)
+template <class T> void launch_restrict(const Table &, double omega, cudaStream_t);
 template <class T> void launch_prolong(const Table &, const OuterView *ov, cudaStream_t);
 // ... and the row-tiled kernels they fall back to (mg_kernels.cu)
 template <class T> void launch_half_rows(const Table &, int colour, double omega, int flags,
                                          const OuterView *ov, cudaStream_t);
-template <class T> void launch_restrict_rows(const Table &, cudaStream_t);
+template <class T> void launch_restrict_rows(const Table &, double omega, cudaStream_t);
 template <class T> void launch_prolong_rows(const Table &, const OuterView *ov, cudaStream_t);
 // V-cycle stages below the row-tiled levels; cyc as Table::cyc
 template <class T> void launch_tail(const TailView *, int count, size_t smem, double omega, int nu1,

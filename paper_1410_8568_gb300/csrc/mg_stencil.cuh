@@ -356,8 +356,33 @@ __device__ __forceinline__ Quad<T> residual_quad(const T *__restrict__ x, const 
 // Restriction for the coarse cell pair (2P, 2P+1) of coarse row `crow` = J + ncy K:
 // the residuals of the fine quad below it in each of the 4 fine rows
 // (2J + dy, 2K + dz), summed per coarse cell in a fixed order, times 1/8.
+// First red half-sweep of the coarse level from a zero correction, at coarse
+// cell (I, J, K) with right-hand side bc: red cells get omega * (-bc / d), d
+// the sum of the cell's face coefficients in the order every half-sweep uses
+// (x low, x high, y low, y high, z low, z high; absent high faces skipped),
+// black cells 0 -- the value the zero-start red half-sweep would write.
 template <class T>
-__device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int J, int K, int P)
+__device__ __forceinline__ T zero_start_red(const LevelView &L, int I, int J, int K, T bc, T omega)
+{
+    if (((I + J + K) & 1) != 0) return T(0);
+    const int nx = L.nc[0], ny = L.nc[1], nz = L.nc[2], per = L.per;
+    const int sy = nx, sz = nx * ny;
+    const int c = I + nx * (J + ny * K);
+    const T *wx = (const T *)L.wc[0], *wy = (const T *)L.wc[1], *wz = (const T *)L.wc[2];
+    T d = wx[c];
+    if (I + 1 < nx) d += wx[c + 1];
+    else if (per & 1) d += wx[c + 1 - nx];
+    d += wy[c];
+    if (J + 1 < ny) d += wy[c + sy];
+    else if (per & 2) d += wy[c - sy * (ny - 1)];
+    d += wz[c];
+    if (K + 1 < nz) d += wz[c + sz];
+    else if (per & 4) d += wz[c - sz * (nz - 1)];
+    return d > T(0) ? omega * relax_div(-bc, d) : T(0);
+}
+
+template <class T>
+__device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int J, int K, int P, T omega)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], ncx = L.nc[0];
     const T *x = (const T *)L.x;
@@ -376,8 +401,14 @@ __device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int 
             s1 += r.v[3];
         }
     T *bc = (T *)L.bc + ncx * crow + 2 * P;
-    bc[0] = s0 * T(0.125);
-    bc[1] = s1 * T(0.125);
+    const T b0 = s0 * T(0.125), b1 = s1 * T(0.125);
+    bc[0] = b0;
+    bc[1] = b1;
+    if (L.zr) {
+        T *xc = (T *)L.xc + ncx * crow + 2 * P;
+        xc[0] = zero_start_red<T>(L, 2 * P, J, K, b0, omega);
+        xc[1] = zero_start_red<T>(L, 2 * P + 1, J, K, b1, omega);
+    }
 }
 
 // Interpolation along x on one coarse row `er` for the 4 fine cells of the quad

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ l
 
 template <class T, int B, int Q>
 __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict__ lv,
-                                                     const int *__restrict__ start, int count, int cyc)
+                                                     const int *__restrict__ start, int count, int cyc,
+                                                     T omega)
 {
     const int e = find_entry(start, count);
     const LevelView &L = lv[e];
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict
         if (g >= items) return;
         const int crow = fdiv(g, L.dp);
         const int K = fdiv(crow, L.dcy);
-        restrict_pair<T>(L, crow, crow - K * ncy, K, g - crow * np);
+        restrict_pair<T>(L, crow, crow - K * ncy, K, g - crow * np, omega);
     }
 }
 
@@ -159,14 +160,14 @@ void launch_half(const Table &tb, int colour, double omega, int flags, const Out
 }
 
 template <class T>
-void launch_restrict(const Table &tb, cudaStream_t s)
+void launch_restrict(const Table &tb, double omega, cudaStream_t s)
 {
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
+        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega);
     });
-    if (!flat) launch_restrict_rows<T>(tb, s);
+    if (!flat) launch_restrict_rows<T>(tb, omega, s);
 }
 
 template <class T>
@@ -186,8 +187,8 @@ void launch_prolong(const Table &tb, const OuterView *ov, cudaStream_t s)
 
 template void launch_half<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);
 template void launch_half<double>(const Table &, int, double, int, const OuterView *, cudaStream_t);
-template void launch_restrict<float>(const Table &, cudaStream_t);
-template void launch_restrict<double>(const Table &, cudaStream_t);
+template void launch_restrict<float>(const Table &, double, cudaStream_t);
+template void launch_restrict<double>(const Table &, double, cudaStream_t);
 template void launch_prolong<float>(const Table &, const OuterView *, cudaStream_t);
 template void launch_prolong<double>(const Table &, const OuterView *, cudaStream_t);
 

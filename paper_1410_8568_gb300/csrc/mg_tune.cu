@@ -147,7 +147,7 @@ int time_shape(mg_handle *h, int kind, int l, int v, float *ms)
     TK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, s));
     Table tb{h->dview, h->dstart, 1, blocks, v};
     auto run = [&](int i) {
-        if (kind == MG_TILE_RESTRICT) launch_restrict<T>(tb, s);
+        if (kind == MG_TILE_RESTRICT) launch_restrict<T>(tb, 1.0, s);
         else if (kind == MG_TILE_PROLONG) launch_prolong<T>(tb, nullptr, s);
         else launch_half<T>(tb, i & 1, 1.0, 0, nullptr, s);
     };
