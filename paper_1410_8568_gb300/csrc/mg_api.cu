@@ -352,6 +352,7 @@ int Plan::fill(mg_handle *const *handles, int count)
             v.dx[t] = make_fastdiv((unsigned)Lv.n[0]);
             v.dhx[t] = make_fastdiv(Lv.n[0] >= 2 ? (unsigned)(Lv.n[0] >> 1) : 1u);
             v.dy[t] = make_fastdiv((unsigned)Lv.n[1]);
+            v.dq[t] = make_fastdiv(Lv.n[0] >= 4 ? (unsigned)(Lv.n[0] >> 2) : 1u);
             v.a[t] = mixed ? (const void *)Lv.alpha32 : (const void *)Lv.alpha64;
             off += (flux ? 6 : 5) * (int)Lv.N;
             off = (off + 3) & ~3;

@@ -228,6 +228,7 @@ struct TailView {
     const double *G;         // coarsest-level inverse
     const GridState *st;
     FastDiv dx[kMaxTail], dhx[kMaxTail], dy[kMaxTail];  // division by n[t][0], n[t][0] / 2, n[t][1]
+    FastDiv dq[kMaxTail];    // division by n[t][0] / 4 (quads per row)
     int flux;                // flux-conserving prolongation: level t >= 1 also holds its cell
     const void *a[kMaxTail]; //   coefficients (6th array of the level in shared memory)
 };

@@ -440,10 +440,54 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
     }
     __syncthreads();
 
-    auto half = [&](int t, int colour) {
+    // A tail level as a LevelView on shared memory, so that the per-quad
+    // functions of the per-level kernels (half_quad, restrict_pair,
+    // prolong_quad) run here unchanged on levels whose rows are a multiple of 4
+    // cells: one quad per thread at 16^3, 16-byte shared-memory loads, and the
+    // zero-start red half-sweep writes both colours (no clearing pass).  Other
+    // levels take one cell per thread.
+    auto view = [&](int t) {
+        LevelView L;
+        const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
+        for (int d = 0; d < 3; d++) {
+            L.n[d] = V.n[t][d];
+            L.w[d] = sm + V.off[t] + (2 + d) * N;
+            L.nc[d] = t + 1 < nt ? V.n[t + 1][d] : 1;
+        }
+        L.per = per;
+        L.x = sm + V.off[t];
+        L.b = sm + V.off[t] + N;
+        if (t + 1 < nt) {
+            const int NC = V.n[t + 1][0] * V.n[t + 1][1] * V.n[t + 1][2];
+            L.xc = sm + V.off[t + 1];
+            L.bc = sm + V.off[t + 1] + NC;
+            L.ac = sm + V.off[t + 1] + 5 * NC;
+        }
+        L.zr = 0;
+        return L;
+    };
+
+    // zero: the correction is zero on entry (first red half-sweep of a cycle)
+    auto half = [&](int t, int colour, bool zero) {
         const int nx = V.n[t][0], ny = V.n[t][1], nz = V.n[t][2], N = nx * ny * nz;
         T *x = sm + V.off[t];
         const T *b = x + N, *wx = x + 2 * N, *wy = x + 3 * N, *wz = x + 4 * N;
+        if ((nx & 3) == 0) {
+            const int nq = nx >> 2;
+            for (int q = threadIdx.x; q < (N >> 2); q += blockDim.x) {
+                const int row = fdiv(q, V.dq[t]);
+                const int k = fdiv(row, V.dy[t]);
+                half_quad<T, false>(x, b, wx, wy, wz, nx, ny, nz, per, row, row - k * ny, k, q - row * nq,
+                                    colour, omega, zero, OuterOut{});
+            }
+            __syncthreads();
+            return;
+        }
+        if (zero) {
+            // no cell of the level may be read before it is set
+            for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = T(0);
+            __syncthreads();
+        }
         const int hx = nx >> 1;
         for (int m = threadIdx.x; m < (N >> 1); m += blockDim.x) {
             // m-th cell of the colour: rows of hx cells, the colour's cells at
@@ -463,36 +507,39 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
 
     for (int t = 0; t + 1 < nt; t++) {
         for (int it = 0; it < nu1; it++) {
-            if (it == 0) {
-                // zero initial correction: no cell of the level may be read before it is set
-                const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
-                T *x = sm + V.off[t];
-                for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = T(0);
-                __syncthreads();
-            }
-            half(t, 0);
-            half(t, 1);
+            half(t, 0, it == 0);
+            half(t, 1, false);
         }
         // restriction of the residual to level t + 1
         const int nx = V.n[t][0], ny = V.n[t][1], nz = V.n[t][2], N = nx * ny * nz;
         const int ncx = V.n[t + 1][0], ncy = V.n[t + 1][1], NC = ncx * ncy * V.n[t + 1][2];
-        const T *x = sm + V.off[t];
-        const T *b = x + N, *wx = x + 2 * N, *wy = x + 3 * N, *wz = x + 4 * N;
-        T *bc = sm + V.off[t + 1] + NC;
-        for (int C = threadIdx.x; C < NC; C += blockDim.x) {
-            const int crow = fdiv(C, V.dx[t + 1]);
-            const int K = fdiv(crow, V.dy[t + 1]);
-            const int I = C - crow * ncx, J = crow - K * ncy;
-            T s = T(0);
-            for (int dz = 0; dz < 2; dz++)
-                for (int dy = 0; dy < 2; dy++)
-                    for (int dx = 0; dx < 2; dx++) {
-                        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-                        const int c = i + nx * (j + ny * k);
-                        T d;
-                        s += b[c] - smem_flux(x, wx, wy, wz, nx, ny, nz, per, i, j, k, c, x[c], d);
-                    }
-            bc[C] = s * T(0.125);
+        if ((nx & 3) == 0) {
+            const LevelView L = view(t);
+            const int np = ncx >> 1;
+            for (int g = threadIdx.x; g < (NC >> 1); g += blockDim.x) {
+                const int crow = fdiv(g, V.dq[t]);  // np = nx / 4
+                const int K = fdiv(crow, V.dy[t + 1]);
+                restrict_pair<T>(L, crow, crow - K * ncy, K, g - crow * np, omega);
+            }
+        } else {
+            const T *x = sm + V.off[t];
+            const T *b = x + N, *wx = x + 2 * N, *wy = x + 3 * N, *wz = x + 4 * N;
+            T *bc = sm + V.off[t + 1] + NC;
+            for (int C = threadIdx.x; C < NC; C += blockDim.x) {
+                const int crow = fdiv(C, V.dx[t + 1]);
+                const int K = fdiv(crow, V.dy[t + 1]);
+                const int I = C - crow * ncx, J = crow - K * ncy;
+                T s = T(0);
+                for (int dz = 0; dz < 2; dz++)
+                    for (int dy = 0; dy < 2; dy++)
+                        for (int dx = 0; dx < 2; dx++) {
+                            const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+                            const int c = i + nx * (j + ny * k);
+                            T d;
+                            s += b[c] - smem_flux(x, wx, wy, wz, nx, ny, nz, per, i, j, k, c, x[c], d);
+                        }
+                bc[C] = s * T(0.125);
+            }
         }
         __syncthreads();
     }
@@ -514,20 +561,31 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
     }
     for (int t = nt - 2; t >= 0; t--) {
         const int nx = V.n[t][0], ny = V.n[t][1], N = nx * ny * V.n[t][2];
-        const int nc[3] = {V.n[t + 1][0], V.n[t + 1][1], V.n[t + 1][2]};
-        T *x = sm + V.off[t];
-        const T *ec = sm + V.off[t + 1];
-        const T *ac = ec + 5 * (nc[0] * nc[1] * nc[2]);
-        for (int c = threadIdx.x; c < N; c += blockDim.x) {
-            const int row = fdiv(c, V.dx[t]);
-            const int k = fdiv(row, V.dy[t]);
-            x[c] += V.flux ? prolong_at_flux(ec, ac, nc, per, c - row * nx, row - k * ny, k)
-                           : prolong_at(ec, nc, per, c - row * nx, row - k * ny, k);
+        if ((nx & 3) == 0) {
+            const LevelView L = view(t);
+            const int nq = nx >> 2;
+            for (int q = threadIdx.x; q < (N >> 2); q += blockDim.x) {
+                const int row = fdiv(q, V.dq[t]);
+                const int k = fdiv(row, V.dy[t]);
+                if (V.flux) prolong_quad_flux<T, false>(L, row, row - k * ny, k, q - row * nq, OuterOut{});
+                else prolong_quad<T, false>(L, row, row - k * ny, k, q - row * nq, OuterOut{});
+            }
+        } else {
+            const int nc[3] = {V.n[t + 1][0], V.n[t + 1][1], V.n[t + 1][2]};
+            T *x = sm + V.off[t];
+            const T *ec = sm + V.off[t + 1];
+            const T *ac = ec + 5 * (nc[0] * nc[1] * nc[2]);
+            for (int c = threadIdx.x; c < N; c += blockDim.x) {
+                const int row = fdiv(c, V.dx[t]);
+                const int k = fdiv(row, V.dy[t]);
+                x[c] += V.flux ? prolong_at_flux(ec, ac, nc, per, c - row * nx, row - k * ny, k)
+                               : prolong_at(ec, nc, per, c - row * nx, row - k * ny, k);
+            }
         }
         __syncthreads();
         for (int it = 0; it < nu2; it++) {
-            half(t, 0);
-            half(t, 1);
+            half(t, 0, false);
+            half(t, 1, false);
         }
     }
     stage((T *)V.x0, sm + V.off[0], V.n[0][0] * V.n[0][1] * V.n[0][2]);
