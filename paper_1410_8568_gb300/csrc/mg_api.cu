@@ -361,6 +361,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.b0 = h->lev[lt[g]].b;
         v.G = h->G;
         v.st = h->state;
+        v.err = h->err + 2;
         tail_smem = std::max(tail_smem, (size_t)off * esz);
     }
     for (int g = 0; g < G; g++) {
@@ -834,11 +835,12 @@ int plan_sync_states(Plan &P)
     return MG_OK;
 }
 
-void fill_stats(const GridState &s, const int herr[2], double ms, mg_stats *o, int *status_out)
+void fill_stats(const GridState &s, const int herr[3], double ms, mg_stats *o, int *status_out)
 {
     int status = s.status;
     if (herr[0]) status = MG_EINVAL;
     else if (herr[1]) status = MG_ESINGULAR;
+    else if (herr[2]) status = MG_ETIMEOUT;  // a staging wait on the device gave up
     if (o) {
         o->iters = s.iters;
         o->status = status;
@@ -873,7 +875,7 @@ int run_plan(Plan &P, Prof &pf, const double *const *rhs, double *const *p, cons
     int first_bad = MG_OK;
     for (int g = 0; g < P.G; g++) {
         // coefficient problems found on the device by mg_set_faces / mg_set_density
-        int herr[2] = {0, 0};
+        int herr[3] = {0, 0, 0};
         cudaMemcpy(herr, P.hs[g]->err, sizeof(herr), cudaMemcpyDeviceToHost);
         int status;
         fill_stats(P.st_h[g], herr, ms, out ? &out[g] : nullptr, &status);
@@ -925,7 +927,7 @@ static int upload_faces(mg_handle *h)
 int gbmg::set_faces_impl(mg_handle *h, const double *ax, const double *ay, const double *az)
 {
     if (!ax || !ay || !az) return MG_EINVAL;
-    CK(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->err, 0, 3 * sizeof(int), h->stream));
     FaceArgs a;
     memset(&a, 0, sizeof(a));
     const double *in[3] = {ax, ay, az};
@@ -946,7 +948,7 @@ int gbmg::set_faces_impl(mg_handle *h, const double *ax, const double *ay, const
 static int set_density_impl(mg_handle *h, const double *rho, int mode)
 {
     if (!rho || (mode != MG_FACE_HARMONIC && mode != MG_FACE_ARITHMETIC)) return MG_EINVAL;
-    CK(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->err, 0, 3 * sizeof(int), h->stream));
     FaceArgs a;
     memset(&a, 0, sizeof(a));
     for (int d = 0; d < 3; d++) {
@@ -1153,7 +1155,7 @@ int mg_create(const mg_grid *grid, const double *ax, const double *ay, const dou
     if (rc) return rc;
     rc = set_faces_impl(h, ax, ay, az);
     if (rc == MG_OK) {
-        int herr[2] = {0, 0};
+        int herr[3] = {0, 0, 0};
         cudaError_t e = cudaStreamSynchronize(h->stream);
         if (e == cudaSuccess) e = cudaMemcpy(herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {

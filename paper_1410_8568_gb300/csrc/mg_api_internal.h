@@ -73,7 +73,7 @@ struct mg_handle {
     double *b0 = nullptr;      // right-hand side minus its mean (FP64)
     double *part = nullptr;    // reduction partials of the outer launches
     int nblk0 = 0;
-    int *err = nullptr;        // [0] bad coefficient, [1] singular coarsest grid
+    int *err = nullptr;        // [0] bad coefficient, [1] singular coarsest grid, [2] device wait gave up
     gbmg::GridState *state = nullptr;    // solve state of this grid (kept across plans)
     gbmg::GridState *dstate = nullptr;   // always-active state of the unit calls
     gbmg::LevelView *dview = nullptr;    // view slot of the unit calls
@@ -162,6 +162,6 @@ int kernel_blocks(int kind, const int n[3], const int nc[3], int v);
 // allocate a handle (no coefficients yet) / set its coefficients (async)
 int handle_alloc(const mg_grid *grid, const mg_params *params, void *stream, mg_handle **out);
 int set_faces_impl(mg_handle *h, const double *ax, const double *ay, const double *az);
-void fill_stats(const GridState &s, const int herr[2], double ms, mg_stats *o, int *status);
+void fill_stats(const GridState &s, const int herr[3], double ms, mg_stats *o, int *status);
 
 }  // namespace gbmg

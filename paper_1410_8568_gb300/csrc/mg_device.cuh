@@ -214,7 +214,7 @@ struct CoarseView {
 // Bottom of the V-cycle in one block per grid (levels of at most kTailCells
 // cells, shared memory resident).
 constexpr int kTailCells = 4096;
-constexpr int kTailThreads = 1024;
+constexpr int kTailThreads = 512;
 constexpr int kMaxTail = 8;
 
 struct TailView {
@@ -229,6 +229,7 @@ struct TailView {
     const GridState *st;
     FastDiv dx[kMaxTail], dhx[kMaxTail], dy[kMaxTail];  // division by n[t][0], n[t][0] / 2, n[t][1]
     FastDiv dq[kMaxTail];    // division by n[t][0] / 4 (quads per row)
+    int *err;                // set to 1 when the staging copies did not complete in time
     int flux;                // flux-conserving prolongation: level t >= 1 also holds its cell
     const void *a[kMaxTail]; //   coefficients (6th array of the level in shared memory)
 };

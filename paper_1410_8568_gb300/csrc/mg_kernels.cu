@@ -18,6 +18,7 @@
 #include "mg_kernels.h"
 #include "mg_stencil.cuh"
 #include "mg_outer.cuh"
+#include "mg_bulk.cuh"
 
 #include <math.h>
 
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
 
 // ---------------------------------------------------------------------------
 // The bottom of the V-cycle in one launch: every level of a grid with at most
-// kTailCells cells (and the coarsest solve) is processed by one block of 1024
+// kTailCells cells (and the coarsest solve) is processed by one block of kTailThreads
 // threads, all operands in shared memory, phases separated by block barriers.
 // These levels are too small to fill the GPU; as separate launches they cost
 // a launch latency each (10 per level per cycle) while doing almost no work.
@@ -419,15 +420,24 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
     if (!in_cycle(V.st, cyc)) return;
     const int nt = V.nt, per = V.per;
     // stage the faces of every tail level but the coarsest (solved with G) and
-    // the right-hand side of the first; levels above the coarsest have even
-    // sizes, so N % 8 == 0 and the slab offsets keep 16-byte alignment
-    for (int t = 0; t + 1 < nt; t++) {
-        const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
-        T *base = sm + V.off[t];
-        for (int d = 0; d < 3; d++) stage(base + (2 + d) * N, (const T *)V.w[t][d], N);
+    // the right-hand side of the first by bulk asynchronous copies, issued by
+    // one thread and completed on one mbarrier; levels above the coarsest have
+    // even sizes, so N % 8 == 0: sizes are multiples of 32 bytes and the slab
+    // offsets keep 16-byte alignment
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        const int N0 = V.n[0][0] * V.n[0][1] * V.n[0][2];
+        unsigned bytes = (unsigned)(N0 * sizeof(T));
+        for (int t = 0; t + 1 < nt; t++) bytes += 3u * (unsigned)(V.n[t][0] * V.n[t][1] * V.n[t][2] * sizeof(T));
+        mbar_arrive_expect_tx(&bar, bytes);
+        for (int t = 0; t + 1 < nt; t++) {
+            const int N = V.n[t][0] * V.n[t][1] * V.n[t][2];
+            T *base = sm + V.off[t];
+            for (int d = 0; d < 3; d++) bulk_g2s(base + (2 + d) * N, V.w[t][d], (unsigned)(N * sizeof(T)), &bar);
+        }
+        bulk_g2s(sm + V.off[0] + N0, V.b0, (unsigned)(N0 * sizeof(T)), &bar);
     }
-    stage(sm + V.off[0] + V.n[0][0] * V.n[0][1] * V.n[0][2], (const T *)V.b0,
-          V.n[0][0] * V.n[0][1] * V.n[0][2]);
     if (V.flux) {
         // cell coefficients of the tail's coarse levels (a small odd-sized
         // coarsest level rules out the vector copy)
@@ -438,7 +448,16 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
             for (int c = threadIdx.x; c < N; c += blockDim.x) d[c] = g[c];
         }
     }
-    __syncthreads();
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    // every thread waits (bounded); the outcome is made uniform over the block
+    const int staged = __syncthreads_and(mbar_wait(&bar, 0, kBulkWaitPolls) ? 1 : 0);
+    if (!staged) {
+        // give up on this grid (reported as MG_ETIMEOUT), but let the copies
+        // land before the block's shared memory is released
+        if (threadIdx.x == 0 && V.err) *V.err = 1;
+        mbar_wait(&bar, 0, kBulkWaitPolls);
+        return;
+    }
 
     // A tail level as a LevelView on shared memory, so that the per-quad
     // functions of the per-level kernels (half_quad, restrict_pair,

@@ -146,7 +146,7 @@ void mg_server::retire(std::vector<Request *> &finished)
     auto now = Clock::now();
     std::lock_guard<std::mutex> lk(mu);
     for (Request *r : finished) {
-        int herr[2] = {0, 0};
+        int herr[3] = {0, 0, 0};
         cudaMemcpy(herr, r->h->err, sizeof(herr), cudaMemcpyDeviceToHost);
         GridState s;
         cudaMemcpy(&s, r->h->state, sizeof(s), cudaMemcpyDeviceToHost);
