@@ -496,8 +496,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
             for (int q = threadIdx.x; q < (N >> 2); q += blockDim.x) {
                 const int row = fdiv(q, V.dq[t]);
                 const int k = fdiv(row, V.dy[t]);
-                half_quad<T, false>(x, b, wx, wy, wz, nx, ny, nz, per, row, row - k * ny, k, q - row * nq,
-                                    colour, omega, zero, OuterOut{});
+                half_quad_sm<T>(x, b, wx, wy, wz, nx, ny, nz, per, row, row - k * ny, k, q - row * nq, colour,
+                                omega, zero);
             }
             __syncthreads();
             return;

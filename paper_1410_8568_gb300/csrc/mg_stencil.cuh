@@ -226,6 +226,73 @@ __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T
     if constexpr (OUT) add_outer_quad<T>(po, c, out.v, 0xF);
 }
 
+// half_quad for operands in shared memory (the tail kernel): the same
+// relaxation with the same relax_cell inputs, so the same results, but every
+// operand of the two colour cells comes from a 16-byte quad load.  A warp's
+// scalar loads at a stride of one quad (4 words) hit 8 of the 32 banks: 4
+// wavefronts for 128 useful bytes, where a quad load carries 512.
+template <class T>
+__device__ __forceinline__ T colour_cell(const Quad<T> &q, int par, int second)
+{
+    return second ? (par ? q.v[3] : q.v[2]) : (par ? q.v[1] : q.v[0]);
+}
+
+template <class T>
+__device__ __forceinline__ void half_quad_sm(T *x, const T *b, const T *wx, const T *wy, const T *wz, int nx,
+                                             int ny, int nz, int per, int row, int j, int k, int qx, int colour,
+                                             T omega, bool zero)
+{
+    const int sy = nx, sz = nx * ny;
+    const int i0 = qx << 2;
+    const int c = row * nx + i0;
+    const int par = (colour + j + k) & 1;
+    const bool has_w = i0 > 0 || (per & 1), has_e = i0 + 4 < nx || (per & 1);
+    const int cw = i0 > 0 ? c - 1 : c + nx - 1;
+    const int ce = i0 + 4 < nx ? c + 4 : c + 4 - nx;
+    const bool has_n = j + 1 < ny || (per & 2), has_t = k + 1 < nz || (per & 4);
+    const bool has_s = j > 0 || (per & 2), has_b = k > 0 || (per & 4);
+    const int ds = j > 0 ? -sy : sy * (ny - 1);
+    const int dn = j + 1 < ny ? sy : -sy * (ny - 1);
+    const int db = k > 0 ? -sz : sz * (nz - 1);
+    const int dt = k + 1 < nz ? sz : -sz * (nz - 1);
+    const Quad<T> z4{{T(0), T(0), T(0), T(0)}};
+    const Quad<T> fx = ldq(wx + c);
+    const T fxe = has_e ? wx[ce] : T(0);
+    const Quad<T> bq = ldq(b + c);
+    const Quad<T> fsq = ldq(wy + c), fnq = has_n ? ldq(wy + c + dn) : z4;
+    const Quad<T> fbq = ldq(wz + c), ftq = has_t ? ldq(wz + c + dt) : z4;
+    Quad<T> xq = z4, xsq = z4, xnq = z4, xbq = z4, xtq = z4;
+    T xw = T(0), xe = T(0);
+    if (!zero) {
+        xq = ldq(x + c);
+        if (has_w) xw = x[cw];
+        if (has_e) xe = x[ce];
+        if (has_s) xsq = ldq(x + c + ds);
+        if (has_n) xnq = ldq(x + c + dn);
+        if (has_b) xbq = ldq(x + c + db);
+        if (has_t) xtq = ldq(x + c + dt);
+    }
+    const T xc0 = par ? xq.v[1] : xq.v[0], xc1 = par ? xq.v[3] : xq.v[2];
+    const T xl0 = par ? xq.v[0] : xw, xr0 = par ? xq.v[2] : xq.v[1];
+    const T xl1 = par ? xq.v[2] : xq.v[1], xr1 = par ? xe : xq.v[3];
+    const T fl0 = par ? fx.v[1] : fx.v[0], fr0 = par ? fx.v[2] : fx.v[1];
+    const T fl1 = par ? fx.v[3] : fx.v[2], fr1 = par ? fxe : fx.v[3];
+    const T v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, colour_cell(fsq, par, 0), colour_cell(fnq, par, 0),
+                            colour_cell(fbq, par, 0), colour_cell(ftq, par, 0), colour_cell(xsq, par, 0),
+                            colour_cell(xnq, par, 0), colour_cell(xbq, par, 0), colour_cell(xtq, par, 0),
+                            colour_cell(bq, par, 0), omega);
+    const T v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, colour_cell(fsq, par, 1), colour_cell(fnq, par, 1),
+                            colour_cell(fbq, par, 1), colour_cell(ftq, par, 1), colour_cell(xsq, par, 1),
+                            colour_cell(xnq, par, 1), colour_cell(xbq, par, 1), colour_cell(xtq, par, 1),
+                            colour_cell(bq, par, 1), omega);
+    Quad<T> out;
+    out.v[0] = par ? xq.v[0] : v0;
+    out.v[1] = par ? v0 : xq.v[1];
+    out.v[2] = par ? xq.v[2] : v1;
+    out.v[3] = par ? v1 : xq.v[3];
+    stq(x + c, out);
+}
+
 // Coarse partner of fine index i along an axis of nc coarse cells: the coarse
 // cell across the coarse face nearer to the fine centre.  It lies one step
 // outside [0, nc) at most: wrap on a periodic axis, else (wall) the cell itself.
