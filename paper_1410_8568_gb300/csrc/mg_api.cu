@@ -780,6 +780,7 @@ static int run_plan_t(Plan &P, Prof &pf, bool use_graph)
         CK(cudaEventRecord(P.e1, s));
     }
     CK(cudaGetLastError());
+    if (P.post_bytes) CK(cudaMemcpyAsync(P.post_dst, P.post_src, P.post_bytes, cudaMemcpyDeviceToHost, s));
     launch_gather_states(P.ot, P.st, s);
     CK(cudaMemcpyAsync(P.st_h, P.st, P.G * sizeof(GridState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1264,7 +1265,24 @@ static int ensure_host_buffers(mg_handle *h, bool rho)
     if (!h->io_rhs) CK(cudaMalloc((void **)&h->io_rhs, n));
     if (!h->io_p) CK(cudaMalloc((void **)&h->io_p, n));
     if (rho && !h->io_rho) CK(cudaMalloc((void **)&h->io_rho, n));
+    if (rho && !h->io_stream) CK(cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking));
+    if (rho && !h->io_ready) CK(cudaEventCreateWithFlags(&h->io_ready, cudaEventDisableTiming));
     return MG_OK;
+}
+
+// Solve on the staged io_rhs / io_p; the result goes back to p_host before the
+// solve's own synchronisation.
+static int solve_staged(mg_handle *h, double *p_host, double tol, mg_stats *st)
+{
+    Plan &P = *h->plan;
+    P.post_dst = p_host;
+    P.post_src = h->io_p;
+    P.post_bytes = (size_t)h->lev[0].N * sizeof(double);
+    const int rc = mg_solve(h, h->io_rhs, h->io_p, tol, st);
+    P.post_dst = nullptr;
+    P.post_src = nullptr;
+    P.post_bytes = 0;
+    return rc;
 }
 
 int mg_solve_host(mg_handle *h, const double *rhs_host, double *p_host, double tol, mg_stats *st)
@@ -1275,24 +1293,29 @@ int mg_solve_host(mg_handle *h, const double *rhs_host, double *p_host, double t
     const size_t n = (size_t)h->lev[0].N * sizeof(double);
     CK(cudaMemcpyAsync(h->io_rhs, rhs_host, n, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->io_p, p_host, n, cudaMemcpyHostToDevice, h->stream));
-    rc = mg_solve(h, h->io_rhs, h->io_p, tol, st);
-    if (rc != MG_OK && rc != MG_ENOTCONV && rc != MG_EDIVERGED) return rc;
-    CK(cudaMemcpyAsync(p_host, h->io_p, n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    return rc;
+    return solve_staged(h, p_host, tol, st);
 }
 
 int mg_step_host(mg_handle *h, const double *rho_host, int mode, const double *rhs_host,
                  double *p_host, double tol, mg_stats *st)
 {
-    if (!h || !rho_host) return MG_EINVAL;
+    if (!h || !rho_host || !rhs_host || !p_host) return MG_EINVAL;
     int rc = ensure_host_buffers(h, true);
     if (rc) return rc;
     const size_t n = (size_t)h->lev[0].N * sizeof(double);
+    // the density first; the right-hand side and the initial p on a side
+    // stream while the faces, coarse faces and coarsest inverse are built
     CK(cudaMemcpyAsync(h->io_rho, rho_host, n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->io_rhs, rhs_host, n, cudaMemcpyHostToDevice, h->io_stream));
+    CK(cudaMemcpyAsync(h->io_p, p_host, n, cudaMemcpyHostToDevice, h->io_stream));
+    CK(cudaEventRecord(h->io_ready, h->io_stream));
     rc = set_density_impl(h, h->io_rho, mode);
-    if (rc) return rc;
-    return mg_solve_host(h, rhs_host, p_host, tol, st);
+    if (rc) {
+        cudaStreamSynchronize(h->io_stream);
+        return rc;
+    }
+    CK(cudaStreamWaitEvent(h->stream, h->io_ready, 0));
+    return solve_staged(h, p_host, tol, st);
 }
 
 int mg_destroy(mg_handle *h)
@@ -1305,9 +1328,12 @@ int mg_destroy(mg_handle *h)
         h->plan->release();
         delete h->plan;
     }
+    if (h->io_stream) cudaStreamSynchronize(h->io_stream);
     if (h->io_rhs) cudaFree(h->io_rhs);
     if (h->io_p) cudaFree(h->io_p);
     if (h->io_rho) cudaFree(h->io_rho);
+    if (h->io_ready) cudaEventDestroy(h->io_ready);
+    if (h->io_stream) cudaStreamDestroy(h->io_stream);
     if (h->slab) cudaFree(h->slab);
     delete h;
     return MG_OK;

@@ -85,6 +85,8 @@ struct mg_handle {
     gbmg::Plan *plan = nullptr;          // single-grid launch plan
     gbmg::Prof prof;
     double *io_rhs = nullptr, *io_p = nullptr, *io_rho = nullptr;  // host-call staging
+    cudaStream_t io_stream = nullptr;  // host-call input copies that overlap the face set-up
+    cudaEvent_t io_ready = nullptr;
     signed char tile[3][MG_MAX_LEVELS] = {};  // launch shape per kernel (MG_TILE_*) and level
     double *pcg[4] = {nullptr, nullptr, nullptr, nullptr};  // CG: r, z, d, q (FP64, finest level)
     bool gmres = false;        // coarsest grid solved by GMRES (no dense inverse)
@@ -106,6 +108,11 @@ struct Plan {
     int Lmax = 0;
     bool mixed = true;
     bool xp = false;  // extended-precision outer iteration (every handle of a plan shares its params)
+    // optional device-to-host copy enqueued after the solve and before its final
+    // synchronisation (the host-buffer calls: one round trip instead of two)
+    void *post_dst = nullptr;
+    const void *post_src = nullptr;
+    size_t post_bytes = 0;
     mg_params prm;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
