@@ -320,6 +320,9 @@ int Plan::fill(mg_handle *const *handles, int count)
         down[l] = Table{d_lv + lv0, d_starts + sf0, cnt, sf.back(), var[MG_TILE_PROLONG], flux ? 1 : 0};
         rest[l] = Table{d_lv + lv0, d_starts + sc0, cnt, sc.back(), var[MG_TILE_RESTRICT]};
         half[l] = Table{d_lv + lv0, d_starts + sh0, cnt, sh.back(), var[MG_TILE_HALF]};
+        // a one-grid table also hands its view to the kernels by value (the
+        // host copy stays in the staging buffer, rewritten only by fill)
+        if (cnt == 1) down[l].hv = rest[l].hv = half[l].hv = lv + lv0;
     }
     const int so0 = nst;
     starts[nst++] = 0;

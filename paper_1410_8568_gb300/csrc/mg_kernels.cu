@@ -188,15 +188,10 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
 // MAYOUT: the launch carries kOuter; the test of the step's last cycle is
 // per grid, so uniform over a block, and picks one of two instances of the body.
 template <class T, bool MAYOUT>
-__global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
-                                                   const int *__restrict__ start, int count,
-                                                   int colour, T omega, int flags, int cyc,
-                                                   const OuterView *__restrict__ ov)
+__device__ __forceinline__ void half_entry(const LevelView &L, int lb, int colour, T omega, int flags, int cyc,
+                                           const OuterView *__restrict__ ov)
 {
-    const int e = find_entry(start, count);
-    const LevelView L = lv[e];
     if (!in_cycle(L.st, cyc)) return;
-    const int lb = blockIdx.x - start[e];
     const bool zero = flags & kZeroGuess;
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
@@ -205,6 +200,23 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
         }
     }
     half_body<T, false>(L, lb, colour, omega, zero, OuterOut{});
+}
+
+// single: a one-grid table, its view passed by value (`one`, parameter space):
+// no dependent load of the view before the grid's state and data.
+template <class T, bool MAYOUT>
+__global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__ lv,
+                                                   const int *__restrict__ start, int count,
+                                                   int colour, T omega, int flags, int cyc,
+                                                   const OuterView *__restrict__ ov,
+                                                   const __grid_constant__ LevelView one, int single)
+{
+    if (single) {
+        half_entry<T, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov);
+        return;
+    }
+    const int e = find_entry(start, count);
+    half_entry<T, MAYOUT>(lv[e], blockIdx.x - start[e], colour, omega, flags, cyc, ov);
 }
 
 // Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64
@@ -223,16 +235,11 @@ int prolong_blocks(const int n[3]) { return half_blocks(n); }
 // ---------------------------------------------------------------------------
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restrict__ lv,
-                                                       const int *__restrict__ start, int count, int cyc,
-                                                       T omega)
+__device__ __forceinline__ void restrict_entry(const LevelView &L, int lb, int cyc, T omega)
 {
-    const int e = find_entry(start, count);
-    const LevelView L = lv[e];
     if (!in_cycle(L.st, cyc)) return;
     const int ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2];
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int lb = blockIdx.x - start[e];
     const T *x = (const T *)L.x;
     const T *b = (const T *)L.b;
     const T *wx = (const T *)L.w[0], *wy = (const T *)L.w[1], *wz = (const T *)L.w[2];
@@ -272,6 +279,20 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
     const T bcv = s * T(0.125);
     ((T *)L.bc)[I + (long long)ncx * crow] = bcv;
     if (L.zr) ((T *)L.xc)[I + (long long)ncx * crow] = zero_start_red<T>(L, I, J, K, bcv, omega);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restrict__ lv,
+                                                       const int *__restrict__ start, int count, int cyc,
+                                                       T omega, const __grid_constant__ LevelView one,
+                                                       int single)
+{
+    if (single) {
+        restrict_entry<T>(one, blockIdx.x, cyc, omega);
+        return;
+    }
+    const int e = find_entry(start, count);
+    restrict_entry<T>(lv[e], blockIdx.x - start[e], cyc, omega);
 }
 
 // Blocks of a restriction launch over the coarse level of `n`.
@@ -322,14 +343,9 @@ __device__ __forceinline__ void prolong_body(const LevelView &L, int lb, const O
 }
 
 template <class T, bool FLUX, bool MAYOUT>
-__global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
-                                                      const int *__restrict__ start, int count, int cyc,
-                                                      const OuterView *__restrict__ ov)
+__device__ __forceinline__ void prolong_entry(const LevelView &L, int lb, int cyc, const OuterView *__restrict__ ov)
 {
-    const int e = find_entry(start, count);
-    const LevelView L = lv[e];
     if (!in_cycle(L.st, cyc)) return;
-    const int lb = blockIdx.x - start[e];
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
             prolong_body<T, FLUX, true>(L, lb, outer_out(ov[L.g]));
@@ -337,6 +353,20 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
         }
     }
     prolong_body<T, FLUX, false>(L, lb, OuterOut{});
+}
+
+template <class T, bool FLUX, bool MAYOUT>
+__global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restrict__ lv,
+                                                      const int *__restrict__ start, int count, int cyc,
+                                                      const OuterView *__restrict__ ov,
+                                                      const __grid_constant__ LevelView one, int single)
+{
+    if (single) {
+        prolong_entry<T, FLUX, MAYOUT>(one, blockIdx.x, cyc, ov);
+        return;
+    }
+    const int e = find_entry(start, count);
+    prolong_entry<T, FLUX, MAYOUT>(lv[e], blockIdx.x - start[e], cyc, ov);
 }
 
 // ---------------------------------------------------------------------------
@@ -1450,26 +1480,31 @@ template <class T>
 void launch_half_rows(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
     if (flags & kOuter)
-        k_half<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc, ov);
+        k_half<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc, ov,
+                                                       table_view(tb), table_single(tb));
     else
         k_half<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc,
-                                                        nullptr);
+                                                        nullptr, table_view(tb), table_single(tb));
 }
 template <class T>
 void launch_restrict_rows(const Table &tb, double omega, cudaStream_t s)
 {
-    k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega);
+    k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega, table_view(tb),
+                                                 table_single(tb));
 }
 template <class T>
 void launch_prolong_rows(const Table &tb, const OuterView *ov, cudaStream_t s)
 {
     const int c = tb.cyc;
+    const LevelView one = table_view(tb);
+    const int single = table_single(tb);
     if (tb.flux) {
-        if (ov) k_prolong<T, true, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov);
-        else k_prolong<T, true, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr);
+        if (ov) k_prolong<T, true, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov, one, single);
+        else k_prolong<T, true, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr, one, single);
     } else {
-        if (ov) k_prolong<T, false, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov);
-        else k_prolong<T, false, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr);
+        if (ov) k_prolong<T, false, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov, one, single);
+        else k_prolong<T, false, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr, one,
+                                                                      single);
     }
 }
 template <class T>

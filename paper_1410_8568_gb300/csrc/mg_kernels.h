@@ -15,7 +15,12 @@ struct Table {
     int variant = 0;  // launch shape (tile_shape); 0 = row tiles
     int flux = 0;     // prolongation tables: flux-conserving (row tiles only)
     int cyc = 0;      // V-cycle of the refinement step: grids asking fewer cycles skip the launch
+    const LevelView *hv = nullptr;  // host copy of the view of a one-grid table: passed by value
 };
+
+// the by-value view of a one-grid table (kernel parameter space), else zeros
+inline int table_single(const Table &tb) { return (tb.hv != nullptr && tb.count == 1) ? 1 : 0; }
+inline LevelView table_view(const Table &tb) { return table_single(tb) ? *tb.hv : LevelView{}; }
 
 struct OuterTable {
     const OuterView *ov;

@@ -35,15 +35,10 @@ __device__ __forceinline__ void half_flat_body(const LevelView &L, int lb, int c
 
 // MAYOUT: the launch carries kOuter (see k_half)
 template <class T, int B, int Q, bool MAYOUT>
-__global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ lv,
-                                                 const int *__restrict__ start, int count,
-                                                 int colour, T omega, int flags, int cyc,
-                                                 const OuterView *__restrict__ ov)
+__device__ __forceinline__ void half_flat_entry(const LevelView &L, int lb, int colour, T omega, int flags,
+                                                int cyc, const OuterView *__restrict__ ov)
 {
-    const int e = find_entry(start, count);
-    const LevelView &L = lv[e];
     if (!in_cycle(L.st, cyc)) return;
-    const int lb = blockIdx.x - start[e];
     const bool zero = flags & kZeroGuess;
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
@@ -54,17 +49,28 @@ __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ l
     half_flat_body<T, B, Q, false>(L, lb, colour, omega, zero, OuterOut{});
 }
 
-template <class T, int B, int Q>
-__global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict__ lv,
-                                                     const int *__restrict__ start, int count, int cyc,
-                                                     T omega)
+// single: a one-grid table, its view passed by value (see k_half)
+template <class T, int B, int Q, bool MAYOUT>
+__global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ lv,
+                                                 const int *__restrict__ start, int count,
+                                                 int colour, T omega, int flags, int cyc,
+                                                 const OuterView *__restrict__ ov,
+                                                 const __grid_constant__ LevelView one, int single)
 {
+    if (single) {
+        half_flat_entry<T, B, Q, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov);
+        return;
+    }
     const int e = find_entry(start, count);
-    const LevelView &L = lv[e];
+    half_flat_entry<T, B, Q, MAYOUT>(lv[e], blockIdx.x - start[e], colour, omega, flags, cyc, ov);
+}
+
+template <class T, int B, int Q>
+__device__ __forceinline__ void restrict_flat_entry(const LevelView &L, int lb, int cyc, T omega)
+{
     if (!in_cycle(L.st, cyc)) return;
     const int np = L.nc[0] >> 1, ncy = L.nc[1];
     const int items = np * ncy * L.nc[2];
-    const int lb = blockIdx.x - start[e];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
         const int g = (lb * Q + q) * B + (int)threadIdx.x;
@@ -76,16 +82,26 @@ __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict
 }
 
 template <class T, int B, int Q>
-__global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict__ lv,
-                                                    const int *__restrict__ start, int count, int cyc)
+__global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict__ lv,
+                                                     const int *__restrict__ start, int count, int cyc,
+                                                     T omega, const __grid_constant__ LevelView one,
+                                                     int single)
+{
+    if (single) {
+        restrict_flat_entry<T, B, Q>(one, blockIdx.x, cyc, omega);
+        return;
+    }
+    const int e = find_entry(start, count);
+    restrict_flat_entry<T, B, Q>(lv[e], blockIdx.x - start[e], cyc, omega);
+}
+
+template <class T, int B, int Q>
+__device__ __forceinline__ void prolong_flat_entry(const LevelView &L, int lb, int cyc)
 {
     // items: coarse cell pairs; each covers a quad of the 2 x 2 fine rows above it
-    const int e = find_entry(start, count);
-    const LevelView &L = lv[e];
     if (!in_cycle(L.st, cyc)) return;
     const int np = L.nc[0] >> 1, ncy = L.nc[1];
     const int items = np * ncy * L.nc[2];
-    const int lb = blockIdx.x - start[e];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
         const int g = (lb * Q + q) * B + (int)threadIdx.x;
@@ -94,6 +110,19 @@ __global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict_
         const int K = fdiv(crow, L.dcy);
         prolong_block<T>(L, crow - K * ncy, K, g - crow * np);
     }
+}
+
+template <class T, int B, int Q>
+__global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict__ lv,
+                                                    const int *__restrict__ start, int count, int cyc,
+                                                    const __grid_constant__ LevelView one, int single)
+{
+    if (single) {
+        prolong_flat_entry<T, B, Q>(one, blockIdx.x, cyc);
+        return;
+    }
+    const int e = find_entry(start, count);
+    prolong_flat_entry<T, B, Q>(lv[e], blockIdx.x - start[e], cyc);
 }
 
 namespace {
@@ -151,10 +180,12 @@ void launch_half(const Table &tb, int colour, double omega, int flags, const Out
         constexpr TileShape ts = tile_shape(decltype(V)::value);
         if (flags & kOuter)
             k_half_flat<T, ts.B, ts.Q, true><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
-                                                                        (T)omega, flags, tb.cyc, ov);
+                                                                        (T)omega, flags, tb.cyc, ov,
+                                                                        table_view(tb), table_single(tb));
         else
             k_half_flat<T, ts.B, ts.Q, false><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
-                                                                         (T)omega, flags, tb.cyc, nullptr);
+                                                                         (T)omega, flags, tb.cyc, nullptr,
+                                                                         table_view(tb), table_single(tb));
     });
     if (!flat) launch_half_rows<T>(tb, colour, omega, flags, ov, s);
 }
@@ -165,7 +196,8 @@ void launch_restrict(const Table &tb, double omega, cudaStream_t s)
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega);
+        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega,
+                                                                  table_view(tb), table_single(tb));
     });
     if (!flat) launch_restrict_rows<T>(tb, omega, s);
 }
@@ -180,7 +212,8 @@ void launch_prolong(const Table &tb, const OuterView *ov, cudaStream_t s)
     }
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_prolong_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc);
+        k_prolong_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, table_view(tb),
+                                                                 table_single(tb));
     });
     if (!flat) launch_prolong_rows<T>(tb, nullptr, s);
 }

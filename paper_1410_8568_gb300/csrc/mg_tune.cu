@@ -146,6 +146,7 @@ int time_shape(mg_handle *h, int kind, int l, int v, float *ms)
     TK(cudaMemcpyAsync(h->dview, &lv, sizeof(lv), cudaMemcpyHostToDevice, s));
     TK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, s));
     Table tb{h->dview, h->dstart, 1, blocks, v};
+    tb.hv = &lv;  // as the solves launch one-grid tables
     auto run = [&](int i) {
         if (kind == MG_TILE_RESTRICT) launch_restrict<T>(tb, 1.0, s);
         else if (kind == MG_TILE_PROLONG) launch_prolong<T>(tb, nullptr, s);
