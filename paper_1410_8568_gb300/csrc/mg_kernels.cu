@@ -132,7 +132,7 @@ struct LoadPlain {
 // cyc: index of the V-cycle within its refinement step (in_cycle).
 template <class T, bool OUT>
 __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour, T omega, bool zero,
-                                          const OuterOut &po)
+                                          const OuterOut &po, bool go = true)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], per = L.per;
     T *__restrict__ x = (T *)L.x;
@@ -149,6 +149,7 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+            if (!go) return;
             if (i >= nx || ((i + t.j + t.k) & 1) != colour) {
                 if (zero && i < nx) x[(long long)nx * t.row + i] = T(0);
                 // the other colour's final value (the launch leaves it as it is)
@@ -182,17 +183,24 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
     if (row >= ny * nz) return;
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
-    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, po);
+    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, po, go);
 }
 
 // MAYOUT: the launch carries kOuter; the test of the step's last cycle is
 // per grid, so uniform over a block, and picks one of two instances of the body.
+// defer (one-grid tables, whose launches the graph limits to the grid's own
+// cycles): the state's load overlaps the data's and only the stores wait for
+// it; with several grids a grid that sits the cycle out returns at once.
 template <class T, bool MAYOUT>
 __device__ __forceinline__ void half_entry(const LevelView &L, int lb, int colour, T omega, int flags, int cyc,
-                                           const OuterView *__restrict__ ov)
+                                           const OuterView *__restrict__ ov, bool defer)
 {
-    if (!in_cycle(L.st, cyc)) return;
     const bool zero = flags & kZeroGuess;
+    if (!MAYOUT && defer) {
+        half_body<T, false>(L, lb, colour, omega, zero, OuterOut{}, in_cycle(L.st, cyc));
+        return;
+    }
+    if (!in_cycle(L.st, cyc)) return;
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
             half_body<T, true>(L, lb, colour, omega, zero, outer_out(ov[L.g]));
@@ -212,11 +220,11 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
                                                    const __grid_constant__ LevelView one, int single)
 {
     if (single) {
-        half_entry<T, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov);
+        half_entry<T, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov, true);
         return;
     }
     const int e = find_entry(start, count);
-    half_entry<T, MAYOUT>(lv[e], blockIdx.x - start[e], colour, omega, flags, cyc, ov);
+    half_entry<T, MAYOUT>(lv[e], blockIdx.x - start[e], colour, omega, flags, cyc, ov, false);
 }
 
 // Blocks of a half-sweep launch over a level: row tiles of 32 quads (or 64

@@ -158,10 +158,13 @@ __device__ __forceinline__ void add_outer_quad(const OuterOut &o, int c, const T
 // launch, FP64 ones in the FP64 case, whose throughput on this GPU is a small
 // fraction of FP32's; kernels that may update pick one of the two instances
 // per block).
+// go: store the result (false: a grid that sits this cycle out; the loads are
+// issued before its state is known, so they overlap that load's latency).
 template <class T, bool OUT>
 __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T *wy, const T *wz,
                                           int nx, int ny, int nz, int per, int row, int j, int k,
-                                          int qx, int colour, T omega, bool zero, const OuterOut &po)
+                                          int qx, int colour, T omega, bool zero, const OuterOut &po,
+                                          bool go = true)
 {
     // cell indices fit in 32 bits: a grid has fewer than 2^31 cells
     const int sy = nx, sz = nx * ny;
@@ -222,6 +225,7 @@ __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T
     out.v[1] = par ? v0 : xq.v[1];
     out.v[2] = par ? xq.v[2] : v1;
     out.v[3] = par ? v1 : xq.v[3];
+    if (!go) return;
     stq(x + c, out);
     if constexpr (OUT) add_outer_quad<T>(po, c, out.v, 0xF);
 }

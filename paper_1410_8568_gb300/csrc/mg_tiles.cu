@@ -17,7 +17,7 @@ namespace gbmg {
 // threads touch consecutive 16-byte vectors.
 template <class T, int B, int Q, bool OUT>
 __device__ __forceinline__ void half_flat_body(const LevelView &L, int lb, int colour, T omega, bool zero,
-                                               const OuterOut &po)
+                                               const OuterOut &po, bool go = true)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], nq = nx >> 2;
     const int items = nq * ny * nz;
@@ -29,17 +29,22 @@ __device__ __forceinline__ void half_flat_body(const LevelView &L, int lb, int c
         const int k = fdiv(row, L.dy);
         half_quad<T, OUT>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
                           (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
-                          omega, zero, po);
+                          omega, zero, po, go);
     }
 }
 
 // MAYOUT: the launch carries kOuter (see k_half)
+// defer: see half_entry
 template <class T, int B, int Q, bool MAYOUT>
 __device__ __forceinline__ void half_flat_entry(const LevelView &L, int lb, int colour, T omega, int flags,
-                                                int cyc, const OuterView *__restrict__ ov)
+                                                int cyc, const OuterView *__restrict__ ov, bool defer)
 {
-    if (!in_cycle(L.st, cyc)) return;
     const bool zero = flags & kZeroGuess;
+    if (!MAYOUT && defer) {
+        half_flat_body<T, B, Q, false>(L, lb, colour, omega, zero, OuterOut{}, in_cycle(L.st, cyc));
+        return;
+    }
+    if (!in_cycle(L.st, cyc)) return;
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
             half_flat_body<T, B, Q, true>(L, lb, colour, omega, zero, outer_out(ov[L.g]));
@@ -58,11 +63,11 @@ __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ l
                                                  const __grid_constant__ LevelView one, int single)
 {
     if (single) {
-        half_flat_entry<T, B, Q, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov);
+        half_flat_entry<T, B, Q, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov, true);
         return;
     }
     const int e = find_entry(start, count);
-    half_flat_entry<T, B, Q, MAYOUT>(lv[e], blockIdx.x - start[e], colour, omega, flags, cyc, ov);
+    half_flat_entry<T, B, Q, MAYOUT>(lv[e], blockIdx.x - start[e], colour, omega, flags, cyc, ov, false);
 }
 
 template <class T, int B, int Q>
