@@ -242,10 +242,12 @@ int prolong_blocks(const int n[3]) { return half_blocks(n); }
 // (3) residual and restriction: coarse b = mean of (b - A x) over 8 children
 // ---------------------------------------------------------------------------
 
+// defer: see half_entry
 template <class T>
-__device__ __forceinline__ void restrict_entry(const LevelView &L, int lb, int cyc, T omega)
+__device__ __forceinline__ void restrict_entry(const LevelView &L, int lb, int cyc, T omega, bool defer)
 {
-    if (!in_cycle(L.st, cyc)) return;
+    const bool go = in_cycle(L.st, cyc);
+    if (!defer && !go) return;
     const int ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2];
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const T *x = (const T *)L.x;
@@ -261,9 +263,10 @@ __device__ __forceinline__ void restrict_entry(const LevelView &L, int lb, int c
         if (crow >= ncy * ncz) return;
         const int P = (xt << 5) + (threadIdx.x & 31);
         if (P >= np) return;
-        restrict_pair<T>(L, crow, crow % ncy, crow / ncy, P, omega);
+        restrict_pair<T>(L, crow, crow % ncy, crow / ncy, P, omega, go);
         return;
     }
+    if (!go) return;
     const int xt_n = coarse_xtiles(ncx);
     const int xt = lb % xt_n, rb = lb / xt_n;
     const int crow = rb * kRowsPerBlock + (threadIdx.x >> 5);
@@ -296,11 +299,11 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
                                                        int single)
 {
     if (single) {
-        restrict_entry<T>(one, blockIdx.x, cyc, omega);
+        restrict_entry<T>(one, blockIdx.x, cyc, omega, true);
         return;
     }
     const int e = find_entry(start, count);
-    restrict_entry<T>(lv[e], blockIdx.x - start[e], cyc, omega);
+    restrict_entry<T>(lv[e], blockIdx.x - start[e], cyc, omega, false);
 }
 
 // Blocks of a restriction launch over the coarse level of `n`.
@@ -319,7 +322,7 @@ int restrict_blocks(const int n[3], const int nc[3])
 // ---------------------------------------------------------------------------
 
 template <class T, bool FLUX, bool OUT>
-__device__ __forceinline__ void prolong_body(const LevelView &L, int lb, const OuterOut &po)
+__device__ __forceinline__ void prolong_body(const LevelView &L, int lb, const OuterOut &po, bool go = true)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const T *ec = (const T *)L.xc;
@@ -332,10 +335,15 @@ __device__ __forceinline__ void prolong_body(const LevelView &L, int lb, const O
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
-        if constexpr (FLUX) prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, po);
-        else prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, po);
+        if constexpr (FLUX) {
+            if (!go) return;
+            prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, po);
+        } else {
+            prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, po, go);
+        }
         return;
     }
+    if (!go) return;
     const Tile t = fine_tile(L.n, lb);
     if (!t.ok) return;
 #pragma unroll
@@ -350,9 +358,15 @@ __device__ __forceinline__ void prolong_body(const LevelView &L, int lb, const O
     }
 }
 
+// defer: see half_entry
 template <class T, bool FLUX, bool MAYOUT>
-__device__ __forceinline__ void prolong_entry(const LevelView &L, int lb, int cyc, const OuterView *__restrict__ ov)
+__device__ __forceinline__ void prolong_entry(const LevelView &L, int lb, int cyc, const OuterView *__restrict__ ov,
+                                              bool defer)
 {
+    if (!MAYOUT && defer) {
+        prolong_body<T, FLUX, false>(L, lb, OuterOut{}, in_cycle(L.st, cyc));
+        return;
+    }
     if (!in_cycle(L.st, cyc)) return;
     if constexpr (MAYOUT) {
         if (last_cycle(L.st, cyc)) {
@@ -370,11 +384,11 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
                                                       const __grid_constant__ LevelView one, int single)
 {
     if (single) {
-        prolong_entry<T, FLUX, MAYOUT>(one, blockIdx.x, cyc, ov);
+        prolong_entry<T, FLUX, MAYOUT>(one, blockIdx.x, cyc, ov, true);
         return;
     }
     const int e = find_entry(start, count);
-    prolong_entry<T, FLUX, MAYOUT>(lv[e], blockIdx.x - start[e], cyc, ov);
+    prolong_entry<T, FLUX, MAYOUT>(lv[e], blockIdx.x - start[e], cyc, ov, false);
 }
 
 // ---------------------------------------------------------------------------

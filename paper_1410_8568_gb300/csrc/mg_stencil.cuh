@@ -453,7 +453,8 @@ __device__ __forceinline__ T zero_start_red(const LevelView &L, int I, int J, in
 }
 
 template <class T>
-__device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int J, int K, int P, T omega)
+__device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int J, int K, int P, T omega,
+                                              bool go = true)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2], ncx = L.nc[0];
     const T *x = (const T *)L.x;
@@ -473,6 +474,7 @@ __device__ __forceinline__ void restrict_pair(const LevelView &L, int crow, int 
         }
     T *bc = (T *)L.bc + ncx * crow + 2 * P;
     const T b0 = s0 * T(0.125), b1 = s1 * T(0.125);
+    if (!go) return;  // (see half_quad)
     bc[0] = b0;
     bc[1] = b1;
     if (L.zr) {
@@ -500,7 +502,7 @@ __device__ __forceinline__ void lin_x(const T *__restrict__ er, int Im, int I0, 
 // half_quad).
 template <class T, bool OUT>
 __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j, int k, int qx,
-                                             const OuterOut &po)
+                                             const OuterOut &po, bool go = true)
 {
     const int nx = L.n[0], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
     const T *__restrict__ ec = (const T *)L.xc;
@@ -520,6 +522,7 @@ __device__ __forceinline__ void prolong_quad(const LevelView &L, int row, int j,
     for (int u = 0; u < 4; u++) {
         xq.v[u] += lin(lin(a00[u], a10[u]), lin(a01[u], a11[u]));
     }
+    if (!go) return;  // (see half_quad)
     stq(x + c, xq);
     if constexpr (OUT) add_outer_quad<T>(po, c, xq.v, 0xF);
 }
@@ -575,7 +578,7 @@ __device__ __forceinline__ void prolong_quad_flux(const LevelView &L, int row, i
 // coarse rows: they use J and its two partners Jm, Jp (and K, Km, Kp), 9 coarse
 // rows in all instead of 16.  Same rounding order as prolong_at.
 template <class T>
-__device__ __forceinline__ void prolong_block(const LevelView &L, int J, int K, int P)
+__device__ __forceinline__ void prolong_block(const LevelView &L, int J, int K, int P, bool go = true)
 {
     const int nx = L.n[0], ny = L.n[1], ncx = L.nc[0], ncy = L.nc[1], ncz = L.nc[2], per = L.per;
     const T *__restrict__ ec = (const T *)L.xc;
@@ -609,7 +612,7 @@ __device__ __forceinline__ void prolong_block(const LevelView &L, int J, int K, 
             for (int u = 0; u < 4; u++) {
                 xq.v[u] += lin(ey[1][dy][u], ey[dz ? 2 : 0][dy][u]);
             }
-            stq(x + c, xq);
+            if (go) stq(x + c, xq);
         }
 }
 

@@ -70,10 +70,12 @@ __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ l
     half_flat_entry<T, B, Q, MAYOUT>(lv[e], blockIdx.x - start[e], colour, omega, flags, cyc, ov, false);
 }
 
+// defer: see half_entry
 template <class T, int B, int Q>
-__device__ __forceinline__ void restrict_flat_entry(const LevelView &L, int lb, int cyc, T omega)
+__device__ __forceinline__ void restrict_flat_entry(const LevelView &L, int lb, int cyc, T omega, bool defer)
 {
-    if (!in_cycle(L.st, cyc)) return;
+    const bool go = in_cycle(L.st, cyc);
+    if (!defer && !go) return;
     const int np = L.nc[0] >> 1, ncy = L.nc[1];
     const int items = np * ncy * L.nc[2];
 #pragma unroll
@@ -82,7 +84,7 @@ __device__ __forceinline__ void restrict_flat_entry(const LevelView &L, int lb, 
         if (g >= items) return;
         const int crow = fdiv(g, L.dp);
         const int K = fdiv(crow, L.dcy);
-        restrict_pair<T>(L, crow, crow - K * ncy, K, g - crow * np, omega);
+        restrict_pair<T>(L, crow, crow - K * ncy, K, g - crow * np, omega, go);
     }
 }
 
@@ -93,18 +95,20 @@ __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict
                                                      int single)
 {
     if (single) {
-        restrict_flat_entry<T, B, Q>(one, blockIdx.x, cyc, omega);
+        restrict_flat_entry<T, B, Q>(one, blockIdx.x, cyc, omega, true);
         return;
     }
     const int e = find_entry(start, count);
-    restrict_flat_entry<T, B, Q>(lv[e], blockIdx.x - start[e], cyc, omega);
+    restrict_flat_entry<T, B, Q>(lv[e], blockIdx.x - start[e], cyc, omega, false);
 }
 
+// defer: see half_entry
 template <class T, int B, int Q>
-__device__ __forceinline__ void prolong_flat_entry(const LevelView &L, int lb, int cyc)
+__device__ __forceinline__ void prolong_flat_entry(const LevelView &L, int lb, int cyc, bool defer)
 {
     // items: coarse cell pairs; each covers a quad of the 2 x 2 fine rows above it
-    if (!in_cycle(L.st, cyc)) return;
+    const bool go = in_cycle(L.st, cyc);
+    if (!defer && !go) return;
     const int np = L.nc[0] >> 1, ncy = L.nc[1];
     const int items = np * ncy * L.nc[2];
 #pragma unroll
@@ -113,7 +117,7 @@ __device__ __forceinline__ void prolong_flat_entry(const LevelView &L, int lb, i
         if (g >= items) return;
         const int crow = fdiv(g, L.dp);
         const int K = fdiv(crow, L.dcy);
-        prolong_block<T>(L, crow - K * ncy, K, g - crow * np);
+        prolong_block<T>(L, crow - K * ncy, K, g - crow * np, go);
     }
 }
 
@@ -123,11 +127,11 @@ __global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict_
                                                     const __grid_constant__ LevelView one, int single)
 {
     if (single) {
-        prolong_flat_entry<T, B, Q>(one, blockIdx.x, cyc);
+        prolong_flat_entry<T, B, Q>(one, blockIdx.x, cyc, true);
         return;
     }
     const int e = find_entry(start, count);
-    prolong_flat_entry<T, B, Q>(lv[e], blockIdx.x - start[e], cyc);
+    prolong_flat_entry<T, B, Q>(lv[e], blockIdx.x - start[e], cyc, false);
 }
 
 namespace {
