@@ -111,7 +111,7 @@ def read_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mg_kernels.cu", "mg_tiles.cu", "mg_stencil.cuh", "mg_device.cuh"):
+    for f in ("mg_kernels.cu", "mg_tiles.cu", "mg_stencil.cuh", "mg_device.cuh", "mg_launch.cuh"):
         with open(os.path.join(ROOT, "paper_1410_8568_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

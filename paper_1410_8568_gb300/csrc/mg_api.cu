@@ -589,8 +589,8 @@ static void prologue(Plan &P, Prof &pf)
         if (P.xp) launch_xp_prepare(P.ot, s);
         pf.end(s);
         pf.begin(s, MG_K_RESIDUAL, 0);
-        if (P.xp) launch_residual_xp(P.ot, s);
-        else launch_residual<T>(P.ot, 0, s);
+        if (P.xp) launch_residual_xp(P.ot, 1, s);
+        else launch_residual<T>(P.ot, 2, s);
         pf.end(s);
     }
     pf.begin(s, MG_K_OTHER, 0);
@@ -638,7 +638,7 @@ static void body_residual(Plan &P, Prof &pf)
 {
     const cudaStream_t s = P.stream;
     pf.begin(s, MG_K_RESIDUAL, 0);
-    if (P.xp) launch_residual_xp(P.ot, s);
+    if (P.xp) launch_residual_xp(P.ot, 0, s);
     else launch_residual<T>(P.ot, 0, s);
     pf.end(s);
     pf.begin(s, MG_K_OTHER, 0);
@@ -756,10 +756,20 @@ template <class T>
 static int run_plan_t(Plan &P, Prof &pf, bool use_graph)
 {
     const cudaStream_t s = P.stream;
+    // per-launch event profiling times each kernel alone: plain launches there
+    DepScope dep(P.dep && !pf.on);
     CK(cudaMemcpyAsync(P.ov, P.ov_h, P.G * sizeof(OuterView), cudaMemcpyHostToDevice, s));
     if (use_graph && !pf.on) {
         if (!P.gexec) {
             int rc = build_graph<T>(P);
+            if (rc && P.dep) {
+                // the graph was not accepted with programmatic edges: rebuild it
+                // with plain launches
+                cudaGetLastError();
+                P.dep = 0;
+                DepScope plain(0);
+                rc = build_graph<T>(P);
+            }
             if (rc) return rc;
         }
         CK(cudaEventRecord(P.e0, s));
@@ -809,6 +819,7 @@ static Prof g_no_prof;
 
 int plan_prologue(Plan &P)
 {
+    DepScope dep(P.dep);
     if (P.mixed) prologue<float>(P, g_no_prof);
     else prologue<double>(P, g_no_prof);
     CK(cudaGetLastError());
@@ -817,6 +828,7 @@ int plan_prologue(Plan &P)
 
 int plan_body(Plan &P)
 {
+    DepScope dep(P.dep);
     const int c = step_cycles(P);
     if (P.mixed) body<float>(P, g_no_prof, c);
     else body<double>(P, g_no_prof, c);
@@ -826,6 +838,7 @@ int plan_body(Plan &P)
 
 int plan_final(Plan &P)
 {
+    DepScope dep(P.dep);
     epilogue(P, g_no_prof);
     CK(cudaGetLastError());
     return MG_OK;
@@ -930,6 +943,7 @@ static int upload_faces(mg_handle *h)
 
 int gbmg::set_faces_impl(mg_handle *h, const double *ax, const double *ay, const double *az)
 {
+    DepScope dep(dep_launch_default());
     if (!ax || !ay || !az) return MG_EINVAL;
     CK(cudaMemsetAsync(h->err, 0, 3 * sizeof(int), h->stream));
     FaceArgs a;
@@ -951,6 +965,7 @@ int gbmg::set_faces_impl(mg_handle *h, const double *ax, const double *ay, const
 
 static int set_density_impl(mg_handle *h, const double *rho, int mode)
 {
+    DepScope dep(dep_launch_default());
     if (!rho || (mode != MG_FACE_HARMONIC && mode != MG_FACE_ARITHMETIC)) return MG_EINVAL;
     CK(cudaMemsetAsync(h->err, 0, 3 * sizeof(int), h->stream));
     FaceArgs a;

@@ -135,6 +135,10 @@ struct Plan {
     cudaEvent_t staged = nullptr;  // the last table copy out of stage_h has run
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // launches of this plan may be scheduled while the previous kernel runs
+    // (programmatic dependent launch, mg_launch.cuh); cleared if a graph with
+    // such edges is not accepted
+    int dep = dep_launch_default();
     int capacity = 0;              // most grids the tables can hold
     char *stage_h = nullptr;       // pinned host copy of the table region of mem
     size_t tables_bytes = 0, o_lv = 0, o_starts = 0, o_cv = 0, o_tv = 0;

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mg_launch.cuh"
+
 namespace gbmg {
 
 constexpr int kThreads = 256;     // threads per block of every cell kernel
@@ -38,6 +40,7 @@ struct GridState {
     int active;     // 1 while the grid is being iterated
     int cycles_next;  // V-cycles of the next refinement step (1 .. inner)
     int steps;        // refinement steps done
+    int pnz;          // the caller's starting iterate has a nonzero cell (multigrid iteration)
     double rprev;     // ||r|| before the last refinement step
     double rz;      // conjugate gradients: r . z of the current step
     double alpha;   //   step length

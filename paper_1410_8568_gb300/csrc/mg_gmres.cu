@@ -65,6 +65,7 @@ template <class T>
 __global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView *__restrict__ cv, int cyc,
                                                                 const OuterView *__restrict__ ov)
 {
+    dep_entry();
     const CoarseView &C = cv[blockIdx.x];
     if (!C.gmres || !in_cycle(C.st, cyc)) return;
     __shared__ double H[(kGmresM + 1) * kGmresM];
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kGmresThreads) k_coarse_gmres(const CoarseView
 template <class T>
 void launch_coarse_gmres(const CoarseView *cv, int count, int cyc, const OuterView *ov, cudaStream_t s)
 {
-    k_coarse_gmres<T><<<count, kGmresThreads, 0, s>>>(cv, cyc, ov);
+    launch_k(k_coarse_gmres<T>, count, kGmresThreads, 0, s, cv, cyc, ov);
 }
 
 template void launch_coarse_gmres<float>(const CoarseView *, int, int, const OuterView *, cudaStream_t);

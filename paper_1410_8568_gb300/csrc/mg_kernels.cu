@@ -21,6 +21,7 @@
 #include "mg_bulk.cuh"
 
 #include <math.h>
+#include <stdlib.h>
 
 namespace gbmg {
 
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_half(const LevelView *__restrict__
                                                    const OuterView *__restrict__ ov,
                                                    const __grid_constant__ LevelView one, int single)
 {
+    dep_entry();
     if (single) {
         half_entry<T, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov, true);
         return;
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const LevelView *__restri
                                                        T omega, const __grid_constant__ LevelView one,
                                                        int single)
 {
+    dep_entry();
     if (single) {
         restrict_entry<T>(one, blockIdx.x, cyc, omega, true);
         return;
@@ -383,6 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const LevelView *__restric
                                                       const OuterView *__restrict__ ov,
                                                       const __grid_constant__ LevelView one, int single)
 {
+    dep_entry();
     if (single) {
         prolong_entry<T, FLUX, MAYOUT>(one, blockIdx.x, cyc, ov, true);
         return;
@@ -466,6 +470,7 @@ template <class T>
 __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restrict__ tv, T omega,
                                                        int nu1, int nu2, int cyc)
 {
+    dep_entry();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = (T *)smem_raw;
     const TailView &V = tv[blockIdx.x];
@@ -670,6 +675,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_apply(const LevelView *__restrict__ lv,
                                                     const int *__restrict__ start, int count)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
     const Tile t = fine_tile(L.n, blockIdx.x - start[e]);
@@ -703,6 +709,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__restrict__ cv, int cyc,
                                                            const OuterView *__restrict__ ov)
 {
+    dep_entry();
     const CoarseView &C = cv[blockIdx.x];
     if (C.gmres || !in_cycle(C.st, cyc)) return;  // GMRES grids: k_coarse_gmres
     __shared__ double rb[kMaxCoarse];
@@ -734,6 +741,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_solve(const CoarseView *__r
 // cut into pieces by zero coefficients and raises *err.
 __global__ void __launch_bounds__(1024) k_coarse_setup(const CoarseView *__restrict__ cv)
 {
+    dep_entry();
     const CoarseView &C = cv[blockIdx.x];
     const int n = C.nc;
     const int nx = C.n[0], ny = C.n[1], nz = C.n[2];
@@ -837,6 +845,7 @@ __device__ __forceinline__ double recip_nr(double x)
 
 __global__ void __launch_bounds__(kThreads) k_faces_from_density(FaceArgs a)
 {
+    dep_entry();
     const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int rest = fdiv(c, a.dx);
@@ -870,6 +879,7 @@ __global__ void __launch_bounds__(kThreads) k_faces_from_density(FaceArgs a)
 
 __global__ void __launch_bounds__(kThreads) k_scale_faces(FaceArgs a)
 {
+    dep_entry();
     const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int i = c % a.n[0];
@@ -897,6 +907,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_faces(FaceArgs a)
 // non-wall faces of alpha = w h_d^2 (1 for a cell without any).
 __global__ void __launch_bounds__(kThreads) k_cell_alpha(AlphaArgs a)
 {
+    dep_entry();
     const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
     const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
@@ -934,6 +945,7 @@ __global__ void __launch_bounds__(kThreads) k_cell_alpha(AlphaArgs a)
 // S = D u / dt: sum over axes of (high face - low face) / h_d, divided by dt
 __global__ void __launch_bounds__(kThreads) k_divergence(ProjArgs a)
 {
+    dep_entry();
     const int N = a.n[0] * a.n[1] * a.n[2];  // grids have fewer than 2^31 cells
     const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
@@ -957,6 +969,7 @@ __global__ void __launch_bounds__(kThreads) k_divergence(ProjArgs a)
 // the operator of Eq. 10, D(alpha G p) = A p, so D u = dt (S - A p).
 __global__ void __launch_bounds__(kThreads) k_project(ProjArgs a)
 {
+    dep_entry();
     const int N = a.n[0] * a.n[1] * a.n[2];
     const int stride[3] = {1, a.n[0], a.n[0] * a.n[1]};
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
@@ -974,6 +987,7 @@ __global__ void __launch_bounds__(kThreads) k_project(ProjArgs a)
 
 __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
 {
+    dep_entry();
     const int NC = a.nc[0] * a.nc[1] * a.nc[2];
     const int nx = a.nf[0], ny = a.nf[1];
     for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < NC; C += gridDim.x * blockDim.x) {
@@ -1007,6 +1021,7 @@ __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
 // Start of a solve: reset the state of every grid.
 __global__ void k_begin(const OuterView *__restrict__ ov)
 {
+    dep_entry();
     if (threadIdx.x != 0) return;
     const OuterView &O = ov[blockIdx.x];
     GridState *s = O.st;
@@ -1025,6 +1040,7 @@ __global__ void k_begin(const OuterView *__restrict__ ov)
     s->xscale = 1.0;
     s->xinv = 1.0;
     s->rprev = 0.0;
+    s->pnz = 0;
 }
 
 // Partial sums of the caller's right-hand side (which = 0, partial slot 3) or
@@ -1032,6 +1048,7 @@ __global__ void k_begin(const OuterView *__restrict__ ov)
 __global__ void __launch_bounds__(kThreads) k_sum(const OuterView *__restrict__ ov,
                                                   const int *__restrict__ start, int count, int which)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const int lb = blockIdx.x - start[e];
@@ -1079,10 +1096,14 @@ __device__ __forceinline__ void split3(double v, float &h, float &m, float &z)
     z = (float)(r - (double)m);
 }
 
-// b0 = b - mean(b) in FP64 and the partial sums of ||b0||^2 (slot 2).
+// b0 = b - mean(b) in FP64 and the partial sums of ||b0||^2 (slot 2).  Also
+// notes whether the caller's starting iterate p has a cell that is not zero
+// (GridState::pnz; a NaN counts as nonzero): a cold start (p = 0) then takes
+// its starting residual as b0 itself (k_residual, mode 2).
 __global__ void __launch_bounds__(kThreads) k_center_rhs(const OuterView *__restrict__ ov,
                                                     const int *__restrict__ start, int count)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     if (!O.st->active) return;
@@ -1090,6 +1111,7 @@ __global__ void __launch_bounds__(kThreads) k_center_rhs(const OuterView *__rest
     const int ntiles = fine_blocks(O.n);
     const double m = O.st->bmean;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
+    int nz = 0;
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
         const Tile t = fine_tile(O.n, tile);
         if (!t.ok) continue;
@@ -1100,10 +1122,12 @@ __global__ void __launch_bounds__(kThreads) k_center_rhs(const OuterView *__rest
             const double bc = O.b[rowoff + i] - m;
             O.b0[rowoff + i] = bc;
             v[2] += bc * bc;
+            nz |= !(O.p[rowoff + i] == 0.0);
         }
     }
     double out[4];
     block_sum4(v, out);
+    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&O.st->pnz, 1);
     if (threadIdx.x == 0) O.part[kPart * lb + 2] = out[2];
 }
 
@@ -1111,6 +1135,7 @@ __global__ void __launch_bounds__(kThreads) k_center_rhs(const OuterView *__rest
 __global__ void __launch_bounds__(kThreads) k_xp_prepare(const OuterView *__restrict__ ov,
                                                          const int *__restrict__ start, int count)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     if (!O.st->active) return;
@@ -1151,11 +1176,15 @@ __global__ void __launch_bounds__(kThreads) k_xp_prepare(const OuterView *__rest
 // carry no branches; the zero terms leave the sums unchanged.  Other rows: one
 // cell at a time, wall faces skipped.
 __global__ void __launch_bounds__(kThreads) k_residual_xp(const OuterView *__restrict__ ov,
-                                                          const int *__restrict__ start, int count)
+                                                          const int *__restrict__ start, int count,
+                                                          int first)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView &O = ov[e];
     if (!O.st->active) return;
+    // first: the starting residual, r = b0 where the starting iterate is zero
+    const bool cold = first && !O.st->pnz;
     const int lb = blockIdx.x - start[e];
     const int nx = O.n[0], ny = O.n[1], nz = O.n[2], per = O.per, nblk = O.nblk;
     const int sy = nx, sz = nx * ny;  // grids have fewer than 2^31 cells
@@ -1188,53 +1217,55 @@ __global__ void __launch_bounds__(kThreads) k_residual_xp(const OuterView *__res
             const int dn = j + 1 < ny ? sy : ((per & 2) ? -sy * (ny - 1) : 0);
             const int db = k > 0 ? -sz : ((per & 4) ? sz * (nz - 1) : 0);
             const int dt = k + 1 < nz ? sz : ((per & 4) ? -sz * (nz - 1) : 0);
-            const float4 A0 = *(const float4 *)(P0 + c), A1 = *(const float4 *)(P1 + c),
-                         A2 = *(const float4 *)(P2 + c);
-            const float a0[4] = {A0.x, A0.y, A0.z, A0.w}, a1[4] = {A1.x, A1.y, A1.z, A1.w},
-                        a2[4] = {A2.x, A2.y, A2.z, A2.w};
             float F0[4] = {0.f, 0.f, 0.f, 0.f}, F1[4] = {0.f, 0.f, 0.f, 0.f};
-            auto term = [&](int u, float n0, float n1, float n2, float w0, float w1) {
-                float l;
-                const float h = triple_diff(n0, n1, n2, a0[u], a1[u], a2[u], l);
-                pair_fma_acc(F0[u], F1[u], h, l, w0, w1);
-            };
-            {
-                const float4 X0 = *(const float4 *)(wx + c), X1 = *(const float4 *)(lx + c);
-                const float x0[5] = {X0.x, X0.y, X0.z, X0.w, has_e ? wx[ce] : 0.f};
-                const float x1[5] = {X1.x, X1.y, X1.z, X1.w, has_e ? lx[ce] : 0.f};
-                const float w0v = P0[cw], w1v = P1[cw], w2v = P2[cw];
-                const float e0v = P0[ce], e1v = P1[ce], e2v = P2[ce];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    if (u == 0) term(0, w0v, w1v, w2v, x0[0], x1[0]);
-                    else term(u, a0[u - 1], a1[u - 1], a2[u - 1], x0[u], x1[u]);
-                    if (u == 3) term(3, e0v, e1v, e2v, x0[4], x1[4]);
-                    else term(u, a0[u + 1], a1[u + 1], a2[u + 1], x0[u + 1], x1[u + 1]);
+            if (!cold) {  // A p is zero: no terms
+                const float4 A0 = *(const float4 *)(P0 + c), A1 = *(const float4 *)(P1 + c),
+                             A2 = *(const float4 *)(P2 + c);
+                const float a0[4] = {A0.x, A0.y, A0.z, A0.w}, a1[4] = {A1.x, A1.y, A1.z, A1.w},
+                            a2[4] = {A2.x, A2.y, A2.z, A2.w};
+                auto term = [&](int u, float n0, float n1, float n2, float w0, float w1) {
+                    float l;
+                    const float h = triple_diff(n0, n1, n2, a0[u], a1[u], a2[u], l);
+                    pair_fma_acc(F0[u], F1[u], h, l, w0, w1);
+                };
+                {
+                    const float4 X0 = *(const float4 *)(wx + c), X1 = *(const float4 *)(lx + c);
+                    const float x0[5] = {X0.x, X0.y, X0.z, X0.w, has_e ? wx[ce] : 0.f};
+                    const float x1[5] = {X1.x, X1.y, X1.z, X1.w, has_e ? lx[ce] : 0.f};
+                    const float w0v = P0[cw], w1v = P1[cw], w2v = P2[cw];
+                    const float e0v = P0[ce], e1v = P1[ce], e2v = P2[ce];
+    #pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        if (u == 0) term(0, w0v, w1v, w2v, x0[0], x1[0]);
+                        else term(u, a0[u - 1], a1[u - 1], a2[u - 1], x0[u], x1[u]);
+                        if (u == 3) term(3, e0v, e1v, e2v, x0[4], x1[4]);
+                        else term(u, a0[u + 1], a1[u + 1], a2[u + 1], x0[u + 1], x1[u + 1]);
+                    }
                 }
+                auto axis = [&](int dlo, int dhi, bool has_hi, const float *w, const float *wl) {
+                    const float4 L0 = *(const float4 *)(P0 + c + dlo), L1 = *(const float4 *)(P1 + c + dlo),
+                                 L2 = *(const float4 *)(P2 + c + dlo);
+                    const float4 H0 = *(const float4 *)(P0 + c + dhi), H1 = *(const float4 *)(P1 + c + dhi),
+                                 H2 = *(const float4 *)(P2 + c + dhi);
+                    const float4 WL0 = *(const float4 *)(w + c), WL1 = *(const float4 *)(wl + c);
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 WH0 = has_hi ? *(const float4 *)(w + c + dhi) : z4;
+                    const float4 WH1 = has_hi ? *(const float4 *)(wl + c + dhi) : z4;
+                    const float l0[4] = {L0.x, L0.y, L0.z, L0.w}, l1[4] = {L1.x, L1.y, L1.z, L1.w},
+                                l2[4] = {L2.x, L2.y, L2.z, L2.w};
+                    const float h0[4] = {H0.x, H0.y, H0.z, H0.w}, h1[4] = {H1.x, H1.y, H1.z, H1.w},
+                                h2[4] = {H2.x, H2.y, H2.z, H2.w};
+                    const float wl0[4] = {WL0.x, WL0.y, WL0.z, WL0.w}, wl1[4] = {WL1.x, WL1.y, WL1.z, WL1.w};
+                    const float wh0[4] = {WH0.x, WH0.y, WH0.z, WH0.w}, wh1[4] = {WH1.x, WH1.y, WH1.z, WH1.w};
+    #pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        term(u, l0[u], l1[u], l2[u], wl0[u], wl1[u]);
+                        term(u, h0[u], h1[u], h2[u], wh0[u], wh1[u]);
+                    }
+                };
+                axis(ds, dn, has_n, wy, ly);
+                axis(db, dt, has_t, wz, lz);
             }
-            auto axis = [&](int dlo, int dhi, bool has_hi, const float *w, const float *wl) {
-                const float4 L0 = *(const float4 *)(P0 + c + dlo), L1 = *(const float4 *)(P1 + c + dlo),
-                             L2 = *(const float4 *)(P2 + c + dlo);
-                const float4 H0 = *(const float4 *)(P0 + c + dhi), H1 = *(const float4 *)(P1 + c + dhi),
-                             H2 = *(const float4 *)(P2 + c + dhi);
-                const float4 WL0 = *(const float4 *)(w + c), WL1 = *(const float4 *)(wl + c);
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 WH0 = has_hi ? *(const float4 *)(w + c + dhi) : z4;
-                const float4 WH1 = has_hi ? *(const float4 *)(wl + c + dhi) : z4;
-                const float l0[4] = {L0.x, L0.y, L0.z, L0.w}, l1[4] = {L1.x, L1.y, L1.z, L1.w},
-                            l2[4] = {L2.x, L2.y, L2.z, L2.w};
-                const float h0[4] = {H0.x, H0.y, H0.z, H0.w}, h1[4] = {H1.x, H1.y, H1.z, H1.w},
-                            h2[4] = {H2.x, H2.y, H2.z, H2.w};
-                const float wl0[4] = {WL0.x, WL0.y, WL0.z, WL0.w}, wl1[4] = {WL1.x, WL1.y, WL1.z, WL1.w};
-                const float wh0[4] = {WH0.x, WH0.y, WH0.z, WH0.w}, wh1[4] = {WH1.x, WH1.y, WH1.z, WH1.w};
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    term(u, l0[u], l1[u], l2[u], wl0[u], wl1[u]);
-                    term(u, h0[u], h1[u], h2[u], wh0[u], wh1[u]);
-                }
-            };
-            axis(ds, dn, has_n, wy, ly);
-            axis(db, dt, has_t, wz, lz);
             const float4 Q0 = *(const float4 *)(B0 + c), Q1 = *(const float4 *)(B1 + c);
             const float q0[4] = {Q0.x, Q0.y, Q0.z, Q0.w}, q1[4] = {Q1.x, Q1.y, Q1.z, Q1.w};
             float rq[4];
@@ -1261,18 +1292,20 @@ __global__ void __launch_bounds__(kThreads) k_residual_xp(const OuterView *__res
                 const int c = rowoff + i;
                 const float a0 = P0[c], a1 = P1[c], a2 = P2[c];
                 float F0 = 0.f, F1 = 0.f;
-                if (i > 0) XP_FACE(c - 1, wx[c], lx[c]);
-                else if (per & 1) XP_FACE(c + nx - 1, wx[c], lx[c]);
-                if (i + 1 < nx) XP_FACE(c + 1, wx[c + 1], lx[c + 1]);
-                else if (per & 1) XP_FACE(c + 1 - nx, wx[c + 1 - nx], lx[c + 1 - nx]);
-                if (j > 0) XP_FACE(c - sy, wy[c], ly[c]);
-                else if (per & 2) XP_FACE(c + sy * (ny - 1), wy[c], ly[c]);
-                if (j + 1 < ny) XP_FACE(c + sy, wy[c + sy], ly[c + sy]);
-                else if (per & 2) XP_FACE(c - sy * (ny - 1), wy[c - sy * (ny - 1)], ly[c - sy * (ny - 1)]);
-                if (k > 0) XP_FACE(c - sz, wz[c], lz[c]);
-                else if (per & 4) XP_FACE(c + sz * (nz - 1), wz[c], lz[c]);
-                if (k + 1 < nz) XP_FACE(c + sz, wz[c + sz], lz[c + sz]);
-                else if (per & 4) XP_FACE(c - sz * (nz - 1), wz[c - sz * (nz - 1)], lz[c - sz * (nz - 1)]);
+                if (!cold) {
+                    if (i > 0) XP_FACE(c - 1, wx[c], lx[c]);
+                    else if (per & 1) XP_FACE(c + nx - 1, wx[c], lx[c]);
+                    if (i + 1 < nx) XP_FACE(c + 1, wx[c + 1], lx[c + 1]);
+                    else if (per & 1) XP_FACE(c + 1 - nx, wx[c + 1 - nx], lx[c + 1 - nx]);
+                    if (j > 0) XP_FACE(c - sy, wy[c], ly[c]);
+                    else if (per & 2) XP_FACE(c + sy * (ny - 1), wy[c], ly[c]);
+                    if (j + 1 < ny) XP_FACE(c + sy, wy[c + sy], ly[c + sy]);
+                    else if (per & 2) XP_FACE(c - sy * (ny - 1), wy[c - sy * (ny - 1)], ly[c - sy * (ny - 1)]);
+                    if (k > 0) XP_FACE(c - sz, wz[c], lz[c]);
+                    else if (per & 4) XP_FACE(c + sz * (nz - 1), wz[c], lz[c]);
+                    if (k + 1 < nz) XP_FACE(c + sz, wz[c + sz], lz[c + sz]);
+                    else if (per & 4) XP_FACE(c - sz * (nz - 1), wz[c - sz * (nz - 1)], lz[c - sz * (nz - 1)]);
+                }
                 float tt;
                 const float hh = two_diff(B0[c], F0, tt);
                 const float rc = __fadd_rn(hh, __fadd_rn(tt, __fsub_rn(B1[c], F1)));
@@ -1291,15 +1324,19 @@ __global__ void __launch_bounds__(kThreads) k_residual_xp(const OuterView *__res
 // Outer residual r = (b - mean b) - A p in FP64, handed to the V-cycle in its
 // precision Te, scaled by xscale (a power of 2; 1 for CG).  init = 1 (start of
 // a CG solve): also stores b0 = b - mean(b) and the partial sums of ||b0||^2
-// (slot 2), all FP64.  ||r||^2 goes to slot 0; after the first CG residual it
-// is accumulated from the rounded, scaled r handed to the cycle (a norm only
-// steers the stopping test, so its own rounding at 1e-7 relative is
-// immaterial, and the scale keeps FP32 squares inside the FP32 range).
+// (slot 2), all FP64.  init = 2 (start of a multigrid iteration): as 0, but a
+// grid whose starting iterate is zero everywhere (GridState::pnz clear) takes
+// r = b0 without evaluating A p, which is exactly zero there.  ||r||^2 goes to
+// slot 0; after the first CG residual it is accumulated from the rounded,
+// scaled r handed to the cycle (a norm only steers the stopping test, so its
+// own rounding at 1e-7 relative is immaterial, and the scale keeps FP32
+// squares inside the FP32 range).
 template <class Te>
 __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restrict__ ov,
                                                        const int *__restrict__ start, int count,
                                                        int init)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const GridState *s = O.st;
@@ -1309,6 +1346,8 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
     const int nx = O.n[0];
     Te *r = (Te *)O.r;
     const double m = s->bmean, sc = s->xscale;
+    const bool cold = init == 2 && !s->pnz;
+    if (init == 2) init = 0;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     Te racc = Te(0);
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
@@ -1319,7 +1358,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
             const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
             if (i >= nx) continue;
             const long long c = rowoff + i;
-            const double f = flux64(O, O.p, i, t.j, t.k, c);
+            const double f = cold ? 0.0 : flux64(O, O.p, i, t.j, t.k, c);
             double bc;
             if (init) {
                 bc = O.b[c] - m;
@@ -1353,6 +1392,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
 // not converged.
 __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restrict__ ov, int mode)
 {
+    dep_entry();
     const OuterView &O = ov[blockIdx.x];
     GridState *s = O.st;
     if (mode != 3 && !s->active) return;
@@ -1423,6 +1463,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
 __global__ void __launch_bounds__(kThreads) k_final(const OuterView *__restrict__ ov,
                                                     const int *__restrict__ start, int count)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const GridState *s = O.st;
@@ -1454,6 +1495,7 @@ __global__ void __launch_bounds__(kThreads) k_final(const OuterView *__restrict_
 // the loop is bounded.
 __global__ void k_loop_ctl(cudaGraphConditionalHandle h, const OuterView *__restrict__ ov, int count)
 {
+    dep_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned int any = 0;
     for (int g = 0; g < count; g++) any |= (unsigned int)(ov[g].st->active != 0);
@@ -1464,6 +1506,7 @@ __global__ void k_loop_ctl(cudaGraphConditionalHandle h, const OuterView *__rest
 // the most any active grid of the plan asks for (switch branch c - 1).
 __global__ void k_step_ctl(cudaGraphConditionalHandle h, const OuterView *__restrict__ ov, int count)
 {
+    dep_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int c = 1;
     for (int g = 0; g < count; g++) {
@@ -1477,6 +1520,7 @@ __global__ void k_step_ctl(cudaGraphConditionalHandle h, const OuterView *__rest
 // device-to-host copy then serves the whole batch).
 __global__ void k_gather_states(const OuterView *__restrict__ ov, int count, GridState *out)
 {
+    dep_entry();
     for (int g = threadIdx.x; g < count; g += blockDim.x) out[g] = *ov[g].st;
 }
 
@@ -1484,35 +1528,46 @@ __global__ void k_gather_states(const OuterView *__restrict__ ov, int count, Gri
 // host launchers
 // ---------------------------------------------------------------------------
 
+thread_local int tl_dep_launch = 0;
+
+int dep_launch_default()
+{
+    static const int on = [] {
+        const char *e = getenv("MG_DEP_LAUNCH");
+        return (e && e[0] == '0') ? 0 : 1;
+    }();
+    return on;
+}
+
 void launch_gather_states(const OuterTable &ot, GridState *out, cudaStream_t s)
 {
-    k_gather_states<<<1, 128, 0, s>>>(ot.ov, ot.count, out);
+    launch_k(k_gather_states, 1, 128, 0, s, ot.ov, ot.count, out);
 }
 
 void launch_step_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStream_t s)
 {
-    k_step_ctl<<<1, 32, 0, s>>>(h, ot.ov, ot.count);
+    launch_k(k_step_ctl, 1, 32, 0, s, h, ot.ov, ot.count);
 }
 void launch_loop_ctl(cudaGraphConditionalHandle h, const OuterTable &ot, cudaStream_t s)
 {
-    k_loop_ctl<<<1, 32, 0, s>>>(h, ot.ov, ot.count);
+    launch_k(k_loop_ctl, 1, 32, 0, s, h, ot.ov, ot.count);
 }
 
 template <class T>
 void launch_half_rows(const Table &tb, int colour, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
     if (flags & kOuter)
-        k_half<T, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc, ov,
-                                                       table_view(tb), table_single(tb));
+        launch_k(k_half<T, true>, tb.blocks, kThreads, 0, s, tb.lv, tb.start, tb.count, colour, (T)omega, flags,
+                 tb.cyc, ov, table_view(tb), table_single(tb));
     else
-        k_half<T, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, colour, (T)omega, flags, tb.cyc,
-                                                        nullptr, table_view(tb), table_single(tb));
+        launch_k(k_half<T, false>, tb.blocks, kThreads, 0, s, tb.lv, tb.start, tb.count, colour, (T)omega, flags,
+                 tb.cyc, nullptr, table_view(tb), table_single(tb));
 }
 template <class T>
 void launch_restrict_rows(const Table &tb, double omega, cudaStream_t s)
 {
-    k_restrict<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega, table_view(tb),
-                                                 table_single(tb));
+    launch_k(k_restrict<T>, tb.blocks, kThreads, 0, s, tb.lv, tb.start, tb.count, tb.cyc, (T)omega,
+             table_view(tb), table_single(tb));
 }
 template <class T>
 void launch_prolong_rows(const Table &tb, const OuterView *ov, cudaStream_t s)
@@ -1520,13 +1575,13 @@ void launch_prolong_rows(const Table &tb, const OuterView *ov, cudaStream_t s)
     const int c = tb.cyc;
     const LevelView one = table_view(tb);
     const int single = table_single(tb);
+    const dim3 g(tb.blocks), b(kThreads);
     if (tb.flux) {
-        if (ov) k_prolong<T, true, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov, one, single);
-        else k_prolong<T, true, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr, one, single);
+        if (ov) launch_k(k_prolong<T, true, true>, g, b, 0, s, tb.lv, tb.start, tb.count, c, ov, one, single);
+        else launch_k(k_prolong<T, true, false>, g, b, 0, s, tb.lv, tb.start, tb.count, c, nullptr, one, single);
     } else {
-        if (ov) k_prolong<T, false, true><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, ov, one, single);
-        else k_prolong<T, false, false><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count, c, nullptr, one,
-                                                                      single);
+        if (ov) launch_k(k_prolong<T, false, true>, g, b, 0, s, tb.lv, tb.start, tb.count, c, ov, one, single);
+        else launch_k(k_prolong<T, false, false>, g, b, 0, s, tb.lv, tb.start, tb.count, c, nullptr, one, single);
     }
 }
 template <class T>
@@ -1538,21 +1593,21 @@ void launch_tail(const TailView *tv, int count, size_t smem, double omega, int n
         cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_tail<T><<<count, kTailThreads, smem, s>>>(tv, (T)omega, nu1, nu2, cyc);
+    launch_k(k_tail<T>, count, kTailThreads, smem, s, tv, (T)omega, nu1, nu2, cyc);
 }
 template <class T>
 void launch_apply(const Table &tb, cudaStream_t s)
 {
-    k_apply<T><<<tb.blocks, kThreads, 0, s>>>(tb.lv, tb.start, tb.count);
+    launch_k(k_apply<T>, tb.blocks, kThreads, 0, s, tb.lv, tb.start, tb.count);
 }
 template <class T>
 void launch_coarse_solve(const CoarseView *cv, int count, int cyc, const OuterView *ov, cudaStream_t s)
 {
-    k_coarse_solve<T><<<count, kThreads, 0, s>>>(cv, cyc, ov);
+    launch_k(k_coarse_solve<T>, count, kThreads, 0, s, cv, cyc, ov);
 }
 void launch_coarse_setup(const CoarseView *cv, int count, cudaStream_t s)
 {
-    k_coarse_setup<<<count, 1024, 0, s>>>(cv);
+    launch_k(k_coarse_setup, count, 1024, 0, s, cv);
 }
 static int cells_grid(long long N)
 {
@@ -1565,57 +1620,57 @@ void launch_faces_from_density(const FaceArgs &a, cudaStream_t s)
     FaceArgs b = a;
     b.dx = make_fastdiv((unsigned)a.n[0]);
     b.dy = make_fastdiv((unsigned)a.n[1]);
-    k_faces_from_density<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(b);
+    launch_k(k_faces_from_density, cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s, b);
 }
 void launch_scale_faces(const FaceArgs &a, cudaStream_t s)
 {
-    k_scale_faces<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+    launch_k(k_scale_faces, cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s, a);
 }
 void launch_cell_alpha(const AlphaArgs &a, cudaStream_t s)
 {
-    k_cell_alpha<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+    launch_k(k_cell_alpha, cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s, a);
 }
 void launch_divergence(const ProjArgs &a, cudaStream_t s)
 {
-    k_divergence<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+    launch_k(k_divergence, cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s, a);
 }
 void launch_project(const ProjArgs &a, cudaStream_t s)
 {
-    k_project<<<cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s>>>(a);
+    launch_k(k_project, cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s, a);
 }
 void launch_coarsen_faces(const CoarsenArgs &a, cudaStream_t s)
 {
-    k_coarsen_faces<<<cells_grid((long long)a.nc[0] * a.nc[1] * a.nc[2]), kThreads, 0, s>>>(a);
+    launch_k(k_coarsen_faces, cells_grid((long long)a.nc[0] * a.nc[1] * a.nc[2]), kThreads, 0, s, a);
 }
-void launch_begin(const OuterView *ov, int count, cudaStream_t s) { k_begin<<<count, 32, 0, s>>>(ov); }
+void launch_begin(const OuterView *ov, int count, cudaStream_t s) { launch_k(k_begin, count, 32, 0, s, ov); }
 void launch_sum(const OuterTable &ot, int which, cudaStream_t s)
 {
-    k_sum<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, which);
+    launch_k(k_sum, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count, which);
 }
 template <class Te>
 void launch_residual(const OuterTable &ot, int init, cudaStream_t s)
 {
-    k_residual<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, init);
+    launch_k(k_residual<Te>, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count, init);
 }
 void launch_center_rhs(const OuterTable &ot, cudaStream_t s)
 {
-    k_center_rhs<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    launch_k(k_center_rhs, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count);
 }
 void launch_xp_prepare(const OuterTable &ot, cudaStream_t s)
 {
-    k_xp_prepare<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    launch_k(k_xp_prepare, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count);
 }
-void launch_residual_xp(const OuterTable &ot, cudaStream_t s)
+void launch_residual_xp(const OuterTable &ot, int first, cudaStream_t s)
 {
-    k_residual_xp<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    launch_k(k_residual_xp, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count, first);
 }
 void launch_finalize(const OuterTable &ot, int mode, cudaStream_t s)
 {
-    k_finalize<<<ot.count, kThreads, 0, s>>>(ot.ov, mode);
+    launch_k(k_finalize, ot.count, kThreads, 0, s, ot.ov, mode);
 }
 void launch_final(const OuterTable &ot, cudaStream_t s)
 {
-    k_final<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    launch_k(k_final, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count);
 }
 
 template void launch_half_rows<float>(const Table &, int, double, int, const OuterView *, cudaStream_t);

@@ -117,12 +117,14 @@ void launch_divergence(const ProjArgs &, cudaStream_t);
 void launch_project(const ProjArgs &, cudaStream_t);
 void launch_begin(const OuterView *, int count, cudaStream_t);
 void launch_sum(const OuterTable &, int which, cudaStream_t);
+// init: 0 after a refinement step, 1 start of a CG solve, 2 start of a multigrid
+// iteration (a zero starting iterate gives r = b - mean b without A p)
 template <class Te> void launch_residual(const OuterTable &, int init, cudaStream_t);
 // multigrid iteration: b - mean b and its norm (sets the cycles' scale);
 // extended-precision outer iteration: the scaled float forms of b and p, the residual
 void launch_center_rhs(const OuterTable &, cudaStream_t);
 void launch_xp_prepare(const OuterTable &, cudaStream_t);
-void launch_residual_xp(const OuterTable &, cudaStream_t);
+void launch_residual_xp(const OuterTable &, int first, cudaStream_t);
 void launch_finalize(const OuterTable &, int mode, cudaStream_t);
 void launch_final(const OuterTable &, cudaStream_t);
 void launch_gather_states(const OuterTable &, GridState *out, cudaStream_t);

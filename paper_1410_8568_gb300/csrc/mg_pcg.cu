@@ -42,6 +42,7 @@ __device__ __forceinline__ void for_cells(const OuterView &O, int lb, F &&f)
 __global__ void __launch_bounds__(kThreads) k_pcg_matvec(const OuterView *__restrict__ ov,
                                                          const int *__restrict__ start, int count)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     if (!O.st->active) return;
@@ -63,6 +64,7 @@ template <class Te>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(const OuterView *__restrict__ ov,
                                                          const int *__restrict__ start, int count)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const GridState *s = O.st;
@@ -89,6 +91,7 @@ template <class Te>
 __global__ void __launch_bounds__(kThreads) k_pcg_z(const OuterView *__restrict__ ov,
                                                     const int *__restrict__ start, int count)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     if (!O.st->active) return;
@@ -112,6 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_z(const OuterView *__restrict_
 __global__ void __launch_bounds__(kThreads) k_pcg_dir(const OuterView *__restrict__ ov,
                                                       const int *__restrict__ start, int count, int first)
 {
+    dep_entry();
     const int e = find_entry(start, count);
     const OuterView O = ov[e];
     const GridState *s = O.st;
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dir(const OuterView *__restric
 // later preconditioning (beta, rz, mean z).
 __global__ void __launch_bounds__(kThreads) k_pcg_finalize(const OuterView *__restrict__ ov, int mode)
 {
+    dep_entry();
     const OuterView &O = ov[blockIdx.x];
     GridState *s = O.st;
     if (!s->active) return;
@@ -159,25 +164,25 @@ __global__ void __launch_bounds__(kThreads) k_pcg_finalize(const OuterView *__re
 
 void launch_pcg_matvec(const OuterTable &ot, cudaStream_t s)
 {
-    k_pcg_matvec<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    launch_k(k_pcg_matvec, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count);
 }
 template <class Te>
 void launch_pcg_update(const OuterTable &ot, cudaStream_t s)
 {
-    k_pcg_update<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    launch_k(k_pcg_update<Te>, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count);
 }
 template <class Te>
 void launch_pcg_z(const OuterTable &ot, cudaStream_t s)
 {
-    k_pcg_z<Te><<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count);
+    launch_k(k_pcg_z<Te>, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count);
 }
 void launch_pcg_dir(const OuterTable &ot, int first, cudaStream_t s)
 {
-    k_pcg_dir<<<ot.blocks, kThreads, 0, s>>>(ot.ov, ot.start, ot.count, first);
+    launch_k(k_pcg_dir, ot.blocks, kThreads, 0, s, ot.ov, ot.start, ot.count, first);
 }
 void launch_pcg_finalize(const OuterTable &ot, int mode, cudaStream_t s)
 {
-    k_pcg_finalize<<<ot.count, kThreads, 0, s>>>(ot.ov, mode);
+    launch_k(k_pcg_finalize, ot.count, kThreads, 0, s, ot.ov, mode);
 }
 
 template void launch_pcg_update<float>(const OuterTable &, cudaStream_t);

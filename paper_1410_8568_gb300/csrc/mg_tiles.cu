@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(B) k_half_flat(const LevelView *__restrict__ l
                                                  const OuterView *__restrict__ ov,
                                                  const __grid_constant__ LevelView one, int single)
 {
+    dep_entry();
     if (single) {
         half_flat_entry<T, B, Q, MAYOUT>(one, blockIdx.x, colour, omega, flags, cyc, ov, true);
         return;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict
                                                      T omega, const __grid_constant__ LevelView one,
                                                      int single)
 {
+    dep_entry();
     if (single) {
         restrict_flat_entry<T, B, Q>(one, blockIdx.x, cyc, omega, true);
         return;
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(B) k_prolong_flat(const LevelView *__restrict_
                                                     const int *__restrict__ start, int count, int cyc,
                                                     const __grid_constant__ LevelView one, int single)
 {
+    dep_entry();
     if (single) {
         prolong_flat_entry<T, B, Q>(one, blockIdx.x, cyc, true);
         return;
@@ -188,13 +191,11 @@ void launch_half(const Table &tb, int colour, double omega, int flags, const Out
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
         if (flags & kOuter)
-            k_half_flat<T, ts.B, ts.Q, true><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
-                                                                        (T)omega, flags, tb.cyc, ov,
-                                                                        table_view(tb), table_single(tb));
+            launch_k(k_half_flat<T, ts.B, ts.Q, true>, tb.blocks, ts.B, 0, s, tb.lv, tb.start, tb.count, colour,
+                     (T)omega, flags, tb.cyc, ov, table_view(tb), table_single(tb));
         else
-            k_half_flat<T, ts.B, ts.Q, false><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, colour,
-                                                                         (T)omega, flags, tb.cyc, nullptr,
-                                                                         table_view(tb), table_single(tb));
+            launch_k(k_half_flat<T, ts.B, ts.Q, false>, tb.blocks, ts.B, 0, s, tb.lv, tb.start, tb.count, colour,
+                     (T)omega, flags, tb.cyc, nullptr, table_view(tb), table_single(tb));
     });
     if (!flat) launch_half_rows<T>(tb, colour, omega, flags, ov, s);
 }
@@ -205,8 +206,8 @@ void launch_restrict(const Table &tb, double omega, cudaStream_t s)
     if (tb.blocks == 0) return;
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_restrict_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, (T)omega,
-                                                                  table_view(tb), table_single(tb));
+        launch_k(k_restrict_flat<T, ts.B, ts.Q>, tb.blocks, ts.B, 0, s, tb.lv, tb.start, tb.count, tb.cyc,
+                 (T)omega, table_view(tb), table_single(tb));
     });
     if (!flat) launch_restrict_rows<T>(tb, omega, s);
 }
@@ -221,8 +222,8 @@ void launch_prolong(const Table &tb, const OuterView *ov, cudaStream_t s)
     }
     const bool flat = with_variant(tb.variant, [&](auto V) {
         constexpr TileShape ts = tile_shape(decltype(V)::value);
-        k_prolong_flat<T, ts.B, ts.Q><<<tb.blocks, ts.B, 0, s>>>(tb.lv, tb.start, tb.count, tb.cyc, table_view(tb),
-                                                                 table_single(tb));
+        launch_k(k_prolong_flat<T, ts.B, ts.Q>, tb.blocks, ts.B, 0, s, tb.lv, tb.start, tb.count, tb.cyc,
+                 table_view(tb), table_single(tb));
     });
     if (!flat) launch_prolong_rows<T>(tb, nullptr, s);
 }

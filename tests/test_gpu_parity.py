@@ -560,3 +560,37 @@ def test_scaled_rhs_and_offset_iterate(precision, outer):
         err = np.linalg.norm(x - pstar) / np.linalg.norm(pstar)
         print("offset warm start: iters=%d rel_res=%.2e (oracle %.2e) err=%.2e" % (sto.iters, sto.rel_res, rel, err))
         assert rel <= 1.05 * TOL and err <= ERR
+
+
+@pytest.mark.parametrize("precision,outer", MODES, ids=MODE_IDS)
+def test_zero_start_shortcut(precision, outer):
+    """A starting iterate that is zero in every cell gives the starting residual
+    b - mean b without evaluating A p (the product is exactly zero there).  An
+    iterate of -0.0 everywhere is zero too: the same solve, bit for bit.  One
+    nonzero cell takes the full residual: the starting residual norm the solver
+    reports is that of b - mean b - A p (oracle operator), not that of
+    b - mean b, and the solve still reaches p*."""
+    P = I.config2(40)
+    f = oracle.faces_from_density(P.shape, P.bc, P.rho)
+    pstar = exact_solution("cfg2_dropfilm_40", P, f)
+    bp = P.rhs - P.rhs.mean()
+    with solver_for(P, f, precision=precision, outer=outer) as S:
+        b = dev(P.rhs)
+        p = torch.zeros_like(b)
+        st = S.solve(b, p, tol=TOL)
+        assert st.status == gbmg.OK
+        assert st.res0 == pytest.approx(np.linalg.norm(bp), rel=1e-6)
+        pm = torch.full_like(b, -0.0)
+        stm = S.solve(b, pm, tol=TOL)
+        assert stm.iters == st.iters and stm.res0 == st.res0 and torch.equal(pm, p)
+        d = np.zeros(cells(P.shape))
+        d[17, 5, 23] = 10.0 * np.abs(pstar).max()
+        pd = dev(d)
+        std = S.solve(b, pd, tol=TOL)
+        assert std.status == gbmg.OK and std.rel_res <= TOL
+        r0 = np.linalg.norm(oracle.residual(P.shape, P.bc, f, bp, d))
+        assert abs(r0 / np.linalg.norm(bp) - 1.0) > 0.1
+        assert std.res0 == pytest.approx(r0, rel=1e-6)
+        err = np.linalg.norm(host(pd) - pstar) / np.linalg.norm(pstar)
+        print("single-cell start: iters=%d res0=%.6e (oracle %.6e) err=%.2e" % (std.iters, std.res0, r0, err))
+        assert err <= ERR
