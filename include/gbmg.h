@@ -300,6 +300,11 @@ int mg_level_shape(const mg_handle *h, int level, int *nx, int *ny, int *nz);
 /* Scaled coefficients w_d = alpha_d / h_d^2 of `level` (FP64, DEVICE out). */
 int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double *wz);
 
+/* The FP32 copies of the same coefficients that the V-cycles of a mixed-precision
+ * handle use (each the FP64 value rounded to nearest, ties to even); DEVICE out,
+ * n cells each.  MG_EINVAL for an FP64 handle.  Synchronous. */
+int mg_level_faces32(const mg_handle *h, int level, float *wx, float *wy, float *wz);
+
 /* Cell coefficients of `level` used by the flux-conserving prolongation
  * (MG_PROLONG_FLUX, Sec. 2.3 item 4): the mean alpha of each cell's faces that
  * are not walls, from the level's face coefficients; FP64, DEVICE buffer of the

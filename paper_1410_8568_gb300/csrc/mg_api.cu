@@ -419,6 +419,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.xp = h->xp ? 1 : 0;
         v.xq = make_fastdiv(v.n[0] >= 4 ? (unsigned)(v.n[0] >> 2) : 1u);
         v.xy = make_fastdiv((unsigned)v.n[1]);
+        v.dxt = make_fastdiv((unsigned)fine_xtiles(v.n[0]));
         for (int q = 0; q < 3; q++) {
             v.xp3[q] = h->xp3[q];
             v.w32[q] = h->xp ? h->lev[0].w32[q] : nullptr;
@@ -630,7 +631,10 @@ static void body(Plan &P, Prof &pf, int cycles)
 template <class T>
 static void body_cycles(Plan &P, Prof &pf, int cycles)
 {
-    for (int c = 0; c < cycles; c++) vcycle<T>(P, pf, c, true);
+    // a lone grid's step runs exactly `cycles` cycles (the graph branch and the
+    // host loop both take its own count), so only the last one can end it: the
+    // others launch the half-sweep without the update of the outer iterate
+    for (int c = 0; c < cycles; c++) vcycle<T>(P, pf, c, P.G > 1 || c + 1 == cycles);
 }
 
 template <class T>
@@ -920,6 +924,8 @@ static int upload_faces(mg_handle *h)
             a.wc[d] = h->lev[l].w64[d];
             a.wc32[d] = h->mixed ? h->lev[l].w32[d] : nullptr;
         }
+        a.dx = make_fastdiv((unsigned)a.nc[0]);
+        a.dy = make_fastdiv((unsigned)a.nc[1]);
         launch_coarsen_faces(a, h->stream);
         if (h->lev[l].alpha64) {
             // cell coefficients for the flux-conserving prolongation into level l - 1
@@ -1457,6 +1463,17 @@ int mg_level_faces(const mg_handle *h, int level, double *wx, double *wy, double
     double *o[3] = {wx, wy, wz};
     for (int d = 0; d < 3; d++)
         CK(cudaMemcpyAsync(o[d], h->lev[level].w64[d], n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_level_faces32(const mg_handle *h, int level, float *wx, float *wy, float *wz)
+{
+    if (!h || level < 0 || level >= h->L || !wx || !wy || !wz || !h->mixed) return MG_EINVAL;
+    const size_t n = (size_t)h->lev[level].N * sizeof(float);
+    float *o[3] = {wx, wy, wz};
+    for (int d = 0; d < 3; d++)
+        CK(cudaMemcpyAsync(o[d], h->lev[level].w32[d], n, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return MG_OK;
 }

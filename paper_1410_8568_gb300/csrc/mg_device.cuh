@@ -140,6 +140,10 @@ struct LevelView {
     // flat tilings: quads per fine row n[0]/4, fine rows per plane n[1],
     // coarse cell pairs per coarse row nc[0]/2, coarse rows per plane nc[1]
     FastDiv dq, dy, dp, dcy;
+    // row-tiled kernels: division by the block columns of a row, for quad rows
+    // ((n[0]/4 + 31) / 32), coarse pair rows ((nc[0]/2 + 31) / 32), coarse cell
+    // rows (coarse_xtiles(nc[0])) and fine cell rows (fine_xtiles(n[0]))
+    FastDiv dxq, dxp, dxc, dxt;
     const void *ac;  // cell coefficients of the next coarser level (flux-conserving prolongation)
     // restriction: also give the next coarser level its first (zero-start) red
     // half-sweep, from the restricted right-hand side and that level's faces wc
@@ -173,6 +177,7 @@ struct OuterView {
     // side (b - mean b) * xscale = xb[0] + xb[1], level-0 faces w32[d] + wlo[d]
     int xp;
     FastDiv xq, xy;      // division by the quads per row n[0] / 4 and by n[1]
+    FastDiv dxt;         // division by the row tiles of a row, fine_xtiles(n[0])
     float *xp3[3];
     float *xb[2];
     const float *w32[3];

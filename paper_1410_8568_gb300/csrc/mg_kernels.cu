@@ -145,7 +145,7 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
 
     if ((nx & 3) != 0) {
         // one cell per thread (row tiles of 64 cells per warp, 2 per lane)
-        const Tile t = fine_tile(L.n, lb);
+        const Tile t = fine_tile(L.n, lb, L.dxt, L.dy);
         if (!t.ok) return;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -179,12 +179,13 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
     // a block 8 rows
     const int nq = nx >> 2;
     const int xt_n = (nq + 31) >> 5;
-    const int tq = lb % xt_n, rb = lb / xt_n;
+    const int rb = fdiv(lb, L.dxq), tq = lb - rb * xt_n;
     const int row = rb * kRowsPerBlock + (threadIdx.x >> 5);
     if (row >= ny * nz) return;
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
-    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row % ny, row / ny, qx, colour, omega, zero, po, go);
+    const int k = fdiv(row, L.dy);
+    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row - k * ny, k, qx, colour, omega, zero, po, go);
 }
 
 // MAYOUT: the launch carries kOuter; the test of the step's last cycle is
@@ -260,22 +261,23 @@ __device__ __forceinline__ void restrict_entry(const LevelView &L, int lb, int c
         // in each of the 2 x 2 fine rows below it
         const int np = ncx >> 1;
         const int xt_n = (np + 31) >> 5;
-        const int xt = lb % xt_n, rb = lb / xt_n;
+        const int rb = fdiv(lb, L.dxp), xt = lb - rb * xt_n;
         const int crow = rb * kRowsPerBlock + (threadIdx.x >> 5);
         if (crow >= ncy * ncz) return;
         const int P = (xt << 5) + (threadIdx.x & 31);
         if (P >= np) return;
-        restrict_pair<T>(L, crow, crow % ncy, crow / ncy, P, omega, go);
+        const int K = fdiv(crow, L.dcy);
+        restrict_pair<T>(L, crow, crow - K * ncy, K, P, omega, go);
         return;
     }
     if (!go) return;
     const int xt_n = coarse_xtiles(ncx);
-    const int xt = lb % xt_n, rb = lb / xt_n;
+    const int rb = fdiv(lb, L.dxc), xt = lb - rb * xt_n;
     const int crow = rb * kRowsPerBlock + (threadIdx.x >> 5);
     if (crow >= ncy * ncz) return;
     const int I = xt * kCSeg + (threadIdx.x & 31);
     if (I >= ncx) return;
-    const int J = crow % ncy, K = crow / ncy;
+    const int K = fdiv(crow, L.dcy), J = crow - K * ncy;
     T s = T(0);
 #pragma unroll
     for (int dz = 0; dz < 2; dz++)
@@ -333,21 +335,22 @@ __device__ __forceinline__ void prolong_body(const LevelView &L, int lb, const O
     if ((nx & 3) == 0) {
         const int nq = nx >> 2;
         const int xt_n = (nq + 31) >> 5;
-        const int xt = lb % xt_n, rb = lb / xt_n;
+        const int rb = fdiv(lb, L.dxq), xt = lb - rb * xt_n;
         const int row = rb * kRowsPerBlock + (threadIdx.x >> 5);
         if (row >= ny * nz) return;
         const int qx = (xt << 5) + (threadIdx.x & 31);
         if (qx >= nq) return;
+        const int k = fdiv(row, L.dy);
         if constexpr (FLUX) {
             if (!go) return;
-            prolong_quad_flux<T, OUT>(L, row, row % ny, row / ny, qx, po);
+            prolong_quad_flux<T, OUT>(L, row, row - k * ny, k, qx, po);
         } else {
-            prolong_quad<T, OUT>(L, row, row % ny, row / ny, qx, po, go);
+            prolong_quad<T, OUT>(L, row, row - k * ny, k, qx, po, go);
         }
         return;
     }
     if (!go) return;
-    const Tile t = fine_tile(L.n, lb);
+    const Tile t = fine_tile(L.n, lb, L.dxt, L.dy);
     if (!t.ok) return;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -678,7 +681,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const LevelView *__restrict_
     dep_entry();
     const int e = find_entry(start, count);
     const LevelView L = lv[e];
-    const Tile t = fine_tile(L.n, blockIdx.x - start[e]);
+    const Tile t = fine_tile(L.n, blockIdx.x - start[e], L.dxt, L.dy);
     if (!t.ok) return;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const T *x = (const T *)L.x;
@@ -825,18 +828,48 @@ __global__ void __launch_bounds__(1024) k_coarse_setup(const CoarseView *__restr
 // and coarse faces
 // ---------------------------------------------------------------------------
 
+// Conversions between FP32 and FP64 by their IEEE 754 bit fields, for positive
+// values whose exponent fits the FP32 normal range (the face set-up's case):
+// this GPU issues the F2F conversion instructions to its narrow FP64 pipe, the
+// integer forms run on the ALU.  Exponent bias 1023 (double) vs 127 (float):
+// 896 between them; double mantissa 52 bits, float 23: 29 bits dropped.
+//   widen_pos:   exact float -> double (normal positive f).
+//   trunc_pos:   double -> float, low 29 mantissa bits dropped (a seed).
+//   narrow_rn:   double -> float, round to nearest, ties to even; values
+//                outside the fast range take the hardware conversion.
+__device__ __forceinline__ double widen_pos(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    return __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
+}
+__device__ __forceinline__ float trunc_pos(unsigned hi, unsigned lo)
+{
+    return __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ float narrow_rn(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    // positive, biased exponent 897 .. 1150: a normal float (or, rounding up
+    // from the largest, the overflow to infinity that the rounding rule gives)
+    if ((hi >> 20) - 897u > 253u) return (float)d;
+    unsigned b = __float_as_uint(trunc_pos(hi, lo));
+    const unsigned rem = lo & 0x1FFFFFFFu, half = 0x10000000u;
+    b += (rem > half || (rem == half && (b & 1u))) ? 1u : 0u;  // a carry steps the exponent
+    return __uint_as_float(b);
+}
+
 // 1 / x in FP64 by Newton-Raphson iteration on f(y) = 1/y - x, y <- y + y (1 - x y),
-// from the FP32 reciprocal of x (relative error about 2^-23).  Each step squares
-// the relative error and the last one rounds once, so two steps end within
-// about one ulp of the quotient (Markstein, IBM J. Res. Dev. 34, 1990).  FP64
-// division is a long instruction sequence on this GPU's slow FP64 pipe; the
-// Newton form is 4 fused multiply-adds.  Arguments outside the FP32 range
-// divide exactly.
+// from the FP32 reciprocal of x truncated to FP32 (relative error below
+// 2^-22).  Each step squares the relative error and the last one rounds once,
+// so two steps end within about one ulp of the quotient (Markstein, IBM J.
+// Res. Dev. 34, 1990).  FP64 division is a long instruction sequence on this
+// GPU's slow FP64 pipe; the Newton form is 4 fused multiply-adds.  Arguments
+// that are not positive or lie outside [2^-125, 2^126) divide exactly.
 __device__ __forceinline__ double recip_nr(double x)
 {
-    const float xf = (float)x;
-    if (!(fabsf(xf) > 1e-37f && fabsf(xf) < 1e37f)) return 1.0 / x;
-    double y = (double)__frcp_rn(xf);
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    if ((hi >> 20) - 898u > 250u) return 1.0 / x;  // biased exponent 898 .. 1148
+    double y = widen_pos(__frcp_rn(trunc_pos(hi, lo)));
     double e = fma(-x, y, 1.0);
     y = fma(y, e, y);
     e = fma(-x, y, 1.0);
@@ -870,7 +903,7 @@ __global__ void __launch_bounds__(kThreads) k_faces_from_density(FaceArgs a)
                                 : (0.5 * a.scale[d]) * (recip_nr(rho_l) + inv_c);
             }
             if (a.out64[d]) a.out64[d][c] = v;
-            if (a.out32[d]) a.out32[d][c] = (float)v;
+            if (a.out32[d]) a.out32[d][c] = narrow_rn(v);
             if (a.out32lo[d]) a.out32lo[d][c] = (float)(v - (double)(float)v);
         }
         if (!ok && a.err) *a.err = 1;
@@ -895,7 +928,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_faces(FaceArgs a)
                 v = alpha * a.scale[d];
             }
             a.out64[d][c] = v;
-            if (a.out32[d]) a.out32[d][c] = (float)v;
+            if (a.out32[d]) a.out32[d][c] = narrow_rn(v);
             if (a.out32lo[d]) a.out32lo[d][c] = (float)(v - (double)(float)v);
         }
     }
@@ -931,7 +964,7 @@ __global__ void __launch_bounds__(kThreads) k_cell_alpha(AlphaArgs a)
         }
         const double v = m ? s / m : 1.0;
         if (a.out64) a.out64[c] = v;
-        if (a.out32) a.out32[c] = (float)v;
+        if (a.out32) a.out32[c] = narrow_rn(v);
     }
 }
 
@@ -991,10 +1024,10 @@ __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
     const int NC = a.nc[0] * a.nc[1] * a.nc[2];
     const int nx = a.nf[0], ny = a.nf[1];
     for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < NC; C += gridDim.x * blockDim.x) {
-        const int I = C % a.nc[0];
-        const int rest = C / a.nc[0];
-        const int J = rest % a.nc[1];
-        const int K = rest / a.nc[1];
+        const int rest = fdiv(C, a.dx);
+        const int I = C - rest * a.nc[0];
+        const int K = fdiv(rest, a.dy);
+        const int J = rest - K * a.nc[1];
         const int base[3] = {2 * I, 2 * J, 2 * K};
         for (int d = 0; d < 3; d++) {
             const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
@@ -1009,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
                 }
             const double w = s * 0.0625;
             a.wc[d][C] = w;
-            if (a.wc32[d]) a.wc32[d][C] = (float)w;
+            if (a.wc32[d]) a.wc32[d][C] = narrow_rn(w);
         }
     }
 }
@@ -1059,7 +1092,7 @@ __global__ void __launch_bounds__(kThreads) k_sum(const OuterView *__restrict__ 
     const bool conv = which == 1 && xp_live(O);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile);
+        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
         if (!t.ok) continue;
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {
@@ -1113,7 +1146,7 @@ __global__ void __launch_bounds__(kThreads) k_center_rhs(const OuterView *__rest
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     int nz = 0;
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile);
+        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
         if (!t.ok) continue;
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {
@@ -1143,7 +1176,7 @@ __global__ void __launch_bounds__(kThreads) k_xp_prepare(const OuterView *__rest
     const int ntiles = fine_blocks(O.n);
     const double sc = O.st->xscale;
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile);
+        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
         if (!t.ok) continue;
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {
@@ -1282,7 +1315,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_xp(const OuterView *__res
         const int n3[3] = {nx, ny, nz};
         const int ntiles = fine_blocks(n3);
         for (int tile = lb; tile < ntiles; tile += nblk) {
-            const Tile t = fine_tile(n3, tile);
+            const Tile t = fine_tile(n3, tile, O.dxt, O.xy);
             if (!t.ok) continue;
             const int rowoff = nx * t.row;
             const int j = t.j, k = t.k;
@@ -1351,7 +1384,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const OuterView *__restri
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     Te racc = Te(0);
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile);
+        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
         if (!t.ok) continue;
         const long long rowoff = (long long)nx * t.row;
         for (int h = 0; h < 2; h++) {
@@ -1441,13 +1474,15 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const OuterView *__restri
         // V-cycles of the next refinement step: inner, or (adaptive, multigrid
         // iteration) the number the last step's per-cycle reduction rate g
         // needs to reach the tolerance, taken with a 10% margin on g
+        // (FP32 logarithms: the estimate only picks a cycle count, and one
+        // thread's FP64 transcendentals are a long chain on the FP64 pipe)
         int c = O.inner;
         if (mode == 2 && O.adaptive && !O.r64 && s->rprev > 0.0) {
-            const double g = pow(rn / s->rprev, 1.0 / done);
-            if (g > 0.0 && g < 1.0) {
-                const double ge = fmin(0.95, 1.1 * g);
-                const double need = ceil(log(s->tol * s->bnorm / rn) / log(ge));
-                c = need < 1.0 ? 1 : (need < (double)O.inner ? (int)need : O.inner);
+            const float lr = logf((float)(rn / s->rprev)) / (float)done;  // log g
+            if (lr < 0.0f && isfinite(lr)) {
+                const float lge = fminf(logf(0.95f), logf(1.1f) + lr);      // log min(0.95, 1.1 g)
+                const float need = ceilf(logf((float)(s->tol * s->bnorm / rn)) / lge);
+                c = need < 1.0f ? 1 : (need < (float)O.inner ? (int)need : O.inner);
             }
         }
         const int left = s->max_iters - s->iters;  // >= 1 here
@@ -1474,7 +1509,7 @@ __global__ void __launch_bounds__(kThreads) k_final(const OuterView *__restrict_
     const bool conv = xp_live(O);
     const double inv = conv ? 1.0 / s->xscale : 1.0;  // a power of 2: exact
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile);
+        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
         if (!t.ok) continue;
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {

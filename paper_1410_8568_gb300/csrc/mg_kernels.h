@@ -73,6 +73,7 @@ struct CoarsenArgs {
     const double *wf[3];
     double *wc[3];
     float *wc32[3];
+    FastDiv dx, dy;  // division by nc[0] and by nc[1]
 };
 
 // red-black half-sweep of one colour; flags: 1 zero initial iterate (red

@@ -42,15 +42,17 @@ struct Tile {
     bool ok;
 };
 
-__device__ __forceinline__ Tile fine_tile(const int n[3], int lb)
+// (dxt divides by fine_xtiles(n[0]), dy by n[1]: multiply-shift divisions; an
+// integer division by a run-time divisor goes through float conversions, which
+// this GPU issues to its narrow FP64 pipe)
+__device__ __forceinline__ Tile fine_tile(const int n[3], int lb, const FastDiv &dxt, const FastDiv &dy)
 {
     Tile t;
-    const int xt_n = fine_xtiles(n[0]);
-    const int xt = lb % xt_n, rb = lb / xt_n;
+    const int rb = fdiv(lb, dxt), xt = lb - rb * fine_xtiles(n[0]);
     t.row = rb * kRowsPerBlock + (threadIdx.x >> 5);
     t.ok = t.row < n[1] * n[2];
-    t.j = t.ok ? t.row % n[1] : 0;
-    t.k = t.ok ? t.row / n[1] : 0;
+    t.k = t.ok ? fdiv(t.row, dy) : 0;
+    t.j = t.ok ? t.row - t.k * n[1] : 0;
     t.xbase = xt * kSeg;
     return t;
 }

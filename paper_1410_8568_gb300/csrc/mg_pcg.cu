@@ -28,7 +28,7 @@ __device__ __forceinline__ void for_cells(const OuterView &O, int lb, F &&f)
 {
     const int ntiles = fine_blocks(O.n);
     for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile);
+        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
         if (!t.ok) continue;
         const long long rowoff = (long long)O.n[0] * t.row;
         for (int h = 0; h < 2; h++) {

@@ -60,6 +60,10 @@ void fill_fastdiv(LevelView &v)
     v.dy = make_fastdiv(v.n[1] >= 1 ? (unsigned)v.n[1] : 1u);
     v.dp = make_fastdiv(v.nc[0] >= 2 ? (unsigned)(v.nc[0] >> 1) : 1u);
     v.dcy = make_fastdiv(v.nc[1] >= 1 ? (unsigned)v.nc[1] : 1u);
+    v.dxq = make_fastdiv((unsigned)(((v.n[0] >> 2) + 31) >> 5 > 0 ? ((v.n[0] >> 2) + 31) >> 5 : 1));
+    v.dxp = make_fastdiv((unsigned)(((v.nc[0] >> 1) + 31) >> 5 > 0 ? ((v.nc[0] >> 1) + 31) >> 5 : 1));
+    v.dxc = make_fastdiv((unsigned)(coarse_xtiles(v.nc[0]) > 0 ? coarse_xtiles(v.nc[0]) : 1));
+    v.dxt = make_fastdiv((unsigned)(fine_xtiles(v.n[0]) > 0 ? fine_xtiles(v.n[0]) : 1));
 }
 
 int kernel_blocks(int kind, const int n[3], const int nc[3], int v)

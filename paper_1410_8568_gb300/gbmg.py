@@ -102,6 +102,7 @@ def lib():
             "mg_num_levels": (_I, [_V, _P(_I)]),
             "mg_level_shape": (_I, [_V, _I, _P(_I), _P(_I), _P(_I)]),
             "mg_level_faces": (_I, [_V, _I, _V, _V, _V]),
+            "mg_level_faces32": (_I, [_V, _I, _V, _V, _V]),
             "mg_level_cell_alpha": (_I, [_V, _I, _V]),
             "mg_divergence": (_I, [_V, _V, _V, _V, _D, _V]),
             "mg_project": (_I, [_V, _V, _D, _V, _V, _V]),
@@ -408,6 +409,15 @@ class Solver:
         nx, ny, nz = self.level_shape(level)
         out = [torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
         check(lib().mg_level_faces(self._h, int(level), *[_ptr(o) for o in out]), "mg_level_faces")
+        return out
+
+    def level_faces32(self, level):
+        """FP32 copies of the level's scaled faces (mixed-precision handles)."""
+        import torch
+
+        nx, ny, nz = self.level_shape(level)
+        out = [torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda") for _ in range(3)]
+        check(lib().mg_level_faces32(self._h, int(level), *[_ptr(o) for o in out]), "mg_level_faces32")
         return out
 
     def level_cell_alpha(self, level):

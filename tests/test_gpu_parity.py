@@ -64,6 +64,35 @@ def test_faces_from_density(make, mode):
         np.testing.assert_allclose(host(out[d]), want[d], rtol=2e-15, atol=0)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp32_faces_are_rounded_fp64_faces(mode):
+    """The FP32 faces of every level of a mixed handle (the set-up converts them
+    with integer bit operations) equal the FP64 faces rounded to nearest, ties
+    to even, bit for bit: faces given by the caller (values over 30 orders of
+    magnitude and values exactly halfway between two floats; the scale 1/h^2
+    is a power of 2, so the ties survive it, and the coarse faces, means of 4,
+    make more), then faces from a density (harmonic or arithmetic mean)."""
+    shape, bc = (32, 32, 64), (1, 0, 1)
+    rng = np.random.default_rng(7)
+    alpha = [10.0 ** rng.uniform(-15, 15, size=cells(shape)) for _ in range(3)]
+    for a in alpha:
+        a.flat[::7] = 1.0 + 2.0 ** -24        # tie: rounds down to even
+        a.flat[3::7] = 1.0 + 3 * 2.0 ** -24   # tie: rounds up to even
+        a.flat[5::11] = 2.0 ** -30 * (1.0 + 2.0 ** -24)
+    rho = 10.0 ** rng.uniform(-15, 15, size=cells(shape))
+
+    def check(S):
+        for lvl in range(S.num_levels()):
+            w64, w32 = S.level_faces(lvl), S.level_faces32(lvl)
+            for d in range(3):
+                assert torch.equal(w32[d], w64[d].float()), (lvl, d)
+
+    with gbmg.Solver(shape, bc, faces=[dev(a) for a in alpha], precision=gbmg.MIXED) as S:
+        check(S)
+        S.set_density(dev(rho), mode=mode)
+        check(S)
+
+
 @pytest.mark.parametrize("shape,bc", [((32, 32, 32), (0, 0, 0)), ((48, 24, 96), (1, 1, 0)), ((64, 48, 32), (1, 0, 1))])
 def test_level_faces_match_oracle_coarsening(shape, bc):
     P = random_problem(shape, bc, 1000.0, 1)
