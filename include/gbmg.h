@@ -213,9 +213,17 @@ int mg_set_density(mg_handle *h, const double *rho, int mode);
  * rhs).  rhs and p are DEVICE arrays of nx*ny*nz doubles (p 16-byte aligned,
  * as every cudaMalloc/torch allocation is); p is the starting
  * iterate on entry (warm start; zeros for a cold start) and the zero-mean
- * solution on exit.  rhs is not modified.  Synchronous: returns when the solve
- * has finished on the handle's stream.  `st` may be NULL.  Returns MG_OK,
- * MG_ENOTCONV or MG_EDIVERGED (p then holds the last iterate) or an error. */
+ * solution on exit.  A starting p that is zero in every cell (+0 or -0) is
+ * detected on the device and its starting residual taken as rhs - mean(rhs)
+ * without the product A p (multigrid iteration; the result is bitwise that of
+ * the full evaluation).  rhs is not modified.  Synchronous: returns when the
+ * solve has finished on the handle's stream.  `st` may be NULL.  Returns MG_OK,
+ * MG_ENOTCONV or MG_EDIVERGED (p then holds the last iterate) or an error.
+ *
+ * Consecutive kernels of a solve are launched with programmatic dependent
+ * launch (each kernel's blocks are placed while the previous kernel runs and
+ * wait for its completion before their first memory access); the environment
+ * variable MG_DEP_LAUNCH=0, read once per process, turns that off. */
 int mg_solve(mg_handle *h, const double *rhs, double *p, double tol, mg_stats *st);
 
 /* Same as mg_solve with HOST arrays (pinned or pageable): copies rhs and the
