@@ -489,8 +489,10 @@ Prof::~Prof()
 // from a zero correction: their first red half-sweep, which reads only b and
 // the faces, is done by the restriction that produces b.  The finest
 // level starts from zero in the first cycle of a step and from the previous
-// cycle's correction in the next ones.  outer: in the grid's last cycle of the
-// step, the last black half-sweep on the finest level also adds the correction
+// cycle's correction in the next ones.  outer: this cycle may end a grid's
+// step (the caller passes it for every cycle of a plan of several grids, for
+// the last cycle only of a lone grid's); in the grid's last cycle of the step,
+// the last black half-sweep on the finest level then also adds the correction
 // (both colours) to the outer iterate (the prolongation does if nu2 = 0, the
 // coarse solve if the grid has one level).
 template <class T>
