@@ -66,6 +66,11 @@ def test_host_only_calls():
     assert e.value.code == gbmg.EINVAL
     with pytest.raises(gbmg.MGError):
         gbmg.memory_estimate((1, 8, 8), (0, 0, 0))
+    # level read-back without a handle is refused before any device call
+    buf = (ctypes.c_double * 8)()
+    fbuf = (ctypes.c_float * 8)()
+    assert L.mg_level_faces(None, 0, buf, buf, buf) == gbmg.EINVAL
+    assert L.mg_level_faces32(None, 0, fbuf, fbuf, fbuf) == gbmg.EINVAL
 
 
 def test_tile_shapes_and_params():
