@@ -126,3 +126,23 @@ def test_no_gpu_fails_loudly():
         pytest.skip("a GPU is present")
     with pytest.raises(Exception):
         gbmg.Solver((8, 8, 8), (0, 0, 0), faces=[torch.ones(512, dtype=torch.float64)] * 3)
+
+
+def test_every_launched_kernel_waits_for_its_predecessor_first():
+    """A launch with programmatic stream serialization (launch_k inside a
+    dependent-launch scope) may be scheduled while the previous kernel runs, so
+    every kernel of a source file that launches through launch_k must begin
+    with dep_entry() (griddepcontrol.wait) before any other statement."""
+    import glob
+
+    csrc = os.path.join(os.path.dirname(gbmg.__file__), "csrc")
+    checked = 0
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu"))):
+        src = open(path).read()
+        if "launch_k(" not in src:
+            continue
+        for m in re.finditer(r"__global__[^;{]*\{", src):
+            first = src[m.end():].lstrip().split("\n", 1)[0].strip()
+            assert first == "dep_entry();", (os.path.basename(path), src[m.start():m.end()][:90])
+            checked += 1
+    assert checked >= 30
