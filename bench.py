@@ -46,6 +46,9 @@ import numpy as np  # noqa: E402
 METRIC = "Poisson MG solves/s to 1e-10 rel. residual, mixed vs FP64 on GB300; p50/p99 ms"
 TOL = 1e-10
 L2_FLUSH_BYTES = 256 << 20
+# largest grid whose oracle p* the bench computes on the host (512^3: about a
+# minute on 16 cores and ~10 GB of host memory)
+ORACLE_MAX_CELLS = 512 ** 3
 
 WORKLOADS = {
     "drop_film_128": dict(kind="config2", n=128,
@@ -149,6 +152,11 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.windows = []
+
+    def window(self, t0, t1):
+        """Keep the samples taken between wall times t0 and t1 (time.time())."""
+        self.windows.append((t0, t1))
 
     def start(self):
         try:
@@ -162,7 +170,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def stop(self):
         if self.proc is None:
@@ -175,7 +183,9 @@ class ClockSampler:
         self.t.join(timeout=5)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for ts, line in self.lines:
+            if self.windows and not any(a <= ts <= b for a, b in self.windows):
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -189,7 +199,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "sampled": "every 200 ms, kept inside the timed regions (%d windows)" % len(self.windows)}
 
 
 def level_shapes(shape):
@@ -232,28 +243,66 @@ def cpu_oracle_solve(P, faces, tol=TOL):
     return time.perf_counter() - t, r
 
 
+def single_config(args, P, world):
+    """config of the single-grid workloads (both arms)."""
+    return {"workload": WORKLOADS[args.workload]["desc"], "grid": list(P.shape),
+            "bc": list(P.bc), "density_ratio": P.ratio, "tol": TOL,
+            "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
+            "prolongation": args.prolongation, "solver": args.solver,
+            "step": "set density (faces, coarse faces, coarsest inverse) + cold-start solve",
+            "l2": "flushed before every step (256 MB write, outside the step events)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+# grids above this size time the oracle by single V-cycles (a whole 512^3
+# oracle solve takes about a minute on 16 cores)
+REFERENCE_WHOLE_SOLVE_CELLS = 128 ** 3
+
+
 def run_reference(args, name):
-    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores.
+    Small grids: one whole oracle solve to 1e-10 per step.  Larger grids: one
+    oracle solve to 1e-10 first (untimed: it gives the cycles C a solve
+    needs), then every step is one oracle call of a single V(2,2) cycle (with
+    its set-up and residual norms), and solves/s = 1 / (C x mean step time)."""
     import oracle
     P = make_problem(name)
     faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
     cores = oracle.num_threads()
+    whole = P.cells <= REFERENCE_WHOLE_SOLVE_CELLS
+    if not whole:
+        t_full, r = cpu_oracle_solve(P, faces)
+        C = r.cycles
     times = []
     for s in range(args.warmup + args.steps):
-        dt, r = cpu_oracle_solve(P, faces)
+        if whole:
+            dt, r = cpu_oracle_solve(P, faces)
+        else:
+            t = time.perf_counter()
+            oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=1)
+            dt = time.perf_counter() - t
         if s >= args.warmup:
             times.append(dt)
     tot = sum(times)
-    value = len(times) / tot
+    if whole:
+        value = len(times) / tot
+        sample = "%d whole FP64 oracle solves of the workload to 1e-10 (%d V(2,2) cycles each)" % (
+            len(times), r.cycles)
+        solve_s = [t for t in times]
+    else:
+        value = len(times) / (tot * C)
+        sample = ("%d oracle calls of one V(2,2) cycle each (set-up and residual norms included) on the "
+                  "workload; a whole oracle solve to 1e-10 needs %d cycles (measured once before the "
+                  "steps: %.1f s); solves/s = 1 / (%d x mean step time)" % (len(times), C, t_full, C))
+        solve_s = [t * C for t in times]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[name]["desc"], "grid": list(P.shape), "tol": TOL},
-        "p50_ms": 1000.0 * statistics.median(times), "p99_ms": 1000.0 * float(np.percentile(times, 99)),
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d full FP64 oracle solves of the workload to 1e-10 (%d V(2,2) cycles each)" %
-                                   (len(times), r.cycles)},
+        "config": single_config(args, P, args.gpus),
+        "p50_ms": 1000.0 * statistics.median(solve_s), "p99_ms": 1000.0 * float(np.percentile(solve_s, 99)),
+        "latency": "per solve (whole solves, or C x the one-cycle step time)",
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -414,7 +463,9 @@ def run_batch(args, rank, world, local_rank, dist):
 
 
 def run_serve(args, rank, world, local_rank, dist):
-    """Poisson-arrival request stream through the continuous-batching server."""
+    """Poisson-arrival request stream through the continuous-batching server:
+    for each offered load (a fraction of the measured capacity of the mixed
+    path), the same seeded stream of requests in mixed precision and in FP64."""
     import torch
 
     from paper_1410_8568_gb300 import gbmg
@@ -424,9 +475,13 @@ def run_serve(args, rank, world, local_rank, dist):
     # one field per (edge, ratio bucket); the stream's ratios are log-uniform in
     # [10, 1000] and are mapped to the nearest of 10, 100, 1000
     buckets = (10.0, 100.0, 1000.0)
+
+    def bucket(ratio):
+        return min(buckets, key=lambda b: abs(math.log(b) - math.log(ratio)))
+
     fields, rhs_of = {}, {}
     for _, n, ratio, seed in stream_spec:
-        rb = min(buckets, key=lambda b: abs(math.log(b) - math.log(ratio)))
+        rb = bucket(ratio)
         if (n, rb) in fields:
             continue
         shape = (n, n, n)
@@ -439,44 +494,35 @@ def run_serve(args, rank, world, local_rank, dist):
         fields[(n, rb)] = (shape, I.DROP_FILM_BC, faces, rhs_of[n])
         del rho
     torch.cuda.synchronize()
-    res = {}
-    for prec in (gbmg.MIXED, gbmg.FP64):
-        # service time of each edge alone (new coefficients + cold-start solve, as
-        # a request costs the server): sets the arrival rate, 0.8 x the capacity
-        # of the mixed path
-        if prec == gbmg.MIXED:
-            svc = {}
-            for (n, rb), (shape, bc, faces, rhs) in fields.items():
-                if n in svc:
-                    continue
-                with gbmg.Solver(shape, bc, faces=faces, precision=prec) as S:
-                    p = torch.zeros_like(rhs)
-                    S.solve(rhs, p)
-                    torch.cuda.synchronize()
-                    t = time.perf_counter()
-                    S.set_faces(*faces)
-                    S.solve(rhs, p.zero_())
-                    svc[n] = time.perf_counter() - t
-            mean_svc = sum(svc[n] for _, n, _, _ in stream_spec) / len(stream_spec)
-            rate = 0.8 / mean_svc
-        # the autotuner times each new level size once per process: create one
-        # handle per size first, so no request of the stream pays for tuning
-        for n in sorted({n for _, n, _, _ in stream_spec}):
-            (shape, bc, faces, _), = [v for (m, _), v in fields.items() if m == n][:1]
-            gbmg.Solver(shape, bc, faces=faces, precision=prec).close()
+    sizes = sorted({n for _, n, _, _ in stream_spec})
+
+    def solo_times(prec):
+        """Service time of each edge alone (new coefficients + cold-start solve,
+        as a request costs the server), the launch shapes tuned first."""
+        svc = {}
+        for n in sizes:
+            (shape, bc, faces, rhs), = [v for (m, _), v in fields.items() if m == n][:1]
+            with gbmg.Solver(shape, bc, faces=faces, precision=prec) as S:
+                p = torch.zeros_like(rhs)
+                S.solve(rhs, p)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                S.set_faces(*faces)
+                S.solve(rhs, p.zero_())
+                svc[n] = time.perf_counter() - t
+        return svc
+
+    def run_stream(prec, rate):
         srv = gbmg.Server(hbm_budget_bytes=args.hbm_budget << 30, max_slots=args.slots, precision=prec)
-        outs, tickets, lat = [], [], []
-        t0 = time.perf_counter()
         arrivals = [a / rate for a, _, _, _ in stream_spec]
-        pending = {}
-        k = 0
-        done = 0
+        pending, lat = {}, []
+        k = done = 0
+        t0 = time.perf_counter()
         while done < len(stream_spec):
             now = time.perf_counter() - t0
             while k < len(stream_spec) and arrivals[k] <= now:
                 _, n, ratio, seed = stream_spec[k]
-                rb = min(buckets, key=lambda b: abs(math.log(b) - math.log(ratio)))
-                shape, bc, faces, rhs = fields[(n, rb)]
+                shape, bc, faces, rhs = fields[(n, bucket(ratio))]
                 p = torch.zeros_like(rhs)
                 torch.cuda.synchronize()
                 pending[srv.submit(shape, bc, faces, rhs, p, tol=TOL)] = (p, n)
@@ -487,77 +533,93 @@ def run_serve(args, rank, world, local_rank, dist):
                     rc, st = r
                     if rc != gbmg.OK:
                         raise RuntimeError("served solve failed: %s" % gbmg.strerror(rc))
-                    lat.append(st.ms)
-                    pending.pop(t)
+                    lat.append((pending.pop(t)[1], st.ms))
                     done += 1
             time.sleep(0.0002)
         wall = time.perf_counter() - t0
         info = srv.info()
         srv.close()
-        res[prec] = dict(value=len(stream_spec) / wall, p50=statistics.median(lat),
-                         p99=float(np.percentile(lat, 99)), wall=wall, info=info)
+        ms = [v for _, v in lat]
+        per_size = {}
+        for n in sizes:
+            v = [m for e, m in lat if e == n]
+            if v:
+                per_size["%d^3" % n] = {"requests": len(v), "p50_ms": statistics.median(v),
+                                        "p99_ms": float(np.percentile(v, 99))}
+        return {"value": len(stream_spec) / wall, "wall_s": wall, "p50_ms": statistics.median(ms),
+                "p99_ms": float(np.percentile(ms, 99)), "max_in_flight": info["max_in_flight"],
+                "peak_bytes": info["peak_bytes"], "per_size": per_size}
+
+    svc = solo_times(gbmg.MIXED)
+    mean_svc = sum(svc[n] for _, n, _, _ in stream_spec) / len(stream_spec)
+    capacity = 1.0 / mean_svc
+    solo_fp64 = solo_times(gbmg.FP64)
+    runs = {}
+    for load in args.load:
+        rate = load * capacity
+        runs[load] = {"arrival_rate_per_s": rate,
+                      "mixed": run_stream(gbmg.MIXED, rate), "fp64": run_stream(gbmg.FP64, rate)}
     if rank == 0:
-        m, f = res[gbmg.MIXED], res[gbmg.FP64]
-        line = _line(args, world, args.workload, m["value"], 1000.0 * m["wall"] / len(stream_spec), m["p50"], m["p99"], {
-            "serve": {"requests": len(stream_spec), "arrival_rate_per_s": rate,
-                      "rate_rule": "0.8 x capacity of the mixed path (mean solo time of new coefficients + solve over the stream's sizes)",
-                      "slots": args.slots, "hbm_budget_gib": args.hbm_budget,
-                      "peak_bytes": m["info"]["peak_bytes"], "max_in_flight": m["info"]["max_in_flight"],
+        head = runs[0.8] if 0.8 in runs else runs[args.load[0]]
+        m, f = head["mixed"], head["fp64"]
+        loads = {("%g" % k): v for k, v in runs.items()}
+        line = _line(args, world, args.workload, m["value"], 1000.0 * m["wall_s"] / len(stream_spec),
+                     m["p50_ms"], m["p99_ms"], {
+            "serve": {"requests": len(stream_spec), "slots": args.slots, "hbm_budget_gib": args.hbm_budget,
+                      "capacity_solves_per_s": capacity,
+                      "capacity_rule": "1 / mean solo service time (new coefficients + cold-start solve) of "
+                                       "the stream's requests, mixed path",
+                      "solo_ms": {"%d^3" % n: 1000.0 * v for n, v in svc.items()},
+                      "solo_fp64_ms": {"%d^3" % n: 1000.0 * v for n, v in solo_fp64.items()},
+                      "headline_load": 0.8 if 0.8 in runs else args.load[0],
                       "latency": "submission to completion, ms",
-                      "tuning": "launch shapes of every size tuned before the stream starts"},
-            "fp64": {"value": f["value"], "unit": "solves/s", "p50_ms": f["p50"], "p99_ms": f["p99"],
-                     "max_in_flight": f["info"]["max_in_flight"]},
+                      "lanes": "size lanes of up to 64^3, 128^3, 256^3 and larger grids, one stream each, "
+                               "smaller grids at higher stream priority",
+                      "tuning": "launch shapes of every size tuned before the stream starts",
+                      "loads": loads},
+            "fp64": {"value": f["value"], "unit": "solves/s", "p50_ms": f["p50_ms"], "p99_ms": f["p99_ms"]},
             "mixed_over_fp64": m["value"] / f["value"],
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None})
         print(json.dumps(line))
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="drop_film_128", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prolongation", default="trilinear", choices=["trilinear", "flux"],
-                    help="prolongation of the V-cycle: trilinear or flux-conserving (Sec. 2.3 item 4)")
-    ap.add_argument("--solver", default="mg", choices=["mg", "pcg"],
-                    help="outer iteration: V-cycles in FP64 refinement (mg) or V-cycle-preconditioned CG (pcg)")
-    ap.add_argument("--requests", type=int, default=200, help="serve_stream: requests in the stream")
-    ap.add_argument("--slots", type=int, default=8, help="serve_stream: most requests on the GPU at once")
-    ap.add_argument("--hbm-budget", type=int, default=64, help="serve_stream: GiB of device memory for hierarchies")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
+# Algorithmic bytes per finest cell of the level-0 kernels (FP32 cycle, s = 4 B):
+# a full red + black sweep reads x, b and the 3 face arrays and writes x (6 s),
+# so each of its two half-sweep launches counts half of that; the residual +
+# restriction reads x, b, 3 faces and writes r/8 (5.125 s); the prolongation +
+# correction reads e/8 and reads and writes x (2.125 s).
+ALG_BPC = {"half": 12.0, "restrict": 20.5, "prolong": 8.5}
+# Bytes the unfused kernels actually move per finest cell: a half-sweep reads
+# all of x and the 3 face arrays, the colour's sectors of b (the whole b: the
+# two cells of a colour share the quad's sector) and writes the quad (x).
+ACT_BPC = {"half": 20.0}
+# FP64 residual of a refinement step: reads p, b - mean b and 3 FP64 faces,
+# writes the FP32 residual (44 B); 6 differences, 1 product and 5 fused
+# multiply-adds, the subtraction from b and the scale (14 FP64 operations) and
+# the FP64 -> FP32 conversion, which this GPU also issues to its FP64 pipe.
+RES_BPC, RES_FP64_OPS = 44.0, 15.0
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
-    if args.impl == "reference":
-        if rank == 0:
-            run_reference(args, args.workload)
-        return
+def oracle_reference_run(P, tol=TOL):
+    """The oracle's p* (iterated to rounding level) and the time it took:
+    (p*, seconds, cycles run, cycles that reached tol)."""
+    import oracle
+    faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
+    t = time.perf_counter()
+    r = oracle.solve_exact(P.shape, P.bc, faces, P.rhs)
+    dt = time.perf_counter() - t
+    hist = r.history
+    reach = next((k for k in range(len(hist)) if hist[k] <= tol * r._bnorm), len(hist) - 1)
+    return r.x, dt, r.cycles, reach
 
+
+def run_single(args, rank, world, local_rank, dist):
+    """One grid per step: new density in, cold-start solve to 1e-10 (mixed,
+    FP64, extended-precision outer iteration), end to end through the host
+    entry point, per-launch timing of the level-0 kernels."""
     import torch
 
     from paper_1410_8568_gb300 import gbmg
-
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    import __graft_entry__
-    __graft_entry__.build()
-
-    if WORKLOADS[args.workload]["kind"] == "batch":
-        return run_batch(args, rank, world, local_rank, dist)
-    if WORKLOADS[args.workload]["kind"] == "serve":
-        return run_serve(args, rank, world, local_rank, dist)
-    if WORKLOADS[args.workload]["kind"] == "projection":
-        return run_projection(args, rank, world, local_rank, dist)
 
     P = make_problem(args.workload)
     N = P.cells
@@ -567,13 +629,16 @@ def main():
     rhs = rhs_h.cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.Stream()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
 
-    def timed(solver, steps, host=False):
+    def timed(solver, steps, host=False, window=False):
         """Per-step device times (ms) and the last stats."""
         p = torch.zeros_like(rhs)
         ph = torch.zeros(P.rho.shape, dtype=torch.float64).pin_memory()
-        times, st = [], None
+        st = None
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = time.time()
         with torch.cuda.stream(stream):
             for s in range(steps):
                 flush.fill_(float(s))
@@ -592,6 +657,8 @@ def main():
                 if st.status != gbmg.OK:
                     raise RuntimeError("solve failed: %s" % gbmg.strerror(st.status))
             stream.synchronize()
+        if window:
+            clocks.window(t0, time.time())
         times = [a.elapsed_time(b) for a, b in ev]
         return times, st, p
 
@@ -611,24 +678,16 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks = ClockSampler(local_rank) if key == "mixed" else None
-        if clocks:
-            clocks.start()
-        t0 = time.perf_counter()
-        times, st, p = timed(S, args.steps)
-        wall = time.perf_counter() - t0
+        times, st, p = timed(S, args.steps, window=True)
         torch.cuda.synchronize()
-        if clocks:
-            results["clocks"] = clocks.stop()
-        tot = sum(times)
-        tot = reduce_max(tot, dist)
+        tot = reduce_max(sum(times), dist)
         # host copy of the last step's result, taken at once for the oracle comparison
-        x_host = p.cpu().numpy().copy() if (rank == 0 and N <= 128 ** 3) else None
+        x_host = p.cpu().numpy().copy() if (rank == 0 and N <= ORACLE_MAX_CELLS) else None
         results[key] = dict(ms=tot / args.steps, value=job_value(world, args.steps, tot),
                             p50=statistics.median(times), p99=float(np.percentile(times, 99)),
-                            iters=st.iters, gamma=st.gamma, rel_res=st.rel_res, wall=wall,
+                            iters=st.iters, gamma=st.gamma, rel_res=st.rel_res,
                             levels=S.num_levels(), x=x_host, inner=S.resolved_params()["inner_cycles"],
-                            steps=st.steps)
+                            refine_steps=st.steps)
         if key == "mixed_xp":
             # its residual kernel, per-launch events (NVTX range for a profiler:
             # ncu --nvtx --nvtx-include "profile_pass_xp/")
@@ -648,23 +707,12 @@ def main():
             S.close()  # frees its hierarchy before the next one is built
             del solvers[key]
 
-    # error of each result against the FP64 oracle's converged solution (small grids only)
-    errors = {}
-    if rank == 0 and N <= 128 ** 3:
-        import oracle
-        faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
-        pstar = oracle.solve_exact(P.shape, P.bc, faces, P.rhs).x
-        for key in results:
-            if key != "clocks":
-                x = results[key]["x"]
-                errors[key] = float(np.linalg.norm(x - pstar) / np.linalg.norm(pstar))
-
     # end to end through the host entry point (pinned buffers, copies inside)
     S = solvers["mixed"]
     timed(S, 2, host=True)
-    e2e_times, _, _ = timed(S, args.steps, host=True)
-    e2e_tot = sum(e2e_times)
-    e2e_tot = reduce_max(e2e_tot, dist)
+    e2e_times, _, _ = timed(S, args.steps, host=True, window=True)
+    e2e_tot = reduce_max(sum(e2e_times), dist)
+    clock_rec = clocks.stop()
 
     # roofline of the dominant kernel: finest-level half-sweep, per-launch events
     v0 = S.tile_choice(gbmg.TILE_HALF, 0)
@@ -682,105 +730,158 @@ def main():
         torch.cuda.nvtx.range_pop()
     n_l, ms_l = S.profile_read(gbmg.K_SMOOTH, 0)
     n_r, ms_r = S.profile_read(gbmg.K_RESIDUAL, 0)
-    # the other level-0 kernels of the cycle, algorithmic bytes per finest cell:
-    # restriction reads x, b, 3 faces (FP32) and writes the coarse b (1/8 cell);
-    # prolongation reads and writes x and reads the coarse correction (1/8);
-    # the FP64 residual reads p, b0 and 3 FP64 faces and writes r (FP32)
+    peak, peak_kind = read_peaks()
     per_kernel = {}
-    for name, kind, bpc, bound in (("restrict", gbmg.K_RESTRICT, 20.5, "hbm"),
-                                   ("prolong", gbmg.K_PROLONG, 8.5, "hbm"),
-                                   ("residual_fp64", gbmg.K_RESIDUAL, 44.0, "fp64 alu")):
+    for name, kind in (("restrict", gbmg.K_RESTRICT), ("prolong", gbmg.K_PROLONG)):
         n_k, ms_k = S.profile_read(kind, 0)
         if n_k:
             us = 1000.0 * ms_k / n_k
-            per_kernel[name] = {"avg_launch_us": us, "bytes_per_launch": bpc * N,
-                                "achieved_gbs": bpc * N / (us * 1e3), "bound": bound}
+            b = ALG_BPC[name] * N
+            per_kernel[name] = {"avg_launch_us": us, "algorithmic_bytes_per_launch": b,
+                                "achieved_gbs": b / (us * 1e3), "frac": b / (us * 1e3) / peak, "bound": "hbm"}
     S.profile(False)
+    fp64_rate = gbmg.probe_fp64_rate(stream=stream)
+    res_us = 1000.0 * ms_r / max(1, n_r)
+    residual = {"avg_launch_us": res_us, "launches_timed": n_r,
+                "bytes_per_launch": RES_BPC * N, "achieved_gbs": RES_BPC * N / (res_us * 1e3),
+                "hbm_frac": RES_BPC * N / (res_us * 1e3) / peak,
+                "fp64_ops_per_cell": RES_FP64_OPS,
+                "fp64_ops_per_s": RES_FP64_OPS * N / (res_us * 1e-6),
+                "fp64_frac": RES_FP64_OPS * N / (res_us * 1e-6) / fp64_rate,
+                "bound": "fp64 pipe (min of HBM and FP64 issue rate: the larger fraction)"}
     avg_s = ms_l / n_l / 1000.0
-    # FP32 half-sweep, algorithmic: read x (all cells), b of the colour (half),
-    # the 3 face arrays (every face borders one cell of each colour), write the colour (half)
-    bytes_launch = (4 + 2 + 12 + 2) * N
-    peak, peak_kind = read_peaks()
+    bytes_launch = ALG_BPC["half"] * N
     achieved = bytes_launch / avg_s / 1e9
     traffic = profiled_traffic(args.workload)
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    # error of each result against the FP64 oracle's converged solution p*, and
+    # the oracle's own time (its p* run: mean cycle time x the cycles it needed
+    # to reach the tolerance)
+    errors, cpu = {}, None
+    if rank == 0 and N <= ORACLE_MAX_CELLS:
+        import oracle
+        pstar, dt, ncyc, reach = oracle_reference_run(P)
+        nrm = np.linalg.norm(pstar)
+        for key in ("mixed", "fp64", "mixed_xp"):
+            if key in results:
+                errors[key] = float(np.linalg.norm(results[key]["x"] - pstar) / nrm)
+        if not args.no_cpu_baseline:
+            t_solve = dt / ncyc * reach
+            cpu = {"value": 1.0 / t_solve, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": "the oracle's p* run on this workload (%d V(2,2) cycles to rounding level, %.1f s), "
+                             "timed; solves/s = 1 / (mean cycle time x the %d cycles that reached 1e-10)" %
+                             (ncyc, dt, reach)}
+    elif rank == 0 and not args.no_cpu_baseline:
         import oracle
         faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
-        if N <= 128 ** 3:
-            dt, r = cpu_oracle_solve(P, faces)
-            cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
-                   "sample": "1 full FP64 oracle solve of the workload to 1e-10 (%d V(2,2) cycles)" % r.cycles}
-            # the same on one host core: 2 cycles, scaled to the solve's cycles
-            cores = oracle.num_threads()
-            oracle.set_threads(1)
-            t = time.perf_counter()
-            oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=2)
-            dt1 = (time.perf_counter() - t) * r.cycles / 2.0
-            oracle.set_threads(cores)
-            cpu["single_core"] = {"value": 1.0 / dt1, "unit": "solves/s", "ms_per_solve": 1000.0 * dt1,
-                                  "sample": "2 oracle V(2,2) cycles on 1 thread, scaled to %d cycles" % r.cycles}
-        else:
-            # bounded sample: 2 oracle cycles, scaled by the GPU solve's cycle count
-            t = time.perf_counter()
-            r = oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=2)
-            dt = (time.perf_counter() - t) * results["fp64"]["iters"] / 2.0
-            cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
-                   "sample": "2 FP64 oracle V(2,2) cycles of the workload, scaled to %d cycles per solve" %
-                             results["fp64"]["iters"]}
+        t = time.perf_counter()
+        oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=2)
+        dt = (time.perf_counter() - t) * results["fp64"]["iters"] / 2.0
+        cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "2 FP64 oracle V(2,2) cycles of the workload, scaled to %d cycles per solve" %
+                         results["fp64"]["iters"]}
 
     if rank == 0:
         m, f = results["mixed"], results["fp64"]
-        launches = args.steps * count_launches(P.shape, m["iters"], m["steps"], inner=m["inner"],
+        launches = args.steps * count_launches(P.shape, m["iters"], m["refine_steps"], inner=m["inner"],
                                                pcg=args.solver == "pcg")
+        xp = results.get("mixed_xp")
         line = {
             "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "grid": list(P.shape),
-                       "bc": list(P.bc), "density_ratio": P.ratio, "tol": TOL,
-                       "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
-                       "prolongation": args.prolongation, "solver": args.solver,
-                       "step": "set density (faces, coarse faces, coarsest inverse) + cold-start solve",
-                       "l2": "flushed before every step (256 MB write, outside the step events)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": single_config(args, P, world),
             "p50_ms": m["p50"], "p99_ms": m["p99"],
-            "iters": m["iters"], "steps": m["steps"], "inner_cycles": m["inner"], "gamma": m["gamma"],
-            "rel_res": m["rel_res"],
+            "iters": m["iters"], "refine_steps": m["refine_steps"], "inner_cycles": m["inner"],
+            "gamma": m["gamma"], "rel_res": m["rel_res"],
             "err_vs_oracle": errors.get("mixed"),
             "fp64": {"value": f["value"], "unit": "solves/s", "ms_per_step": f["ms"], "p50_ms": f["p50"],
-                     "p99_ms": f["p99"], "iters": f["iters"], "steps": f["steps"], "inner_cycles": f["inner"], "gamma": f["gamma"], "rel_res": f["rel_res"],
+                     "p99_ms": f["p99"], "iters": f["iters"], "refine_steps": f["refine_steps"],
+                     "inner_cycles": f["inner"], "gamma": f["gamma"], "rel_res": f["rel_res"],
                      "err_vs_oracle": errors.get("fp64")},
             "mixed_over_fp64": m["value"] / f["value"],
-            "mixed_xp": None if "mixed_xp" not in results else {
+            "mixed_xp": None if xp is None else {
                 "precision": "FP32 V(2,2) cycles in the extended-precision outer iteration (three-float "
                              "iterate, float-pair faces and b, error-free FP32 residual; FP64 only in "
                              "the set-up and final conversion)",
-                "value": results["mixed_xp"]["value"], "unit": "solves/s", "ms_per_step": results["mixed_xp"]["ms"],
-                "p50_ms": results["mixed_xp"]["p50"], "p99_ms": results["mixed_xp"]["p99"],
-                "iters": results["mixed_xp"]["iters"], "steps": results["mixed_xp"]["steps"],
-                "rel_res": results["mixed_xp"]["rel_res"], "err_vs_oracle": errors.get("mixed_xp"),
-                "residual_avg_launch_us": results["mixed_xp"]["residual_avg_launch_us"],
-                "over_mixed": results["mixed_xp"]["value"] / m["value"]},
+                "value": xp["value"], "unit": "solves/s", "ms_per_step": xp["ms"],
+                "p50_ms": xp["p50"], "p99_ms": xp["p99"], "iters": xp["iters"],
+                "refine_steps": xp["refine_steps"], "rel_res": xp["rel_res"],
+                "err_vs_oracle": errors.get("mixed_xp"),
+                "residual_avg_launch_us": xp["residual_avg_launch_us"],
+                "over_mixed": xp["value"] / m["value"]},
+            "err_note": None if errors else "oracle p* not computed above %d cells" % ORACLE_MAX_CELLS,
             "e2e": {"value": job_value(world, args.steps, e2e_tot), "unit": "solves/s",
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "FP32 half-sweep of level 0 (one red or black colour), launch shape %d "
                                    "(%d threads x %d quads)" % ((v0,) + gbmg.tile_shape(v0)),
-                         "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
-                         "launches_timed": n_l, "peak_source": peak_kind,
-                         "residual_fp64_avg_launch_us": 1000.0 * ms_r / max(1, n_r),
-                         "level0_kernels": {k: dict(v, frac=v["achieved_gbs"] / peak) for k, v in per_kernel.items()}},
+                         "bytes_rule": "algorithmic: 6 s = 24 B per cell per full red+black sweep, "
+                                       "half per colour launch (12 B x cells)",
+                         "bytes_per_launch": bytes_launch,
+                         "actual_bytes_per_launch": ACT_BPC["half"] * N,
+                         "frac_on_actual_bytes": ACT_BPC["half"] * N / avg_s / 1e9 / peak,
+                         "traffic_over_algorithmic": None if traffic is None else traffic / bytes_launch,
+                         "avg_launch_us": avg_s * 1e6, "launches_timed": n_l, "peak_source": peak_kind,
+                         "level0_kernels": per_kernel,
+                         "residual_fp64": residual,
+                         "fp64_peak": {"fma_per_s": fp64_rate, "gflops": 2e-9 * fp64_rate,
+                                       "how": "mg_probe_fp64_rate: 8 independent FP64 FMA chains per thread, "
+                                              "8 blocks of 256 threads per SM, best of 3 event-timed launches"}},
             "cpu_baseline": cpu,
             "gpu_launches": launches,
-            "clocks": results.get("clocks"),
+            "clocks": clock_rec,
         }
         print(json.dumps(line))
     for S in solvers.values():
         S.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="drop_film_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prolongation", default="trilinear", choices=["trilinear", "flux"],
+                    help="prolongation of the V-cycle: trilinear or flux-conserving (Sec. 2.3 item 4)")
+    ap.add_argument("--solver", default="mg", choices=["mg", "pcg"],
+                    help="outer iteration: V-cycles in FP64 refinement (mg) or V-cycle-preconditioned CG (pcg)")
+    ap.add_argument("--requests", type=int, default=500, help="serve_stream: requests in the stream")
+    ap.add_argument("--load", type=float, nargs="+", default=[0.5, 0.8, 1.0],
+                    help="serve_stream: arrival rates as fractions of the measured capacity of the mixed path")
+    ap.add_argument("--slots", type=int, default=8, help="serve_stream: most requests on the GPU at once")
+    ap.add_argument("--hbm-budget", type=int, default=64, help="serve_stream: GiB of device memory for hierarchies")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, args.workload)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+
+    kind = WORKLOADS[args.workload]["kind"]
+    run = {"batch": run_batch, "serve": run_serve, "projection": run_projection}.get(kind, run_single)
+    run(args, rank, world, local_rank, dist)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

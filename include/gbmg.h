@@ -163,6 +163,12 @@ typedef struct {
     double rhs_mean;    /* mean of the right-hand side that was removed */
     double ms;          /* device time of the solve (stream events), milliseconds */
     int steps;          /* FP64 refinement steps (residual evaluations after the first) */
+    /* served solves only (zero for the other calls): */
+    int64_t admit_tick;    /* the server's count of refinement-step launches when the request was admitted */
+    int64_t finish_tick;   /* ... when it finished: two requests overlapped on the GPU when their
+                              [admit_tick, finish_tick] intervals intersect */
+    int inflight_at_admit; /* requests already on the GPU when this one was admitted */
+    int lane;              /* size lane that ran it (see mg_server_create) */
 } mg_stats;
 
 typedef struct mg_handle mg_handle;
@@ -337,26 +343,31 @@ int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x)
 int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e);
 
 /* Exact solve of a small grid without allocating any memory (the paper has no
- * counterpart: this serves callers that cannot allocate device memory when
- * they need the solve, e.g. while a stream is being captured into a CUDA
- * graph, in a real-time loop with a fixed memory budget, or inside a host
- * whose allocator owns the device memory).
+ * counterpart).  For callers that cannot allocate device memory at the point
+ * where they need a solve: a real-time loop whose device memory is budgeted
+ * up front, or a host program whose own allocator has reserved the device
+ * memory (cudaMalloc may then fail, and it can also synchronise the device).
  *
- * Solves A e = r - mean(r) for the grid `grid` (at most MG_STATIC_MAX_CELLS
- * cells, any size per axis, walls or periodic) with face coefficients ax, ay,
- * az (DEVICE, alpha = 1/rho in the layout above, > 0 off the walls) and writes
- * e (DEVICE, nx*ny*nz doubles), all in FP64: it assembles -A + c 1 1^T, inverts
- * it by Gauss-Jordan elimination and applies the inverse, the same arithmetic
- * as the coarsest-grid solve of a handle.  The result has a constant offset
- * -sum(r) / (c n^2) (zero when sum(r) = 0), like mg_coarse_solve.
+ * Writes e (DEVICE, nx*ny*nz doubles) = the zero-mean solution of
+ * A e = r - mean(r) plus the constant -sum(r) / trace(-A), for the grid
+ * `grid` (at most MG_STATIC_MAX_CELLS cells, any size per axis, walls or
+ * periodic) with face coefficients ax, ay, az (DEVICE, alpha = 1/rho in the
+ * layout above, > 0 off the walls) and right-hand side r (DEVICE), all in
+ * FP64.  So e has zero mean exactly when sum(r) = 0.  It assembles
+ * -A + c 1 1^T with c = trace(-A) / n^2, inverts it by Gauss-Jordan
+ * elimination and applies the inverse, the arithmetic of the coarsest-grid
+ * solve of a handle.
  *
  * Scratch: a 2 MiB array in the library's static device memory, held by every
  * device that loads the library until the process exits.  The first call on a
- * device looks up that array's device address (make that first call before
- * any stream capture starts); no call allocates or frees memory.  Every call
- * on a device shares the array: calls whose kernels can overlap on the GPU
- * (unordered streams) race and must be serialised by the caller.  Synchronous
- * on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * device looks up that array's device address; with CUDA's lazy module loading
+ * that first call also loads this part of the library's device code (and its
+ * static array), which can itself take device memory, so make the first call
+ * once at start-up.  Later calls allocate and free nothing.  Every call on a
+ * device shares the array and each call rewrites what it reads: calls whose
+ * kernels can overlap on the GPU (unordered streams) race and must be
+ * serialised by the caller.  Synchronous on `stream` (a cudaStream_t, NULL =
+ * legacy default stream): it reads a status word back before returning.
  * Returns MG_ETOOBIG above MG_STATIC_MAX_CELLS cells, MG_EINVAL for bad
  * arguments or coefficients, MG_ESINGULAR for a grid cut into pieces. */
 int mg_coarse_solve_static(const mg_grid *grid, const double *ax, const double *ay,
@@ -405,7 +416,8 @@ int mg_projection_step(mg_handle *h, double *ux, double *uy, double *uz, double 
 #define MG_K_RESIDUAL 4 /* the FP64 residual + norms (the update p += e is folded into the cycle) */
 #define MG_K_OTHER 5
 #define MG_K_TAIL 6 /* the levels of at most 4096 cells and the coarsest solve, one block per grid */
-#define MG_K_KINDS 7
+#define MG_K_RESIDUAL0 7 /* the starting residual of a solve (a zero starting iterate skips A p) */
+#define MG_K_KINDS 8
 
 int mg_profile_enable(mg_handle *h, int enable);
 int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double *total_ms);
@@ -451,6 +463,17 @@ int mg_tune_cache_load(const char *path, int *loaded);
 /* Number of cached choices. */
 int mg_tune_cache_size(int *entries);
 
+/* Test aid for the bounded device waits (no counterpart in the paper).  The
+ * bottom-of-cycle kernel stages its levels by bulk asynchronous copies and
+ * waits for them a bounded number of polls (default 2^20; the copies take
+ * microseconds); if the wait gives up, the grid's solve reports MG_ETIMEOUT
+ * and the kernel still lets the copies land before it exits.  This sets that
+ * number of polls for h's later solves: 0 makes the first wait give up at
+ * once, so a test can take the timeout path without a fault.  A later
+ * mg_set_faces / mg_set_density clears the reported timeout.  Synchronous on
+ * h's stream; MG_EINVAL for polls < 0. */
+int mg_set_wait_limit(mg_handle *h, long long polls);
+
 /* The parameters h was created with, defaults resolved (inner_cycles). */
 int mg_handle_params(const mg_handle *h, mg_params *params);
 
@@ -459,6 +482,19 @@ int mg_memory_bytes(const mg_handle *h, size_t *bytes);
 
 /* Bytes of device memory a handle for `grid` with `params` would hold. */
 int mg_memory_estimate(const mg_grid *grid, const mg_params *params, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
+ * Device FP64 rate (no counterpart in the paper: the denominator of the FP64
+ * roofline of the outer-iteration kernels, whose bound on this GPU is the
+ * lesser of the HBM bandwidth and the FP64 issue rate).  Runs a kernel of
+ * independent FP64 fused multiply-add chains on every SM of the current
+ * device `repeats` times (`iters` steps per chain), each timed with CUDA
+ * events on `stream` (a cudaStream_t, NULL = legacy default stream), and
+ * writes the best rate in FMA operations per second (an FMA counts once; 2
+ * flops) to *fma_per_s.  Allocates one double of device memory for the call.
+ * Synchronous.  MG_EINVAL for iters or repeats < 1 or a null output.
+ * --------------------------------------------------------------------------- */
+int mg_probe_fp64_rate(int iters, int repeats, double *fma_per_s, void *stream);
 
 #ifdef __cplusplus
 }

@@ -842,6 +842,25 @@ int oracle_solve(const og_grid *g, const double *ax, const double *ay, const dou
     return status;
 }
 
+/* Preconditioner of oracle_pcg_solve: z = M r.  precond = 1: one V(nu1, nu2)
+ * cycle of the hierarchy H on A z = r from z = 0, then z - mean(z);
+ * precond = 0: z = r.  Returns 0, or the cycle's (negative) error status. */
+static int pcg_precondition(og_hier *H, const og_grid *g, int precond, double *r, double *z, size_t bytes)
+{
+    if (!precond) {
+        memcpy(z, r, bytes);
+        return 0;
+    }
+    og_level *L0 = &H->lev[0];
+    L0->b = r;
+    L0->x = z;
+    memset(z, 0, bytes);
+    int st = vcycle(H, 0);
+    if (st) return st;
+    subtract_constant(g, z, oracle_mean(g, z));
+    return 0;
+}
+
 /* Conjugate gradients on the SPD operator -A (zero-mean subspace), with the
  * residual kept in the sign of the multigrid (r = b - A x, q = A d):
  *   alpha = (r.z) / (d.q),  x += alpha d,  r -= alpha q,
@@ -878,13 +897,11 @@ int oracle_pcg_solve(const og_grid *g, const double *ax, const double *ay, const
     hist[0] = rn;
     double rz = 0.0;
     if (bnorm == 0.0 || rn <= tol * bnorm) status = 0;
-    /* preconditioner: z = M r */
-#define OG_PRECOND()                                                             do {                                                                             if (precond) {                                                                   L0->b = r;                                                                   L0->x = z;                                                                   memset(z, 0, bytes);                                                         int st_ = vcycle(&H, 0);                                                     if (st_) { status = st_; break; }                                            subtract_constant(g, z, oracle_mean(g, z));                              } else {                                                                         memcpy(z, r, bytes);                                                     }                                                                        } while (0)
     if (status == 1) {
-        do {
-            OG_PRECOND();
-        } while (0);
-        if (status == 1) {
+        int st = pcg_precondition(&H, g, precond, r, z, bytes);
+        if (st) {
+            status = st;
+        } else {
             memcpy(d, z, bytes);
             rz = 0.0;
             for (long c = 0; c < n; c++) rz += r[c] * z[c];
@@ -905,10 +922,11 @@ int oracle_pcg_solve(const og_grid *g, const double *ax, const double *ay, const
         hist[it] = rn;
         if (!(rn == rn)) { status = -3; break; }
         if (rn <= tol * bnorm) { status = 0; break; }
-        do {
-            OG_PRECOND();
-        } while (0);
-        if (status != 1) break;
+        int st = pcg_precondition(&H, g, precond, r, z, bytes);
+        if (st) {
+            status = st;
+            break;
+        }
         double zq = 0.0, rz_new = 0.0;
         for (long c = 0; c < n; c++) {
             zq += z[c] * q[c];
@@ -918,7 +936,6 @@ int oracle_pcg_solve(const og_grid *g, const double *ax, const double *ay, const
         rz = rz_new;
         for (long c = 0; c < n; c++) d[c] = z[c] + beta * d[c];
     }
-#undef OG_PRECOND
     subtract_constant(g, x, oracle_mean(g, x));
     *nit = it;
     L0->x = NULL;

@@ -365,6 +365,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         v.G = h->G;
         v.st = h->state;
         v.err = h->err + 2;
+        v.wait_polls = h->wait_polls;
         tail_smem = std::max(tail_smem, (size_t)off * esz);
     }
     for (int g = 0; g < G; g++) {
@@ -579,7 +580,7 @@ static void prologue(Plan &P, Prof &pf)
     launch_finalize(P.ot, 0, s);
     pf.end(s);
     if (P.prm.solver == MG_SOLVER_PCG) {
-        pf.begin(s, MG_K_RESIDUAL, 0);
+        pf.begin(s, MG_K_RESIDUAL0, 0);
         launch_residual<T>(P.ot, 1, s);
         pf.end(s);
     } else {
@@ -591,7 +592,7 @@ static void prologue(Plan &P, Prof &pf)
         launch_finalize(P.ot, 4, s);
         if (P.xp) launch_xp_prepare(P.ot, s);
         pf.end(s);
-        pf.begin(s, MG_K_RESIDUAL, 0);
+        pf.begin(s, MG_K_RESIDUAL0, 0);
         if (P.xp) launch_residual_xp(P.ot, 1, s);
         else launch_residual<T>(P.ot, 2, s);
         pf.end(s);
@@ -850,6 +851,13 @@ int plan_final(Plan &P)
     return MG_OK;
 }
 
+int plan_gather_states(Plan &P)
+{
+    launch_gather_states(P.ot, P.st, P.stream);
+    CK(cudaMemcpyAsync(P.st_h, P.st, P.G * sizeof(GridState), cudaMemcpyDeviceToHost, P.stream));
+    return MG_OK;
+}
+
 int plan_sync_states(Plan &P)
 {
     launch_gather_states(P.ot, P.st, P.stream);
@@ -875,6 +883,8 @@ void fill_stats(const GridState &s, const int herr[3], double ms, mg_stats *o, i
         o->rhs_mean = s.bmean;
         o->ms = ms;
         o->steps = s.steps;
+        o->admit_tick = o->finish_tick = 0;
+        o->inflight_at_admit = o->lane = 0;
     }
     *status_out = status;
 }
@@ -1627,6 +1637,21 @@ int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double
     if (!h || kind < 0 || kind >= MG_K_KINDS || level < 0 || level >= MG_MAX_LEVELS) return MG_EINVAL;
     if (launches) *launches = h->prof.launches[kind][level];
     if (total_ms) *total_ms = h->prof.total_ms[kind][level];
+    return MG_OK;
+}
+
+int mg_set_wait_limit(mg_handle *h, long long polls)
+{
+    if (!h || polls < 0) return MG_EINVAL;
+    h->wait_polls = polls;
+    // the tail views live in the plan's device tables (read by the kernels at
+    // run time, also from a captured graph): rewrite them
+    if (h->plan) {
+        mg_handle *one = h;
+        int rc = h->plan->fill(&one, 1);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(h->stream));
+    }
     return MG_OK;
 }
 

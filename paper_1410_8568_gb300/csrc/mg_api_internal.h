@@ -8,6 +8,7 @@
 
 #include "gbmg.h"
 #include "mg_kernels.h"
+#include "mg_bulk.cuh"
 
 namespace gbmg {
 
@@ -97,6 +98,7 @@ struct mg_handle {
     float *xp3[3] = {nullptr, nullptr, nullptr};
     float *xb[2] = {nullptr, nullptr};
     float *wlo[3] = {nullptr, nullptr, nullptr};
+    long long wait_polls = gbmg::kBulkWaitPolls;  // first staging wait of the tail kernel (mg_set_wait_limit)
 };
 
 namespace gbmg {
@@ -164,6 +166,8 @@ int plan_body(Plan &P);
 int plan_final(Plan &P);
 // states of all grids of the plan into P.st_h (synchronises the stream)
 int plan_sync_states(Plan &P);
+// the same, enqueued on the plan's stream only (valid once the stream reaches it)
+int plan_gather_states(Plan &P);
 // autotuner (mg_tune.cu): launch shapes of h's levels into h->tile
 int tune_handle(mg_handle *h);
 void tune_cache_clear();

@@ -238,6 +238,7 @@ struct TailView {
     FastDiv dx[kMaxTail], dhx[kMaxTail], dy[kMaxTail];  // division by n[t][0], n[t][0] / 2, n[t][1]
     FastDiv dq[kMaxTail];    // division by n[t][0] / 4 (quads per row)
     int *err;                // set to 1 when the staging copies did not complete in time
+    long long wait_polls;    // polls of the staging wait before it gives up (kBulkWaitPolls by default)
     int flux;                // flux-conserving prolongation: level t >= 1 also holds its cell
     const void *a[kMaxTail]; //   coefficients (6th array of the level in shared memory)
 };

@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailView *__restric
     }
     __syncthreads();  // the barrier is initialised before anyone waits on it
     // every thread waits (bounded); the outcome is made uniform over the block
-    const int staged = __syncthreads_and(mbar_wait(&bar, 0, kBulkWaitPolls) ? 1 : 0);
+    const int staged = __syncthreads_and(mbar_wait(&bar, 0, V.wait_polls) ? 1 : 0);
     if (!staged) {
         // give up on this grid (reported as MG_ETIMEOUT), but let the copies
         // land before the block's shared memory is released

@@ -1,12 +1,14 @@
 // mg_static.cu -- exact small-grid solve that allocates no memory.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// solve: code running while a CUDA stream is being captured into a graph (an
-// allocation there breaks the capture), real-time loops whose memory budget is
-// fixed up front, or hosts whose allocator owns every byte of device memory.
-// For them mg_coarse_solve_static solves a grid of at most
-// MG_STATIC_MAX_CELLS cells exactly, using only a scratch area that lives for
-// the whole process in this file's static device array.
+// solve: real-time loops whose device memory is budgeted up front, or host
+// programs whose own allocator has reserved the device memory (cudaMalloc may
+// then fail, and it can synchronise the device).  For them
+// mg_coarse_solve_static solves a grid of at most MG_STATIC_MAX_CELLS cells
+// exactly, using only a scratch area that lives for the whole process in this
+// file's static device array.  The first call on a device looks up the
+// array's device address (and, with lazy module loading, loads this file's
+// device code); later calls allocate nothing.
 //
 // The scratch array is shared by every call on a device and keeps the last
 // call's contents; the kernel rewrites everything it reads before reading it.

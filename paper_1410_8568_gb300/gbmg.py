@@ -24,7 +24,7 @@ STATIC_MAX_CELLS = 512
 NEUMANN, PERIODIC = 0, 1
 FP64, MIXED = 0, 1
 HARMONIC, ARITHMETIC = 0, 1
-K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL = range(7)
+K_SMOOTH, K_RESTRICT, K_PROLONG, K_COARSE, K_RESIDUAL, K_OTHER, K_TAIL, K_RESIDUAL0 = range(8)
 TILES_AUTO, TILES_ROWS, TILE_VARIANTS = -1, 0, 7
 PROLONG_TRILINEAR, PROLONG_FLUX = 0, 1
 SOLVER_MG, SOLVER_PCG = 0, 1
@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("res0", ctypes.c_double), ("res", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("rhs_mean", ctypes.c_double), ("ms", ctypes.c_double),
-                ("steps", ctypes.c_int)]
+                ("steps", ctypes.c_int), ("admit_tick", ctypes.c_int64), ("finish_tick", ctypes.c_int64),
+                ("inflight_at_admit", ctypes.c_int), ("lane", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -124,6 +125,8 @@ def lib():
             "mg_tune_cache_load": (_I, [ctypes.c_char_p, _P(_I)]),
             "mg_tune_cache_size": (_I, [_P(_I)]),
             "mg_handle_params": (_I, [_V, _P(Params)]),
+            "mg_probe_fp64_rate": (_I, [_I, _I, _P(_D), _V]),
+            "mg_set_wait_limit": (_I, [_V, ctypes.c_longlong]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -191,6 +194,14 @@ def tile_shape(variant):
     a, b = ctypes.c_int(), ctypes.c_int()
     check(lib().mg_tile_shape(int(variant), ctypes.byref(a), ctypes.byref(b)), "mg_tile_shape")
     return (a.value, b.value)
+
+
+def probe_fp64_rate(iters=20000, repeats=3, stream=None):
+    """Measured FP64 fused multiply-add rate of the current device (FMA/s)."""
+    out = ctypes.c_double()
+    check(lib().mg_probe_fp64_rate(int(iters), int(repeats), ctypes.byref(out), _stream(stream)),
+          "mg_probe_fp64_rate")
+    return out.value
 
 
 def tune_cache_clear():
@@ -385,6 +396,11 @@ class Solver:
         p = Params()
         check(lib().mg_handle_params(self._h, ctypes.byref(p)), "mg_handle_params")
         return {f: getattr(p, f) for f, _ in Params._fields_}
+
+    def set_wait_limit(self, polls):
+        """Polls of the bottom-of-cycle kernel's staging wait before it gives up
+        (0: at once; the solve then reports ETIMEOUT).  A test aid."""
+        check(lib().mg_set_wait_limit(self._h, int(polls)), "mg_set_wait_limit")
 
     def tile_choice(self, kind, level) -> int:
         """Launch shape used for kernel `kind` (TILE_*) on `level`."""

@@ -128,21 +128,36 @@ def test_no_gpu_fails_loudly():
         gbmg.Solver((8, 8, 8), (0, 0, 0), faces=[torch.ones(512, dtype=torch.float64)] * 3)
 
 
+# kernels launched with a plain <<< >>> launch, outside any dependent-launch
+# scope (the allocation-free solve and the FP64 rate probe): they need no wait
+PLAIN_LAUNCH = {"k_coarse_static", "k_fp64_fma"}
+
+
 def test_every_launched_kernel_waits_for_its_predecessor_first():
     """A launch with programmatic stream serialization (launch_k inside a
     dependent-launch scope) may be scheduled while the previous kernel runs, so
-    every kernel of a source file that launches through launch_k must begin
-    with dep_entry() (griddepcontrol.wait) before any other statement."""
+    every kernel defined anywhere in csrc (.cu and .cuh) must begin with
+    dep_entry() (griddepcontrol.wait) before any other statement, except the
+    plain-launched ones, which must never be launched through launch_k."""
     import glob
 
     csrc = os.path.join(os.path.dirname(gbmg.__file__), "csrc")
-    checked = 0
-    for path in sorted(glob.glob(os.path.join(csrc, "*.cu"))):
-        src = open(path).read()
-        if "launch_k(" not in src:
-            continue
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
+    sources = {os.path.basename(p): open(p).read() for p in files}
+    checked, plain = 0, set()
+    for name, src in sources.items():
         for m in re.finditer(r"__global__[^;{]*\{", src):
+            head = src[m.start():m.end()]
+            kernel = re.search(r"\b(k_\w+)\s*\(", head).group(1)
             first = src[m.end():].lstrip().split("\n", 1)[0].strip()
-            assert first == "dep_entry();", (os.path.basename(path), src[m.start():m.end()][:90])
+            if kernel in PLAIN_LAUNCH:
+                plain.add(kernel)
+                assert "<<<" in src, (name, kernel)
+                continue
+            assert first == "dep_entry();", (name, head[:90])
             checked += 1
     assert checked >= 30
+    assert plain == PLAIN_LAUNCH
+    for kernel in PLAIN_LAUNCH:
+        for name, src in sources.items():
+            assert not re.search(r"launch_k\(\s*%s\b" % kernel, src), (name, kernel)

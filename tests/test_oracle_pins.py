@@ -8,6 +8,7 @@ shifted index, transposed axis) would break.  Sec./Eq. numbers refer to Shin,
 Chergui & Juric, arXiv 1410.8568.
 """
 import math
+from fractions import Fraction
 import os
 
 import numpy as np
@@ -502,6 +503,33 @@ def load_flux_golden():
             key, *vals = line.split()
             rows[key] = [float(Fraction(v)) for v in vals]
     return rows
+
+
+def test_trilinear_prolongation_golden():
+    """Hand-worked trilinear prolongation at Neumann walls and across periodic
+    wraps (tests/golden/trilinear_prolongation.txt): pins the coarse partner of
+    the first and last fine cell of every axis."""
+    coarse, cases = {}, []
+    with open(os.path.join(GOLDEN, "trilinear_prolongation.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            if key.startswith("coarse_"):
+                coarse[key] = [float(Fraction(v)) for v in vals]
+            elif key == "case":
+                cases.append((tuple(int(v) for v in vals), []))
+            else:
+                i, j, k, v = vals
+                cases[-1][1].append((int(i), int(j), int(k), float(Fraction(v))))
+    assert len(cases) == 2
+    shape = (8, 4, 4)
+    a, b, c = (np.array(coarse[k]) for k in ("coarse_a", "coarse_b", "coarse_c"))
+    ec = c[:, None, None] + b[None, :, None] + a[None, None, :]  # (K, J, I)
+    for bc, cells_ in cases:
+        got = oracle.prolong_add(shape, bc, ec, np.zeros(cells(shape)))
+        for i, j, k, v in cells_:
+            assert got[k, j, i] == v, (bc, (i, j, k), got[k, j, i], v)
 
 
 def test_flux_prolongation_golden():
