@@ -114,16 +114,17 @@ def read_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mg_kernels.cu", "mg_tiles.cu", "mg_stencil.cuh", "mg_device.cuh", "mg_launch.cuh"):
+    for f in ("mg_kernels.cu", "mg_tiles.cu", "mg_fused.cu", "mg_stencil.cuh", "mg_device.cuh", "mg_launch.cuh"):
         with open(os.path.join(ROOT, "paper_1410_8568_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
-    or None if absent or taken on a different kernel source."""
-    path = os.path.join(ROOT, "profiles", "smooth_level0_%s.md" % workload)
+def profiled_traffic(workload, kernel="smooth"):
+    """DRAM bytes per launch of the dominant kernel (the finest-level half-sweep,
+    "smooth", or one-pass sweep, "sweep") from the committed ncu summary, or None
+    if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "%s_level0_%s.md" % (kernel, workload))
     if not os.path.exists(path):
         return None
     vals = {}
@@ -588,11 +589,14 @@ def run_serve(args, rank, world, local_rank, dist):
 # so each of its two half-sweep launches counts half of that; the residual +
 # restriction reads x, b, 3 faces and writes r/8 (5.125 s); the prolongation +
 # correction reads e/8 and reads and writes x (2.125 s).
-ALG_BPC = {"half": 12.0, "restrict": 20.5, "prolong": 8.5}
+ALG_BPC = {"half": 12.0, "sweep": 24.0, "restrict": 20.5, "prolong": 8.5}
 # Bytes the unfused kernels actually move per finest cell: a half-sweep reads
 # all of x and the 3 face arrays, the colour's sectors of b (the whole b: the
 # two cells of a colour share the quad's sector) and writes the quad (x).
-ACT_BPC = {"half": 20.0}
+ACT_BPC = {"half": 20.0, "sweep": 24.0}
+# The one-pass sweep (both colours in one launch, two iterate buffers) reads
+# the old iterate, b and the 3 face arrays once and writes the new iterate: the
+# algorithmic bytes (its halo rows and planes are re-read through L2).
 # FP64 residual of a refinement step: reads p, b - mean b and 3 FP64 faces,
 # writes the FP32 residual (44 B); 6 differences, 1 product and 5 fused
 # multiply-adds, the subtraction from b and the scale (14 FP64 operations) and
@@ -714,8 +718,11 @@ def run_single(args, rank, world, local_rank, dist):
     e2e_tot = reduce_max(sum(e2e_times), dist)
     clock_rec = clocks.stop()
 
-    # roofline of the dominant kernel: finest-level half-sweep, per-launch events
+    # roofline of the dominant kernel: the finest-level sweep (one-pass) or
+    # half-sweep, per-launch events
     v0 = S.tile_choice(gbmg.TILE_HALF, 0)
+    sv = S.tile_choice(gbmg.TILE_SWEEP, 0)
+    kk = "sweep" if sv > 0 else "half"
     S.profile(True)
     prof_steps = max(3, min(args.steps, 10))
     # an NVTX range lets a profiler select these host-loop launches
@@ -750,9 +757,9 @@ def run_single(args, rank, world, local_rank, dist):
                 "fp64_frac": RES_FP64_OPS * N / (res_us * 1e-6) / fp64_rate,
                 "bound": "fp64 pipe (min of HBM and FP64 issue rate: the larger fraction)"}
     avg_s = ms_l / n_l / 1000.0
-    bytes_launch = ALG_BPC["half"] * N
+    bytes_launch = ALG_BPC[kk] * N
     achieved = bytes_launch / avg_s / 1e9
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload, "sweep" if sv > 0 else "smooth")
 
     # error of each result against the FP64 oracle's converged solution p*, and
     # the oracle's own time (its p* run: mean cycle time x the cycles it needed
@@ -816,13 +823,16 @@ def run_single(args, rank, world, local_rank, dist):
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 8 * N},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "FP32 half-sweep of level 0 (one red or black colour), launch shape %d "
-                                   "(%d threads x %d quads)" % ((v0,) + gbmg.tile_shape(v0)),
-                         "bytes_rule": "algorithmic: 6 s = 24 B per cell per full red+black sweep, "
-                                       "half per colour launch (12 B x cells)",
+                         "kernel": ("FP32 one-pass red-black sweep of level 0 (both colours in one launch), "
+                                    "shape %d (%d threads, %d planes per block)" % ((sv,) + gbmg.sweep_shape(sv)))
+                                   if sv > 0 else
+                                   ("FP32 half-sweep of level 0 (one red or black colour), launch shape %d "
+                                    "(%d threads x %d quads)" % ((v0,) + gbmg.tile_shape(v0))),
+                         "bytes_rule": "algorithmic: 6 s = 24 B per cell per full red+black sweep (%s)" %
+                                       ("one launch" if sv > 0 else "half per colour launch: 12 B x cells"),
                          "bytes_per_launch": bytes_launch,
-                         "actual_bytes_per_launch": ACT_BPC["half"] * N,
-                         "frac_on_actual_bytes": ACT_BPC["half"] * N / avg_s / 1e9 / peak,
+                         "actual_bytes_per_launch": ACT_BPC[kk] * N,
+                         "frac_on_actual_bytes": ACT_BPC[kk] * N / avg_s / 1e9 / peak,
                          "traffic_over_algorithmic": None if traffic is None else traffic / bytes_launch,
                          "avg_launch_us": avg_s * 1e6, "launches_timed": n_l, "peak_source": peak_kind,
                          "level0_kernels": per_kernel,

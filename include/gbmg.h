@@ -114,7 +114,11 @@ extern "C" {
 #define MG_TILE_VARIANTS 7   /* launch shapes 0 .. 6 (see mg_tile_shape) */
 #define MG_TILE_HALF 0       /* kernels with a tunable launch shape: red-black half-sweep, */
 #define MG_TILE_RESTRICT 1   /* residual + restriction, */
-#define MG_TILE_PROLONG 2    /* prolongation + correction */
+#define MG_TILE_PROLONG 2    /* prolongation + correction, */
+#define MG_TILE_SWEEP 3      /* finest-level full red-black sweep (0 = two half-sweep launches) */
+#define MG_SWEEP_AUTO (-1)   /* mg_params.sweep: timed at create */
+#define MG_SWEEP_HALF 0      /* mg_params.sweep: two half-sweep launches per sweep */
+#define MG_SWEEP_VARIANTS 7  /* one-pass sweep shapes 1 .. 6 (see mg_sweep_shape) */
 
 typedef struct {
     int nx, ny, nz;     /* cells per axis */
@@ -150,6 +154,13 @@ typedef struct {
                               rate predicts the tolerance needs, with a 10% margin on the rate;
                               0: always inner_cycles.  Either way a solve stops at max_iters cycles */
     int outer;             /* MG_OUTER_FP64 (default) or MG_OUTER_XP */
+    int sweep;             /* finest-level red-black sweep: MG_SWEEP_AUTO (default: the faster of
+                              two half-sweep launches per sweep and the one-pass sweep shapes that
+                              fit, timed at create), MG_SWEEP_HALF, or a one-pass shape
+                              1 .. MG_SWEEP_VARIANTS - 1 (used where it fits, else MG_SWEEP_HALF).
+                              The one-pass sweep needs even nu1 and nu2 and a second iterate buffer
+                              on the finest level (4 B per cell mixed, 8 B FP64); every choice gives
+                              bitwise the same result */
 } mg_params;
 
 typedef struct {
@@ -336,6 +347,18 @@ int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int swe
 int mg_restrict_residual(mg_handle *h, int level, int prec, const void *b, const void *x,
                          void *coarse_b);
 
+/* `sweeps` red-black sweeps (item 5) in one launch each: both colours of a
+ * sweep in one pass over the level, reading the iterate from one buffer and
+ * writing the new iterate to the other: sweep 1 reads x and writes work, sweep
+ * 2 reads work and writes x, and so on (after an even number the result is in
+ * x, after an odd number in work).  Bitwise the result of mg_smooth.  variant:
+ * a one-pass shape 1 .. MG_SWEEP_VARIANTS - 1, or 0 for the handle's tuned
+ * choice on that level.  MG_EINVAL if the shape does not fit the level (rows
+ * of a multiple of 4 cells, at most a third of the shape's threads quads per
+ * row, an even number of cells along a periodic y or z axis). */
+int mg_smooth_onepass(mg_handle *h, int level, int prec, const void *b, void *x, void *work, int sweeps,
+                      int variant);
+
 /* x += trilinear prolongation of the coarse error e of level+1 (item 4). */
 int mg_prolong(mg_handle *h, int level, int prec, const void *coarse_e, void *x);
 
@@ -436,7 +459,9 @@ int mg_profile_read(mg_handle *h, int kind, int level, int64_t *launches, double
 
 /* Shape chosen for kernel `kind` (MG_TILE_HALF, MG_TILE_RESTRICT,
  * MG_TILE_PROLONG) on `level` of h: 0 .. MG_TILE_VARIANTS - 1 (0 on the
- * coarsest level and on levels run by the bottom-of-cycle kernel). */
+ * coarsest level and on levels run by the bottom-of-cycle kernel); for
+ * MG_TILE_SWEEP the finest level's sweep: 0 (two half-sweep launches) or a
+ * one-pass shape 1 .. MG_SWEEP_VARIANTS - 1 (0 on every other level). */
 int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant);
 
 /* Threads per block and items per thread of shape `variant`: an item is a
@@ -445,6 +470,12 @@ int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant);
  * is the row tiling (a warp per row of up to 32 quads, 8 rows per block:
  * reports 256 threads, 1 item). */
 int mg_tile_shape(int variant, int *threads, int *items_per_thread);
+
+/* Threads per block and planes per block of one-pass sweep shape `variant`
+ * (1 .. MG_SWEEP_VARIANTS - 1; 0 reports 0, 0).  A block owns a strip of full
+ * rows (as many as the threads allow at one thread per 4-cell quad, less the
+ * two halo rows whose red cells it recomputes) of a chunk of planes. */
+int mg_sweep_shape(int variant, int *threads, int *planes);
 
 /* Forget every cached choice (the next mg_create times again). */
 int mg_tune_cache_clear(void);

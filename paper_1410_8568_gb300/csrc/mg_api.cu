@@ -93,6 +93,7 @@ int check_params(const mg_params *p)
     if (!(p->coarse_tol > 0.0 && p->coarse_tol < 1.0)) return MG_EINVAL;
     if (p->adaptive_cycles != 0 && p->adaptive_cycles != 1) return MG_EINVAL;
     if (p->outer != MG_OUTER_FP64 && p->outer != MG_OUTER_XP) return MG_EINVAL;
+    if (p->sweep < MG_SWEEP_AUTO || p->sweep >= MG_SWEEP_VARIANTS) return MG_EINVAL;
     return MG_OK;
 }
 
@@ -101,6 +102,7 @@ struct Layout {
     int L;
     int n[MG_MAX_LEVELS][3];
     size_t w64[MG_MAX_LEVELS][3], w32[MG_MAX_LEVELS][3], x[MG_MAX_LEVELS], b[MG_MAX_LEVELS];
+    size_t x2;  // second iterate buffer of the finest level (one-pass sweep), 0 if none
     size_t alpha64[MG_MAX_LEVELS], alpha32[MG_MAX_LEVELS];
     size_t G, b0, part, err, state, dstate, dview, dstart, dcview, setup_cv, total;
     size_t pcg[4];
@@ -110,6 +112,19 @@ struct Layout {
     size_t gm;
     int nblk0;
 };
+
+// the finest level can run one-pass sweeps (mg_fused.cu): even nu1 and nu2
+// (the sweeps alternate between two buffers and must end in the first) and
+// some one-pass shape fits it
+static bool onepass_possible(const mg_grid &g, const mg_params &p, const int n[3])
+{
+    if (p.sweep == MG_SWEEP_HALF || (p.nu1 & 1) || (p.nu2 & 1)) return false;
+    const int per = (g.bc[0] == MG_BC_PERIODIC ? 1 : 0) | (g.bc[1] == MG_BC_PERIODIC ? 2 : 0) |
+                    (g.bc[2] == MG_BC_PERIODIC ? 4 : 0);
+    for (int v = 1; v < kSweepVariants; v++)
+        if (sweep_fits(n, per, v)) return true;
+    return false;
+}
 
 static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
 {
@@ -124,6 +139,7 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
         for (int d = 0; d < 3; d++) lay.w32[l][d] = mixed ? c.take(N * 4) : 0;
         lay.x[l] = c.take(N * vs);
         lay.b[l] = c.take(N * vs);
+        if (l == 0) lay.x2 = (lay.L > 1 && onepass_possible(g, p, lay.n[0])) ? c.take(N * vs) : 0;
         const bool flux = l > 0 && p.prolongation == MG_PROLONG_FLUX;
         lay.alpha64[l] = flux ? c.take(N * 8) : 0;
         lay.alpha32[l] = (flux && mixed) ? c.take(N * 4) : 0;
@@ -196,7 +212,7 @@ int Plan::alloc(int cap)
 {
     capacity = cap;
     const int LV = cap * (MG_MAX_LEVELS - 1);
-    const int ST = 3 * (cap + 1) * (MG_MAX_LEVELS - 1) + (cap + 1);
+    const int ST = 3 * (cap + 1) * (MG_MAX_LEVELS - 1) + 2 * (cap + 1);
     Carve c;
     o_lv = c.take((size_t)LV * sizeof(LevelView));
     o_starts = c.take((size_t)ST * sizeof(int));
@@ -260,6 +276,7 @@ int Plan::fill(mg_handle *const *handles, int count)
         rest[l] = down[l];
         half[l] = down[l];
     }
+    sweep0 = Table{d_lv, d_starts, 0, 0};
     for (int l = 0; l + 1 < Lmax; l++) {
         const int lv0 = nlv;
         int sf0 = nst, sc0, sh0, cnt = 0;
@@ -281,8 +298,26 @@ int Plan::fill(mg_handle *const *handles, int count)
                 if (!tile_fits(h->lev[l].n, var[k])) var[k] = 0;
         }
         if (flux) var[MG_TILE_PROLONG] = 0;
-        // three prefix arrays, each count + 1 long, laid out one after the other
-        std::vector<int> sf{0}, sc{0}, sh{0};
+        // finest level: one-pass sweep shape of the largest grid if it fits
+        // every grid of the table (each with its second iterate buffer)
+        int sv = 0;
+        if (l == 0) {
+            long long big = -1;
+            for (int g = 0; g < G; g++) {
+                mg_handle *h = hs[g];
+                if (l + 1 >= h->L || l >= lt[g] || h->lev[0].N <= big) continue;
+                big = h->lev[0].N;
+                sv = h->tile[MG_TILE_SWEEP][0];
+            }
+            for (int g = 0; g < G && sv > 0; g++) {
+                mg_handle *h = hs[g];
+                if (l + 1 >= h->L || l >= lt[g]) continue;
+                if (!h->lev[0].x2 || !sweep_fits(h->lev[0].n, h->per, sv)) sv = 0;
+            }
+        }
+        // three prefix arrays (four on the finest level), each count + 1 long,
+        // laid out one after the other
+        std::vector<int> sf{0}, sc{0}, sh{0}, sw{0};
         for (int g = 0; g < G; g++) {
             mg_handle *h = hs[g];
             if (l + 1 >= h->L || l >= lt[g]) continue;
@@ -307,6 +342,8 @@ int Plan::fill(mg_handle *const *handles, int count)
             v.zr = (l + 1 < lt[g] && l + 2 < h->L) ? 1 : 0;
             for (int d = 0; d < 3; d++) v.wc[d] = mixed ? (const void *)C.w32[d] : (const void *)C.w64[d];
             fill_fastdiv(v);
+            v.x2 = F.x2;
+            if (sv > 0) sw.push_back(sw.back() + sweep_layout(v, sv));
             sf.push_back(sf.back() + prolong_blocks_v(F.n, C.n, var[MG_TILE_PROLONG]));
             sc.push_back(sc.back() + restrict_blocks_v(F.n, C.n, var[MG_TILE_RESTRICT]));
             sh.push_back(sh.back() + half_sweep_blocks_v(F.n, var[MG_TILE_HALF]));
@@ -320,9 +357,15 @@ int Plan::fill(mg_handle *const *handles, int count)
         down[l] = Table{d_lv + lv0, d_starts + sf0, cnt, sf.back(), var[MG_TILE_PROLONG], flux ? 1 : 0};
         rest[l] = Table{d_lv + lv0, d_starts + sc0, cnt, sc.back(), var[MG_TILE_RESTRICT]};
         half[l] = Table{d_lv + lv0, d_starts + sh0, cnt, sh.back(), var[MG_TILE_HALF]};
+        if (sv > 0) {
+            const int sw0 = nst;
+            for (int v : sw) starts[nst++] = v;
+            sweep0 = Table{d_lv + lv0, d_starts + sw0, cnt, sw.back(), sv};
+        }
         // a one-grid table also hands its view to the kernels by value (the
         // host copy stays in the staging buffer, rewritten only by fill)
         if (cnt == 1) down[l].hv = rest[l].hv = half[l].hv = lv + lv0;
+        if (cnt == 1 && sv > 0) sweep0.hv = lv + lv0;
     }
     const int so0 = nst;
     starts[nst++] = 0;
@@ -509,7 +552,17 @@ static void vcycle(Plan &P, Prof &pf, int cyc, bool outer)
         const Table H = at(P.half[l]);
         if (H.count == 0) continue;
         const bool zero = !(l == 0 && cyc > 0);
-        for (int it = 0; it < q.nu1; it++) {
+        if (l == 0 && P.sweep0.count > 0) {
+            // one-pass sweeps, alternating between the two iterate buffers
+            // (nu1 even: the last one writes x)
+            const Table W = at(P.sweep0);
+            for (int it = 0; it < q.nu1; it++) {
+                pf.begin(s, MG_K_SMOOTH, l);
+                launch_sweep<T>(W, it & 1, q.omega, (it == 0 && zero) ? kHalfZero : 0, nullptr, s);
+                pf.end(s);
+            }
+        }
+        for (int it = 0; it < q.nu1 && !(l == 0 && P.sweep0.count > 0); it++) {
             // below the finest level the restriction into this level already
             // did the zero-start red half-sweep of every grid in this table
             if (!(it == 0 && l > 0)) {
@@ -543,6 +596,17 @@ static void vcycle(Plan &P, Prof &pf, int cyc, bool outer)
         pf.begin(s, MG_K_PROLONG, l);
         launch_prolong<T>(at(P.down[l]), (top && q.nu2 == 0) ? P.ov : nullptr, s);
         pf.end(s);
+        if (l == 0 && P.sweep0.count > 0) {
+            const Table W = at(P.sweep0);
+            for (int it = 0; it < q.nu2; it++) {
+                // the last sweep adds both colours' final values
+                const int fl = (top && it == q.nu2 - 1) ? kHalfOuter : 0;
+                pf.begin(s, MG_K_SMOOTH, l);
+                launch_sweep<T>(W, it & 1, q.omega, fl, fl ? P.ov : nullptr, s);
+                pf.end(s);
+            }
+            continue;
+        }
         for (int it = 0; it < q.nu2; it++) {
             // the last black half-sweep adds both colours' final values
             const int fl = (top && it == q.nu2 - 1) ? kHalfOuter : 0;
@@ -1051,6 +1115,7 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
         }
         L.N = (long long)L.n[0] * L.n[1] * L.n[2];
         L.x = h->slab + lay.x[l];
+        L.x2 = (l == 0 && lay.x2) ? (void *)(h->slab + lay.x2) : nullptr;
         L.alpha64 = lay.alpha64[l] ? (double *)(h->slab + lay.alpha64[l]) : nullptr;
         L.alpha32 = lay.alpha32[l] ? (float *)(h->slab + lay.alpha32[l]) : nullptr;
         L.b = h->slab + lay.b[l];
@@ -1156,6 +1221,7 @@ int mg_params_default(mg_params *p)
     p->coarse_tol = 1e-8;
     p->adaptive_cycles = 1;
     p->outer = MG_OUTER_FP64;
+    p->sweep = MG_SWEEP_AUTO;
     return MG_OK;
 }
 
@@ -1553,6 +1619,43 @@ int mg_smooth(mg_handle *h, int level, int prec, const void *b, void *x, int swe
             if (prec == MG_PREC_MIXED) launch_half<float>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
             else launch_half<double>(tb, colour, h->prm.omega, 0, nullptr, h->stream);
         }
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+int mg_smooth_onepass(mg_handle *h, int level, int prec, const void *b, void *x, void *work, int sweeps,
+                      int variant)
+{
+    if (!h || !x || !b || !work || sweeps < 0 || level < 0 || level >= h->L) return MG_EINVAL;
+    if (variant < 0 || variant >= kSweepVariants) return MG_EINVAL;
+    if (prec != MG_PREC_FP64 && prec != MG_PREC_MIXED) return MG_EINVAL;
+    if (prec == MG_PREC_MIXED && !h->mixed) return MG_EINVAL;
+    if (variant == 0) variant = level == 0 ? h->tile[MG_TILE_SWEEP][0] : 0;
+    const HLevel &L = h->lev[level];
+    if (!sweep_fits(L.n, h->per, variant)) return MG_EINVAL;
+    LevelView v;
+    memset(&v, 0, sizeof(v));
+    for (int d = 0; d < 3; d++) {
+        v.n[d] = L.n[d];
+        v.w[d] = prec == MG_PREC_MIXED ? (void *)L.w32[d] : (void *)L.w64[d];
+    }
+    v.per = h->per;
+    v.x = x;
+    v.x2 = work;
+    v.b = (void *)b;
+    v.st = h->dstate;
+    fill_fastdiv(v);
+    const int blocks = sweep_layout(v, variant);
+    const int starts[2] = {0, blocks};
+    CK(cudaMemcpyAsync(h->dview, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, h->stream));
+    Table tb{h->dview, h->dstart, 1, blocks, variant};
+    tb.hv = &v;
+    for (int it = 0; it < sweeps; it++) {
+        if (prec == MG_PREC_MIXED) launch_sweep<float>(tb, it & 1, h->prm.omega, 0, nullptr, h->stream);
+        else launch_sweep<double>(tb, it & 1, h->prm.omega, 0, nullptr, h->stream);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));

@@ -33,6 +33,7 @@ struct HLevel {
     double *w64[3];  // alpha / h^2, FP64
     float *w32[3];   // FP32 copy (mixed precision only)
     void *x;         // V-cycle iterate / correction (V-cycle precision)
+    void *x2;        // finest level: second iterate buffer of the one-pass sweep (or null)
     void *b;         // V-cycle right-hand side (V-cycle precision)
     double *alpha64; // cell coefficients (flux-conserving prolongation, levels >= 1), FP64
     float *alpha32;  // FP32 copy (mixed precision only)
@@ -88,7 +89,7 @@ struct mg_handle {
     double *io_rhs = nullptr, *io_p = nullptr, *io_rho = nullptr;  // host-call staging
     cudaStream_t io_stream = nullptr;  // host-call input copies that overlap the face set-up
     cudaEvent_t io_ready = nullptr;
-    signed char tile[3][MG_MAX_LEVELS] = {};  // launch shape per kernel (MG_TILE_*) and level
+    signed char tile[4][MG_MAX_LEVELS] = {};  // launch shape per kernel (MG_TILE_*) and level
     double *pcg[4] = {nullptr, nullptr, nullptr, nullptr};  // CG: r, z, d, q (FP64, finest level)
     bool gmres = false;        // coarsest grid solved by GMRES (no dense inverse)
     double *gm = nullptr;      // GMRES scratch
@@ -122,6 +123,7 @@ struct Plan {
     Table down[MG_MAX_LEVELS];  // prolongation (fine tiles of level l)
     Table rest[MG_MAX_LEVELS];  // restriction (coarse tiles of level l+1)
     Table half[MG_MAX_LEVELS];  // red-black half-sweeps of level l
+    Table sweep0;               // one-pass sweeps of the finest level (count 0: half-sweeps)
     CoarseView *cv = nullptr;   // coarsest solves of the grids without a tail
     int ncv = 0;
     bool cv_dense = false, cv_gmres = false;  // which coarse kernels the cv table needs

@@ -124,6 +124,25 @@ __host__ __device__ constexpr TileShape tile_shape(int v)
                   : TileShape{kThreads, 1};
 }
 
+// Launch shapes of the one-pass red-black sweep (mg_fused.cu): B threads per
+// block (a thread per quad of each row of a strip of rows, 2 halo rows
+// included) and Kc planes per block (a chunk of the z march).  Variant 0 is
+// no one-pass sweep (two half-sweep launches per sweep).
+constexpr int kSweepVariants = 7;
+struct SweepShape {
+    int B, Kc;
+};
+__host__ __device__ constexpr SweepShape sweep_shape(int v)
+{
+    return v == 1 ? SweepShape{1024, 16}
+         : v == 2 ? SweepShape{1024, 32}
+         : v == 3 ? SweepShape{1024, 64}
+         : v == 4 ? SweepShape{512, 16}
+         : v == 5 ? SweepShape{512, 32}
+         : v == 6 ? SweepShape{512, 64}
+                  : SweepShape{0, 0};
+}
+
 // One level of one grid as seen by the V-cycle kernels (precision T is fixed
 // by the kernel instantiation; pointers are typeless here).
 struct LevelView {
@@ -149,6 +168,12 @@ struct LevelView {
     // half-sweep, from the restricted right-hand side and that level's faces wc
     int zr;
     const void *wc[3];
+    // one-pass red-black sweep (finest level): the second iterate buffer (a
+    // sweep reads one and writes the other), rows per strip, planes per chunk,
+    // strips per plane, and division by the strips and by the quads per row
+    void *x2;
+    int fR, fKc, fS;
+    FastDiv dfS, dfq;
 };
 
 // The finest level of one grid for the FP64 outer iteration.

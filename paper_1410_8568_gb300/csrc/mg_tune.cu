@@ -98,8 +98,11 @@ int load_locked(const char *path, int *loaded)
         int v;
         if (sscanf(line, "%d %d %d %d %d %d %d", &k.kind, &k.mixed, &k.per, &k.n[0], &k.n[1], &k.n[2], &v) != 7)
             continue;
-        if (k.kind < 0 || k.kind > 2 || (k.mixed != 0 && k.mixed != 1) || k.per < 0 || k.per > 7 || v < 0 ||
-            v >= kTileVariants || !tile_fits(k.n, v))
+        if (k.kind < 0 || k.kind > MG_TILE_SWEEP || (k.mixed != 0 && k.mixed != 1) || k.per < 0 || k.per > 7 ||
+            v < 0)
+            continue;
+        if (k.kind == MG_TILE_SWEEP ? (v >= kSweepVariants || (v > 0 && !sweep_fits(k.n, k.per, v)))
+                                    : (v >= kTileVariants || !tile_fits(k.n, v)))
             continue;
         g_tune[k] = v;
         n++;
@@ -184,6 +187,125 @@ int time_shape(mg_handle *h, int kind, int l, int v, float *ms)
     return MG_OK;
 }
 
+// One full red-black sweep of the finest level: two half-sweep launches in
+// the level's tuned half-sweep shape (v = 0) or one one-pass launch of shape v
+// (alternating between the two iterate buffers).
+template <class T>
+int time_sweep(mg_handle *h, int v, float *ms)
+{
+    const HLevel &F = h->lev[0], &C = h->lev[1];
+    LevelView lv;
+    memset(&lv, 0, sizeof(lv));
+    for (int d = 0; d < 3; d++) {
+        lv.n[d] = F.n[d];
+        lv.nc[d] = C.n[d];
+        lv.w[d] = h->mixed ? (void *)F.w32[d] : (void *)F.w64[d];
+    }
+    lv.per = h->per;
+    lv.x = F.x;
+    lv.x2 = F.x2;
+    lv.b = F.b;
+    lv.xc = C.x;
+    lv.bc = C.b;
+    lv.st = h->dstate;
+    fill_fastdiv(lv);
+    const int hv = h->tile[MG_TILE_HALF][0];
+    const int blocks = v > 0 ? sweep_layout(lv, v) : half_sweep_blocks_v(lv.n, hv);
+    const int starts[2] = {0, blocks};
+    cudaStream_t s = h->stream;
+    TK(cudaMemcpyAsync(h->dview, &lv, sizeof(lv), cudaMemcpyHostToDevice, s));
+    TK(cudaMemcpyAsync(h->dstart, starts, sizeof(starts), cudaMemcpyHostToDevice, s));
+    Table tb{h->dview, h->dstart, 1, blocks, v > 0 ? v : hv};
+    tb.hv = &lv;
+    auto run = [&](int i) {
+        if (v > 0) {
+            launch_sweep<T>(tb, i & 1, 1.0, 0, nullptr, s);
+        } else {
+            launch_half<T>(tb, 0, 1.0, 0, nullptr, s);
+            launch_half<T>(tb, 1, 1.0, 0, nullptr, s);
+        }
+    };
+    cudaEvent_t e0, e1;
+    TK(cudaEventCreate(&e0));
+    TK(cudaEventCreate(&e1));
+    run(0);
+    run(1);
+    cudaEventRecord(e0, s);
+    run(0);
+    cudaEventRecord(e1, s);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float one = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&one, e0, e1);
+    int reps = one > 0.f ? (int)(0.5f / one) : 64;
+    reps = reps < 4 ? 4 : (reps > 64 ? 64 : reps);
+    reps &= ~1;  // an even number: the one-pass sweeps end in the first buffer
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; i++) run(i);
+    cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float tot = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&tot, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    TK(err);
+    *ms = tot / reps;
+    return MG_OK;
+}
+
+// Finest-level sweep: MG_SWEEP_HALF, a forced one-pass shape, or the fastest
+// of the half-sweep pair and every one-pass shape that fits (cached like the
+// launch shapes).
+int tune_sweep(mg_handle *h)
+{
+    h->tile[MG_TILE_SWEEP][0] = 0;
+    if (!h->lev[0].x2 || h->L < 2 || first_tail_level(h) < 1) return MG_OK;
+    const int *n = h->lev[0].n;
+    const int forced = h->prm.sweep;
+    if (forced >= 0) {
+        h->tile[MG_TILE_SWEEP][0] = (signed char)((forced > 0 && sweep_fits(n, h->per, forced)) ? forced : 0);
+        return MG_OK;
+    }
+    TuneKey key;
+    memset(&key, 0, sizeof(key));
+    key.kind = MG_TILE_SWEEP;
+    key.mixed = h->mixed;
+    key.per = h->per;
+    for (int d = 0; d < 3; d++) key.n[d] = n[d];
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        env_cache_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            h->tile[MG_TILE_SWEEP][0] = (signed char)it->second;
+            return MG_OK;
+        }
+    }
+    float t[kSweepVariants];
+    for (int v = 0; v < kSweepVariants; v++) t[v] = -1.f;
+    for (int round = 0; round < 3; round++)
+        for (int v = 0; v < kSweepVariants; v++) {
+            if (v > 0 && !sweep_fits(n, h->per, v)) continue;
+            float ms = 0.f;
+            const int rc = h->mixed ? time_sweep<float>(h, v, &ms) : time_sweep<double>(h, v, &ms);
+            if (rc) return rc;
+            t[v] = (t[v] < 0.f || ms < t[v]) ? ms : t[v];
+        }
+    int best = 0;
+    for (int v = 1; v < kSweepVariants; v++)
+        if (t[v] >= 0.f && t[v] < t[best]) best = v;
+    h->tile[MG_TILE_SWEEP][0] = (signed char)best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    if (const char *path = env_cache_locked()) {
+        if (FILE *f = fopen(path, "a")) {
+            write_line(f, key, best);
+            fclose(f);
+        }
+    }
+    return MG_OK;
+}
+
 }  // namespace
 
 int tune_handle(mg_handle *h)
@@ -240,7 +362,7 @@ int tune_handle(mg_handle *h)
             }
         }
     }
-    return MG_OK;
+    return tune_sweep(h);
 }
 
 void tune_cache_clear()
@@ -255,8 +377,17 @@ extern "C" {
 
 int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant)
 {
-    if (!h || !variant || kind < 0 || kind > 2 || level < 0 || level >= h->L) return MG_EINVAL;
+    if (!h || !variant || kind < 0 || kind > MG_TILE_SWEEP || level < 0 || level >= h->L) return MG_EINVAL;
     *variant = level + 1 < h->L ? h->tile[kind][level] : 0;
+    return MG_OK;
+}
+
+int mg_sweep_shape(int variant, int *threads, int *planes)
+{
+    if (variant < 0 || variant >= gbmg::kSweepVariants || !threads || !planes) return MG_EINVAL;
+    const gbmg::SweepShape sh = gbmg::sweep_shape(variant);
+    *threads = sh.B;
+    *planes = sh.Kc;
     return MG_OK;
 }
 

@@ -31,7 +31,8 @@ SOLVER_MG, SOLVER_PCG = 0, 1
 COARSE_AUTO, COARSE_GMRES = 0, 1
 OUTER_FP64, OUTER_XP = 0, 1
 MAX_COARSE, MAX_COARSE_GMRES = 512, 32768
-TILE_HALF, TILE_RESTRICT, TILE_PROLONG = 0, 1, 2
+TILE_HALF, TILE_RESTRICT, TILE_PROLONG, TILE_SWEEP = 0, 1, 2, 3
+SWEEP_AUTO, SWEEP_HALF, SWEEP_VARIANTS = -1, 0, 7
 
 
 class MGError(RuntimeError):
@@ -51,7 +52,8 @@ class Params(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("solver", ctypes.c_int), ("prolongation", ctypes.c_int),
                 ("tiles", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_max_iters", ctypes.c_int),
-                ("coarse_tol", ctypes.c_double), ("adaptive_cycles", ctypes.c_int), ("outer", ctypes.c_int)]
+                ("coarse_tol", ctypes.c_double), ("adaptive_cycles", ctypes.c_int), ("outer", ctypes.c_int),
+                ("sweep", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -127,6 +129,8 @@ def lib():
             "mg_handle_params": (_I, [_V, _P(Params)]),
             "mg_probe_fp64_rate": (_I, [_I, _I, _P(_D), _V]),
             "mg_set_wait_limit": (_I, [_V, ctypes.c_longlong]),
+            "mg_sweep_shape": (_I, [_I, _P(_I), _P(_I)]),
+            "mg_smooth_onepass": (_I, [_V, _I, _I, _V, _V, _V, _I, _I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -161,7 +165,8 @@ def make_grid(shape, bc, length=(1.0, 1.0, 1.0)) -> Grid:
 
 def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True,
                 inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
-                coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None, outer=None) -> Params:
+                coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None, outer=None,
+                sweep=None) -> Params:
     p = Params()
     lib().mg_params_default(ctypes.byref(p))
     p.nu1, p.nu2, p.omega = int(nu1), int(nu2), float(omega)
@@ -186,7 +191,16 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
         p.adaptive_cycles = int(adaptive_cycles)
     if outer is not None:
         p.outer = int(outer)
+    if sweep is not None:
+        p.sweep = int(sweep)
     return p
+
+
+def sweep_shape(variant):
+    """(threads per block, planes per block) of one-pass sweep shape `variant`."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(lib().mg_sweep_shape(int(variant), ctypes.byref(a), ctypes.byref(b)), "mg_sweep_shape")
+    return (a.value, b.value)
 
 
 def tile_shape(variant):
@@ -272,7 +286,7 @@ class Solver:
     def __init__(self, shape, bc, faces=None, rho=None, face_mode=HARMONIC, length=(1.0, 1.0, 1.0),
                  precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_graph=True, stream=None,
                  inner_cycles=None, tiles=None, prolongation=None, solver=None, coarse_solver=None,
-                 coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None, outer=None):
+                 coarse_tol=None, coarse_max_iters=None, adaptive_cycles=None, outer=None, sweep=None):
         import torch
 
         self.shape = tuple(int(v) for v in shape)
@@ -283,7 +297,7 @@ class Solver:
         self.grid = make_grid(self.shape, self.bc, self.length)
         self.params = make_params(precision, nu1, nu2, omega, max_iters, use_graph, inner_cycles, tiles,
                                   prolongation, solver, coarse_solver, coarse_tol, coarse_max_iters,
-                                  adaptive_cycles, outer)
+                                  adaptive_cycles, outer, sweep)
         self._h = ctypes.c_void_p()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         if faces is None:
@@ -450,6 +464,12 @@ class Solver:
 
     def smooth(self, level, b, x, sweeps, prec=FP64):
         check(lib().mg_smooth(self._h, int(level), int(prec), _ptr(b), _ptr(x), int(sweeps)), "mg_smooth")
+
+    def smooth_onepass(self, level, b, x, work, sweeps, prec=FP64, variant=0):
+        """`sweeps` one-pass red-black sweeps alternating between x and work
+        (the result is in x after an even number, in work after an odd one)."""
+        check(lib().mg_smooth_onepass(self._h, int(level), int(prec), _ptr(b), _ptr(x), _ptr(work), int(sweeps),
+                                      int(variant)), "mg_smooth_onepass")
 
     def restrict_residual(self, level, b, x, coarse_b, prec=FP64):
         check(lib().mg_restrict_residual(self._h, int(level), int(prec), _ptr(b), _ptr(x), _ptr(coarse_b)),

@@ -97,6 +97,37 @@ def test_tile_shapes_and_params():
     assert gbmg.lib().mg_tune_cache_clear() == gbmg.OK
 
 
+def test_sweep_shapes_and_param():
+    """One-pass sweep shapes and the sweep parameter (host only)."""
+    L = gbmg.lib()
+    p = gbmg.Params()
+    assert L.mg_params_default(ctypes.byref(p)) == 0
+    assert p.sweep == gbmg.SWEEP_AUTO
+    assert gbmg.sweep_shape(0) == (0, 0)
+    shapes = [gbmg.sweep_shape(v) for v in range(1, gbmg.SWEEP_VARIANTS)]
+    assert len(set(shapes)) == gbmg.SWEEP_VARIANTS - 1
+    for threads, planes in shapes:
+        assert threads in (512, 1024) and planes >= 8
+    with pytest.raises(gbmg.MGError):
+        gbmg.sweep_shape(gbmg.SWEEP_VARIANTS)
+    g = gbmg.make_grid((64, 64, 64), (1, 1, 0))
+    size = ctypes.c_size_t()
+    est = {}
+    for sweep in (gbmg.SWEEP_AUTO, gbmg.SWEEP_HALF, 1, gbmg.SWEEP_VARIANTS - 1):
+        p.sweep = sweep
+        assert L.mg_memory_estimate(ctypes.byref(g), ctypes.byref(p), ctypes.byref(size)) == gbmg.OK
+        est[sweep] = size.value
+    # the one-pass sweep's second FP32 iterate buffer on the finest level
+    assert est[gbmg.SWEEP_AUTO] - est[gbmg.SWEEP_HALF] == 64 ** 3 * 4
+    for sweep in (-2, gbmg.SWEEP_VARIANTS):
+        p.sweep = sweep
+        assert L.mg_memory_estimate(ctypes.byref(g), ctypes.byref(p), ctypes.byref(size)) == gbmg.EINVAL
+    # odd nu: the sweeps must end in the first buffer, so no second buffer
+    p.sweep, p.nu1 = gbmg.SWEEP_AUTO, 1
+    assert L.mg_memory_estimate(ctypes.byref(g), ctypes.byref(p), ctypes.byref(size)) == gbmg.OK
+    assert size.value == est[gbmg.SWEEP_HALF]
+
+
 def test_tune_cache_file_roundtrip(tmp_path):
     """Saved launch-shape choices load back; bad lines are skipped (host only)."""
     src = tmp_path / "tune.txt"
@@ -104,14 +135,17 @@ def test_tune_cache_file_roundtrip(tmp_path):
                    "1 0 0 64 48 32 5\n"         # restriction, FP64
                    "garbage line\n"
                    "0 1 0 30 16 16 2\n"         # rows of 30 cells: flat shapes do not fit
-                   "2 1 0 64 64 64 9\n")        # no such shape
+                   "2 1 0 64 64 64 9\n"         # no such shape
+                   "3 1 3 128 128 128 2\n"      # one-pass sweep, FP32, periodic x y
+                   "3 1 3 128 127 128 2\n")     # odd periodic y: the one-pass sweep does not fit
     gbmg.tune_cache_clear()
     assert gbmg.tune_cache_size() == 0
-    assert gbmg.tune_cache_load(str(src)) == 2
-    assert gbmg.tune_cache_size() == 2
+    assert gbmg.tune_cache_load(str(src)) == 3
+    assert gbmg.tune_cache_size() == 3
     out = tmp_path / "out.txt"
     gbmg.tune_cache_save(str(out))
-    assert sorted(out.read_text().split("\n")[:-1]) == ["0 1 3 128 128 128 1", "1 0 0 64 48 32 5"]
+    assert sorted(out.read_text().split("\n")[:-1]) == ["0 1 3 128 128 128 1", "1 0 0 64 48 32 5",
+                                                        "3 1 3 128 128 128 2"]
     with pytest.raises(gbmg.MGError) as e:
         gbmg.tune_cache_load(str(tmp_path / "missing.txt"))
     assert e.value.code == gbmg.ENOTFOUND
