@@ -249,7 +249,7 @@ def single_config(args, P, world):
     return {"workload": WORKLOADS[args.workload]["desc"], "grid": list(P.shape),
             "bc": list(P.bc), "density_ratio": P.ratio, "tol": TOL,
             "precision": "mixed: FP32 V(2,2) red-black cycles inside FP64 iterative refinement",
-            "prolongation": args.prolongation, "solver": args.solver,
+            "prolongation": args.prolongation, "solver": args.solver, "sweep": args.sweep,
             "step": "set density (faces, coarse faces, coarsest inverse) + cold-start solve",
             "l2": "flushed before every step (256 MB write, outside the step events)",
             "parallelism": "replicas" if world > 1 else "single"}
@@ -264,8 +264,11 @@ def run_reference(args, name):
     """--impl reference: the FP64 CPU oracle as it stands, on the host cores.
     Small grids: one whole oracle solve to 1e-10 per step.  Larger grids: one
     oracle solve to 1e-10 first (untimed: it gives the cycles C a solve
-    needs), then every step is one oracle call of a single V(2,2) cycle (with
-    its set-up and residual norms), and solves/s = 1 / (C x mean step time)."""
+    needs), and one call that stops before its first cycle (its set-up: the
+    hierarchy, b - mean b and the starting residual, time s0); then every step
+    is one oracle call of a single V(2,2) cycle, a solve is estimated from
+    each step as s0 + C x (step time - s0), and solves/s = steps / the sum of
+    those estimates."""
     import oracle
     P = make_problem(name)
     faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
@@ -274,6 +277,9 @@ def run_reference(args, name):
     if not whole:
         t_full, r = cpu_oracle_solve(P, faces)
         C = r.cycles
+        t = time.perf_counter()
+        oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=0)
+        s0 = time.perf_counter() - t
     times = []
     for s in range(args.warmup + args.steps):
         if whole:
@@ -291,11 +297,12 @@ def run_reference(args, name):
             len(times), r.cycles)
         solve_s = [t for t in times]
     else:
-        value = len(times) / (tot * C)
-        sample = ("%d oracle calls of one V(2,2) cycle each (set-up and residual norms included) on the "
-                  "workload; a whole oracle solve to 1e-10 needs %d cycles (measured once before the "
-                  "steps: %.1f s); solves/s = 1 / (%d x mean step time)" % (len(times), C, t_full, C))
-        solve_s = [t * C for t in times]
+        solve_s = [s0 + C * max(t - s0, 0.0) for t in times]
+        value = len(times) / sum(solve_s)
+        sample = ("%d oracle calls of one V(2,2) cycle each on the workload; a whole oracle solve to 1e-10 "
+                  "needs %d cycles (one measured before the steps: %.1f s) and its set-up (hierarchy, "
+                  "b - mean b, starting residual) takes %.2f s (a call that stops before its first cycle); "
+                  "a solve = set-up + %d x (step time - set-up)" % (len(times), C, t_full, s0, C))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(times),
@@ -675,8 +682,10 @@ def run_single(args, rank, world, local_rank, dist):
     solvers = {}
     for key, prec, outer in modes:
         with torch.cuda.stream(stream):
+            sweep = {"auto": gbmg.SWEEP_AUTO, "half": gbmg.SWEEP_HALF}.get(args.sweep)
             solvers[key] = gbmg.Solver(P.shape, P.bc, rho=rho, precision=prec, stream=stream, outer=outer,
-                                       prolongation=PROLONG[args.prolongation], solver=SOLVER[args.solver])
+                                       prolongation=PROLONG[args.prolongation], solver=SOLVER[args.solver],
+                                       sweep=int(args.sweep) if sweep is None else sweep)
         S = solvers[key]
         timed(S, args.warmup)
         if dist is not None:
@@ -861,6 +870,9 @@ def main():
                     help="prolongation of the V-cycle: trilinear or flux-conserving (Sec. 2.3 item 4)")
     ap.add_argument("--solver", default="mg", choices=["mg", "pcg"],
                     help="outer iteration: V-cycles in FP64 refinement (mg) or V-cycle-preconditioned CG (pcg)")
+    ap.add_argument("--sweep", default="auto",
+                    help="finest-level red-black sweep of the single-grid workloads: auto (timed at create), "
+                         "half (two half-sweep launches) or a one-pass shape 1..6")
     ap.add_argument("--requests", type=int, default=500, help="serve_stream: requests in the stream")
     ap.add_argument("--load", type=float, nargs="+", default=[0.5, 0.8, 1.0],
                     help="serve_stream: arrival rates as fractions of the measured capacity of the mixed path")
