@@ -1091,19 +1091,35 @@ __global__ void __launch_bounds__(kThreads) k_sum(const OuterView *__restrict__ 
     // three-float one (summed in its internal scale)
     const bool conv = which == 1 && xp_live(O);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
-        if (!t.ok) continue;
-        const long long rowoff = (long long)O.n[0] * t.row;
-        for (int h = 0; h < 2; h++) {
-            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
-            if (i >= O.n[0]) continue;
-            const long long c = rowoff + i;
-            if (conv) {
-                v[0] += ((double)O.xp3[0][c] + (double)O.xp3[1][c]) + (double)O.xp3[2][c];
-            } else {
-                v[0] += src[c];
+    // kUnroll tiles of the block's grid-stride sequence per pass: every load of
+    // the pass is issued before the additions, which then run in the order of
+    // the sequence (one tile after the other, two cells per tile)
+    for (int tile = lb; tile < ntiles; tile += kUnroll * O.nblk) {
+        double val[kUnroll][2];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int tu = tile + u * O.nblk;
+            const Tile t = fine_tile(O.n, tu < ntiles ? tu : tile, O.dxt, O.xy);
+            const long long rowoff = (long long)O.n[0] * t.row;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+                const bool in = tu < ntiles && t.ok && i < O.n[0];
+                const long long c = rowoff + i;
+                double x = 0.0;
+                if (in) x = conv ? ((double)O.xp3[0][c] + (double)O.xp3[1][c]) + (double)O.xp3[2][c] : src[c];
+                val[u][h] = in ? x : 0.0;
             }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int tu = tile + u * O.nblk;
+            if (tu >= ntiles) break;
+            const Tile t = fine_tile(O.n, tu, O.dxt, O.xy);
+            if (!t.ok) continue;
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+                if (t.xbase + (threadIdx.x & 31) + 32 * h < O.n[0]) v[0] += val[u][h];
         }
     }
     double out[4];
@@ -1145,17 +1161,38 @@ __global__ void __launch_bounds__(kThreads) k_center_rhs(const OuterView *__rest
     const double m = O.st->bmean;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     int nz = 0;
-    for (int tile = lb; tile < ntiles; tile += O.nblk) {
-        const Tile t = fine_tile(O.n, tile, O.dxt, O.xy);
-        if (!t.ok) continue;
-        const long long rowoff = (long long)O.n[0] * t.row;
-        for (int h = 0; h < 2; h++) {
-            const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
-            if (i >= O.n[0]) continue;
-            const double bc = O.b[rowoff + i] - m;
-            O.b0[rowoff + i] = bc;
-            v[2] += bc * bc;
-            nz |= !(O.p[rowoff + i] == 0.0);
+    // loads of kUnroll tiles first, then the sequence's arithmetic in order (see k_sum)
+    for (int tile = lb; tile < ntiles; tile += kUnroll * O.nblk) {
+        double bv[kUnroll][2], pv[kUnroll][2];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int tu = tile + u * O.nblk;
+            const Tile t = fine_tile(O.n, tu < ntiles ? tu : tile, O.dxt, O.xy);
+            const long long rowoff = (long long)O.n[0] * t.row;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+                const bool in = tu < ntiles && t.ok && i < O.n[0];
+                bv[u][h] = in ? O.b[rowoff + i] : 0.0;
+                pv[u][h] = in ? O.p[rowoff + i] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int tu = tile + u * O.nblk;
+            if (tu >= ntiles) break;
+            const Tile t = fine_tile(O.n, tu, O.dxt, O.xy);
+            if (!t.ok) continue;
+            const long long rowoff = (long long)O.n[0] * t.row;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int i = t.xbase + (threadIdx.x & 31) + 32 * h;
+                if (i >= O.n[0]) continue;
+                const double bc = bv[u][h] - m;
+                O.b0[rowoff + i] = bc;
+                v[2] += bc * bc;
+                nz |= !(pv[u][h] == 0.0);
+            }
         }
     }
     double out[4];

@@ -10,6 +10,11 @@
 
 namespace gbmg {
 
+// Tiles of a block's grid-stride sequence whose loads the streaming outer
+// kernels k_sum and k_center_rhs issue together before using them (a sum's
+// order is unchanged: the additions run after the loads, in sequence order).
+constexpr int kUnroll = 4;
+
 // Deterministic block sum of up to 4 doubles; result valid in thread 0.
 __device__ __forceinline__ void block_sum4(double v[4], double *out)
 {
