@@ -113,8 +113,12 @@ def read_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources that define the profiled smoother kernels: the flat
+    half-sweep (mg_tiles.cu), the one-pass sweep (mg_fused.cu), the per-quad
+    relaxation they share (mg_stencil.cuh, mg_xprec.cuh) and the views and
+    launch helpers (mg_device.cuh, mg_launch.cuh)."""
     h = hashlib.sha256()
-    for f in ("mg_kernels.cu", "mg_tiles.cu", "mg_fused.cu", "mg_stencil.cuh", "mg_device.cuh", "mg_launch.cuh"):
+    for f in ("mg_tiles.cu", "mg_fused.cu", "mg_stencil.cuh", "mg_xprec.cuh", "mg_device.cuh", "mg_launch.cuh"):
         with open(os.path.join(ROOT, "paper_1410_8568_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
