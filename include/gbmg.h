@@ -386,7 +386,8 @@ int mg_coarse_solve(mg_handle *h, int prec, const void *r, void *e);
  * device looks up that array's device address; with CUDA's lazy module loading
  * that first call also loads this part of the library's device code (and its
  * static array), which can itself take device memory, so make the first call
- * once at start-up.  Later calls allocate and free nothing.  Every call on a
+ * on each device once at start-up, before any stream capture begins.  Later
+ * calls allocate and free nothing.  Every call on a
  * device shares the array and each call rewrites what it reads: calls whose
  * kernels can overlap on the GPU (unordered streams) race and must be
  * serialised by the caller.  Synchronous on `stream` (a cudaStream_t, NULL =

@@ -8,7 +8,8 @@
 // exactly, using only a scratch area that lives for the whole process in this
 // file's static device array.  The first call on a device looks up the
 // array's device address (and, with lazy module loading, loads this file's
-// device code); later calls allocate nothing.
+// device code): make it at start-up, before any stream capture begins; later
+// calls allocate nothing.
 //
 // The scratch array is shared by every call on a device and keeps the last
 // call's contents; the kernel rewrites everything it reads before reading it.

@@ -90,7 +90,10 @@ __device__ __forceinline__ void restrict_flat_entry(const LevelView &L, int lb, 
 }
 
 template <class T, int B, int Q>
-__global__ void __launch_bounds__(B) k_restrict_flat(const LevelView *__restrict__ lv,
+// at least 1024 threads per SM (64 registers a thread): the residuals of the
+// 4 fine rows hold many operands in flight, and unbounded the kernel took 86
+// registers and left DRAM 67 % busy at 29 % of the SM's warps
+__global__ void __launch_bounds__(B, 1024 / B) k_restrict_flat(const LevelView *__restrict__ lv,
                                                      const int *__restrict__ start, int count, int cyc,
                                                      T omega, const __grid_constant__ LevelView one,
                                                      int single)
