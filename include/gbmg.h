@@ -277,14 +277,20 @@ int mg_batch_destroy(mg_batch *b);
 /* ---------------------------------------------------------------------------
  * Serving: a request loop on a host thread that admits queued solves as slots
  * and device memory (an HBM budget) allow, keeps hierarchies of finished
- * requests for reuse by later requests of the same size, and advances all
- * admitted requests together one V-cycle at a time (continuous batching):
- * requests join and leave between cycles.
+ * requests for reuse by later requests of the same size, and advances the
+ * admitted requests of each size lane together one refinement step at a time
+ * (continuous batching): requests join and leave their lane between steps.
  * --------------------------------------------------------------------------- */
 
 /* hbm_budget_bytes: most device memory the server's hierarchies may hold;
  * max_slots: most requests on the GPU at once; params: precision etc. (NULL =
- * defaults); stream: cudaStream_t of the server's work (NULL = its own). */
+ * defaults); stream: NULL = the server's own streams, one per size lane (grids
+ * of up to 64^3, 128^3, 256^3 cells and larger; smaller grids at a higher
+ * stream priority), each lane stepping its requests one refinement step at a
+ * time at its own pace; a cudaStream_t = every request in one lane on that
+ * stream.  Test aid: with the environment variable MG_SERVER_FAIL_AT_STEP=n
+ * (read here) the server's n-th step launch reports MG_ECUDA without launching
+ * anything, a failure made on the host (see mg_server_drain). */
 int mg_server_create(size_t hbm_budget_bytes, int max_slots, const mg_params *params,
                      void *stream, mg_server **out);
 
@@ -301,7 +307,9 @@ int mg_submit(mg_server *s, const mg_grid *grid, const double *ax, const double 
  * latency from submission to completion. */
 int mg_poll(mg_server *s, mg_ticket t, mg_stats *st);
 
-/* Block until every submitted ticket has finished. */
+/* Block until every submitted ticket has finished.  Returns MG_OK, or the
+ * error of the first failed step since the server was created (the tickets
+ * that failed report it too; the server keeps serving later submissions). */
 int mg_server_drain(mg_server *s);
 
 /* Statistics of the server: completed requests, bytes of hierarchies held,
