@@ -103,6 +103,7 @@ struct Layout {
     int n[MG_MAX_LEVELS][3];
     size_t w64[MG_MAX_LEVELS][3], w32[MG_MAX_LEVELS][3], x[MG_MAX_LEVELS], b[MG_MAX_LEVELS];
     size_t x2;  // second iterate buffer of the finest level (one-pass sweep), 0 if none
+    size_t dinv[MG_MAX_LEVELS];  // FP64 cycles: inverse diagonals of the relaxed levels (0 if none)
     size_t alpha64[MG_MAX_LEVELS], alpha32[MG_MAX_LEVELS];
     size_t G, b0, part, err, state, dstate, dview, dstart, dcview, setup_cv, total;
     size_t pcg[4];
@@ -140,6 +141,8 @@ static int plan_layout(const mg_grid &g, const mg_params &p, Layout &lay)
         lay.x[l] = c.take(N * vs);
         lay.b[l] = c.take(N * vs);
         if (l == 0) lay.x2 = (lay.L > 1 && onepass_possible(g, p, lay.n[0])) ? c.take(N * vs) : 0;
+        // FP64 cycles relax every level but the coarsest with its inverse diagonal
+        lay.dinv[l] = (!mixed && l + 1 < lay.L) ? c.take(N * 8) : 0;
         const bool flux = l > 0 && p.prolongation == MG_PROLONG_FLUX;
         lay.alpha64[l] = flux ? c.take(N * 8) : 0;
         lay.alpha32[l] = (flux && mixed) ? c.take(N * 4) : 0;
@@ -343,6 +346,8 @@ int Plan::fill(mg_handle *const *handles, int count)
             for (int d = 0; d < 3; d++) v.wc[d] = mixed ? (const void *)C.w32[d] : (const void *)C.w64[d];
             fill_fastdiv(v);
             v.x2 = F.x2;
+            v.dinv = mixed ? nullptr : F.dinv;
+            v.dinvc = mixed ? nullptr : C.dinv;
             if (sv > 0) sw.push_back(sw.back() + sweep_layout(v, sv));
             sf.push_back(sf.back() + prolong_blocks_v(F.n, C.n, var[MG_TILE_PROLONG]));
             sc.push_back(sc.back() + restrict_blocks_v(F.n, C.n, var[MG_TILE_RESTRICT]));
@@ -1018,6 +1023,21 @@ static int upload_faces(mg_handle *h)
             launch_cell_alpha(c, h->stream);
         }
     }
+    // FP64 cycles: inverse diagonals of the levels that are relaxed
+    for (int l = 0; l < h->L; l++) {
+        if (!h->lev[l].dinv) continue;
+        DiagArgs a;
+        memset(&a, 0, sizeof(a));
+        for (int d = 0; d < 3; d++) {
+            a.n[d] = h->lev[l].n[d];
+            a.w[d] = h->lev[l].w64[d];
+        }
+        a.per = h->per;
+        a.out = h->lev[l].dinv;
+        a.dx = make_fastdiv((unsigned)a.n[0]);
+        a.dy = make_fastdiv((unsigned)a.n[1]);
+        launch_diag_inv(a, h->stream);
+    }
     if (!h->gmres) launch_coarse_setup(h->setup_cv, 1, h->stream);
     CK(cudaGetLastError());
     return MG_OK;
@@ -1116,6 +1136,7 @@ int gbmg::handle_alloc(const mg_grid *grid, const mg_params *params, void *strea
         L.N = (long long)L.n[0] * L.n[1] * L.n[2];
         L.x = h->slab + lay.x[l];
         L.x2 = (l == 0 && lay.x2) ? (void *)(h->slab + lay.x2) : nullptr;
+        L.dinv = lay.dinv[l] ? (double *)(h->slab + lay.dinv[l]) : nullptr;
         L.alpha64 = lay.alpha64[l] ? (double *)(h->slab + lay.alpha64[l]) : nullptr;
         L.alpha32 = lay.alpha32[l] ? (float *)(h->slab + lay.alpha32[l]) : nullptr;
         L.b = h->slab + lay.b[l];
@@ -1581,6 +1602,9 @@ static int unit_view(mg_handle *h, int level, int prec, const void *x, void *b,
     v.ac = level + 1 >= h->L ? nullptr
            : prec == MG_PREC_MIXED ? (const void *)h->lev[level + 1].alpha32
                                    : (const void *)h->lev[level + 1].alpha64;
+    // FP64 unit calls on an FP64 handle relax as its solves do (inverse diagonals)
+    v.dinv = prec == MG_PREC_FP64 ? L.dinv : nullptr;
+    v.dinvc = (prec == MG_PREC_FP64 && level + 1 < h->L) ? h->lev[level + 1].dinv : nullptr;
     fill_fastdiv(v);
     // the shape the handle's solves use on this level (not on the coarsest)
     const int kind = tiles == kCoarseTiles ? MG_TILE_RESTRICT : tiles == kProlongTiles ? MG_TILE_PROLONG
@@ -1646,6 +1670,7 @@ int mg_smooth_onepass(mg_handle *h, int level, int prec, const void *b, void *x,
     v.x2 = work;
     v.b = (void *)b;
     v.st = h->dstate;
+    v.dinv = prec == MG_PREC_FP64 ? L.dinv : nullptr;
     fill_fastdiv(v);
     const int blocks = sweep_layout(v, variant);
     const int starts[2] = {0, blocks};

@@ -35,6 +35,7 @@ struct HLevel {
     void *x;         // V-cycle iterate / correction (V-cycle precision)
     void *x2;        // finest level: second iterate buffer of the one-pass sweep (or null)
     void *b;         // V-cycle right-hand side (V-cycle precision)
+    double *dinv;    // FP64 cycles: inverse diagonal 1 / (sum of the cell's faces), levels below the coarsest
     double *alpha64; // cell coefficients (flux-conserving prolongation, levels >= 1), FP64
     float *alpha32;  // FP32 copy (mixed precision only)
 };

@@ -174,6 +174,11 @@ struct LevelView {
     void *x2;
     int fR, fKc, fS;
     FastDiv dfS, dfq;
+    // FP64 cycles: inverse diagonals (1 / sum of the cell's face coefficients,
+    // 0 for a cell without faces) of this level and of the next coarser one;
+    // null in FP32 cycles (and for FP64 unit calls on a mixed-precision handle)
+    const void *dinv;
+    const void *dinvc;
 };
 
 // The finest level of one grid for the FP64 outer iteration.

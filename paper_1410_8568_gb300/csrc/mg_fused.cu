@@ -33,7 +33,8 @@ template <class T>
 __device__ __forceinline__ Quad<T> relax_quad_global(const T *__restrict__ x, const T *__restrict__ b,
                                                      const T *__restrict__ wx, const T *__restrict__ wy,
                                                      const T *__restrict__ wz, int nx, int ny, int nz, int per,
-                                                     int j, int k, int qx, int colour, T omega, bool zero)
+                                                     int j, int k, int qx, int colour, T omega, bool zero,
+                                                     const T *__restrict__ dinv)
 {
     const int sy = nx, sz = nx * ny;
     const int i0 = qx << 2;
@@ -85,8 +86,15 @@ __device__ __forceinline__ Quad<T> relax_quad_global(const T *__restrict__ x, co
     const T xl1 = par ? xq.v[2] : xq.v[1], xr1 = par ? xe : xq.v[3];
     const T fl0 = par ? fx.v[1] : fx.v[0], fr0 = par ? fx.v[2] : fx.v[1];
     const T fl1 = par ? fx.v[3] : fx.v[2], fr1 = par ? fxe : fx.v[3];
-    const T v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega);
-    const T v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega);
+    T v0, v1;
+    if (sizeof(T) == 8 && dinv != nullptr) {
+        const T di0 = dinv[c0], di1 = dinv[c0 + 2];
+        v0 = relax_cell_inv(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega, di0);
+        v1 = relax_cell_inv(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega, di1);
+    } else {
+        v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega);
+        v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega);
+    }
     Quad<T> out = xq;
     out.v[0] = par ? xq.v[0] : v0;
     out.v[1] = par ? v0 : xq.v[1];
@@ -105,7 +113,7 @@ __device__ __forceinline__ Quad<T> black_quad(const Quad<T> &xq, const T *orow, 
                                               const Quad<T> &xbq, const Quad<T> &xtq, const T *__restrict__ b,
                                               const T *__restrict__ wx, const T *__restrict__ wy,
                                               const T *__restrict__ wz, int nx, int ny, int nz, int per, int j,
-                                              int k, int qx, T omega)
+                                              int k, int qx, T omega, const T *__restrict__ dinv)
 {
     const int sy = nx, sz = nx * ny;
     const int i0 = qx << 2;
@@ -137,8 +145,15 @@ __device__ __forceinline__ Quad<T> black_quad(const Quad<T> &xq, const T *orow, 
     const T xl1 = par ? xq.v[2] : xq.v[1], xr1 = par ? xe : xq.v[3];
     const T fl0 = par ? fx.v[1] : fx.v[0], fr0 = par ? fx.v[2] : fx.v[1];
     const T fl1 = par ? fx.v[3] : fx.v[2], fr1 = par ? fxe : fx.v[3];
-    const T v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega);
-    const T v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega);
+    T v0, v1;
+    if (sizeof(T) == 8 && dinv != nullptr) {
+        const T di0 = dinv[c0], di1 = dinv[c0 + 2];
+        v0 = relax_cell_inv(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega, di0);
+        v1 = relax_cell_inv(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega, di1);
+    } else {
+        v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega);
+        v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega);
+    }
     Quad<T> out = xq;
     out.v[0] = par ? xq.v[0] : v0;
     out.v[1] = par ? v0 : xq.v[1];
@@ -161,6 +176,7 @@ __device__ __forceinline__ void sweep_body(const LevelView &L, int lb, int dir, 
     const T *__restrict__ wx = (const T *)L.w[0];
     const T *__restrict__ wy = (const T *)L.w[1];
     const T *__restrict__ wz = (const T *)L.w[2];
+    const T *__restrict__ dinv = sizeof(T) == 8 ? (const T *)L.dinv : nullptr;
     const int R = L.fR, S = L.fS;
     const int chunk = fdiv(lb, L.dfS), strip = lb - chunk * S;
     const int j0 = strip * R, k0 = chunk * L.fKc;
@@ -193,7 +209,7 @@ __device__ __forceinline__ void sweep_body(const LevelView &L, int lb, int dir, 
             else vpl = false;
         }
         if (vrow && vpl) {
-            q0 = relax_quad_global<T>(xin, b, wx, wy, wz, nx, ny, nz, per, jj, kk, tq, 0, omega, zero);
+            q0 = relax_quad_global<T>(xin, b, wx, wy, wz, nx, ny, nz, per, jj, kk, tq, 0, omega, zero, dinv);
             stq(sm + rk * rowlen + tr * nx + (tq << 2), q0);
         }
         __syncthreads();
@@ -202,7 +218,7 @@ __device__ __forceinline__ void sweep_body(const LevelView &L, int lb, int dir, 
             const int rp = rk == 0 ? 2 : rk - 1;  // ring slot of plane k - 1
             const T *plane = sm + rp * rowlen;
             const Quad<T> out = black_quad<T>(q1, plane + tr * nx, plane + (tr - 1) * nx, plane + (tr + 1) * nx,
-                                              q2, q0, b, wx, wy, wz, nx, ny, nz, per, j, kb, tq, omega);
+                                              q2, q0, b, wx, wy, wz, nx, ny, nz, per, j, kb, tq, omega, dinv);
             const int c = (j + ny * kb) * nx + (tq << 2);
             stq(xout + c, out);
             if constexpr (OUT) add_outer_quad<T>(po, c, out.v, 0xF);

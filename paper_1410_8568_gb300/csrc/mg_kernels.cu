@@ -159,15 +159,21 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
                 continue;
             }
             const long long c = (long long)nx * t.row + i;
+            const T *di = (sizeof(T) == 8) ? (const T *)L.dinv : nullptr;
             T v;
             if (zero) {
-                const T d = diag_of(wx, wy, wz, nx, ny, nz, per, i, t.j, t.k, c);
-                v = d > T(0) ? omega * relax_div(-b[c], d) : T(0);
+                if (di) {
+                    v = di[c] > T(0) ? omega * ((-b[c]) * di[c]) : T(0);
+                } else {
+                    const T d = diag_of(wx, wy, wz, nx, ny, nz, per, i, t.j, t.k, c);
+                    v = d > T(0) ? omega * relax_div(-b[c], d) : T(0);
+                }
             } else {
                 const T xc = x[c];
                 T d, f;
                 stencil(wx, wy, wz, LoadPlain<T>{x}, nx, ny, nz, per, i, t.j, t.k, c, xc, d, f);
-                v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
+                if (di) v = di[c] > T(0) ? xc + omega * ((f - b[c]) * di[c]) : xc;
+                else v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
             }
             x[c] = v;
             if constexpr (OUT) add_outer<T>(po, (int)c, v);
@@ -185,7 +191,8 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
     const int qx = (tq << 5) + (threadIdx.x & 31);
     if (qx >= nq) return;
     const int k = fdiv(row, L.dy);
-    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row - k * ny, k, qx, colour, omega, zero, po, go);
+    half_quad<T, OUT>(x, b, wx, wy, wz, nx, ny, nz, per, row, row - k * ny, k, qx, colour, omega, zero, po, go,
+                      (const T *)L.dinv);
 }
 
 // MAYOUT: the launch carries kOuter; the test of the step's last cycle is
@@ -1018,6 +1025,29 @@ __global__ void __launch_bounds__(kThreads) k_project(ProjArgs a)
     }
 }
 
+// 1 / (sum of the cell's 6 face coefficients), summed in relax_cell's order
+// (x low, x high, y low, y high, z low, z high; a wall's face is 0), so that
+// relax_cell_inv relaxes against the same diagonal; 0 for a cell without faces.
+__global__ void __launch_bounds__(kThreads) k_diag_inv(DiagArgs a)
+{
+    dep_entry();
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2], per = a.per;
+    const int N = nx * ny * nz, sy = nx, sz = nx * ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int rest = fdiv(c, a.dx);
+        const int i = c - rest * nx;
+        const int k = fdiv(rest, a.dy);
+        const int j = rest - k * ny;
+        double d = a.w[0][c];
+        d += i + 1 < nx ? a.w[0][c + 1] : ((per & 1) ? a.w[0][c + 1 - nx] : 0.0);
+        d += a.w[1][c];
+        d += j + 1 < ny ? a.w[1][c + sy] : ((per & 2) ? a.w[1][c - sy * (ny - 1)] : 0.0);
+        d += a.w[2][c];
+        d += k + 1 < nz ? a.w[2][c + sz] : ((per & 4) ? a.w[2][c - sz * (nz - 1)] : 0.0);
+        a.out[c] = d > 0.0 ? 1.0 / d : 0.0;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_coarsen_faces(CoarsenArgs a)
 {
     dep_entry();
@@ -1709,6 +1739,10 @@ void launch_divergence(const ProjArgs &a, cudaStream_t s)
 void launch_project(const ProjArgs &a, cudaStream_t s)
 {
     launch_k(k_project, cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s, a);
+}
+void launch_diag_inv(const DiagArgs &a, cudaStream_t s)
+{
+    launch_k(k_diag_inv, cells_grid((long long)a.n[0] * a.n[1] * a.n[2]), kThreads, 0, s, a);
 }
 void launch_coarsen_faces(const CoarsenArgs &a, cudaStream_t s)
 {

@@ -67,6 +67,16 @@ struct ProjArgs {
     double *S;            // divergence / dt (divergence: written)
 };
 
+// inverse diagonal of a level for the FP64 relaxation: out = 1 / d, d the sum
+// of the cell's face coefficients (relax_cell's order), 0 where d <= 0
+struct DiagArgs {
+    int n[3];
+    int per;
+    const double *w[3];  // scaled FP64 faces of the level
+    double *out;
+    FastDiv dx, dy;      // division by n[0] and by n[1]
+};
+
 struct CoarsenArgs {
     int nf[3];
     int nc[3];
@@ -123,6 +133,7 @@ void launch_coarse_setup(const CoarseView *, int count, cudaStream_t);
 void launch_faces_from_density(const FaceArgs &, cudaStream_t);
 void launch_scale_faces(const FaceArgs &, cudaStream_t);
 void launch_coarsen_faces(const CoarsenArgs &, cudaStream_t);
+void launch_diag_inv(const DiagArgs &, cudaStream_t);
 void launch_cell_alpha(const AlphaArgs &, cudaStream_t);
 void launch_divergence(const ProjArgs &, cudaStream_t);
 void launch_project(const ProjArgs &, cudaStream_t);

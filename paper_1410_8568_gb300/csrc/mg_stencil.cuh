@@ -103,6 +103,25 @@ __device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn
     return d > T(0) ? xc + omega * relax_div(f - bc, d) : xc;
 }
 
+// The same relaxation for FP64 cycles, with the cell's diagonal given by its
+// inverse di = 1 / d (d summed as relax_cell sums it; 0 for a cell without
+// faces), computed once per coefficient set: a multiply in place of the FP64
+// division, which this GPU issues as a long sequence on its narrow FP64 pipe.
+// f is accumulated in relax_cell's order.
+template <class T>
+__device__ __forceinline__ T relax_cell_inv(T xc, T xl, T xr, T fl, T fr, T fs, T fn, T fb, T ft, T xs,
+                                            T xn, T xb, T xt, T bc, T omega, T di)
+{
+    T f;
+    f = fl * (xl - xc);
+    f += fr * (xr - xc);
+    f += fs * (xs - xc);
+    f += fn * (xn - xc);
+    f += fb * (xb - xc);
+    f += ft * (xt - xc);
+    return di > T(0) ? xc + omega * ((f - bc) * di) : xc;
+}
+
 // Add the final correction v of cell c of a refinement step to the outer
 // iterate: p += v / xscale in FP64 (the scale a power of 2, so exact), or the
 // exact three-float update in the scaled units (FP32 cycles with the
@@ -160,11 +179,12 @@ __device__ __forceinline__ void add_outer_quad(const OuterOut &o, int c, const T
 // per block).
 // go: store the result (false: a grid that sits this cycle out; the loads are
 // issued before its state is known, so they overlap that load's latency).
+// dinv: FP64 cycles, the level's inverse diagonals (relax_cell_inv), or null.
 template <class T, bool OUT>
 __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T *wy, const T *wz,
                                           int nx, int ny, int nz, int per, int row, int j, int k,
                                           int qx, int colour, T omega, bool zero, const OuterOut &po,
-                                          bool go = true)
+                                          bool go = true, const T *dinv = nullptr)
 {
     // cell indices fit in 32 bits: a grid has fewer than 2^31 cells
     const int sy = nx, sz = nx * ny;
@@ -218,8 +238,15 @@ __device__ __forceinline__ void half_quad(T *x, const T *b, const T *wx, const T
     const T xl1 = par ? xq.v[2] : xq.v[1], xr1 = par ? xe : xq.v[3];
     const T fl0 = par ? fx.v[1] : fx.v[0], fr0 = par ? fx.v[2] : fx.v[1];
     const T fl1 = par ? fx.v[3] : fx.v[2], fr1 = par ? fxe : fx.v[3];
-    const T v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega);
-    const T v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega);
+    T v0, v1;
+    if (sizeof(T) == 8 && dinv != nullptr) {
+        const T di0 = dinv[c0], di1 = dinv[c0 + 2];
+        v0 = relax_cell_inv(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega, di0);
+        v1 = relax_cell_inv(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega, di1);
+    } else {
+        v0 = relax_cell(xc0, xl0, xr0, fl0, fr0, fs0, fn0, fb0, ft0, xs0, xn0, xb0, xt0, b0, omega);
+        v1 = relax_cell(xc1, xl1, xr1, fl1, fr1, fs1, fn1, fb1, ft1, xs1, xn1, xb1, xt1, b1, omega);
+    }
     Quad<T> out = xq;
     out.v[0] = par ? xq.v[0] : v0;
     out.v[1] = par ? v0 : xq.v[1];
@@ -439,6 +466,11 @@ __device__ __forceinline__ T zero_start_red(const LevelView &L, int I, int J, in
     const int nx = L.nc[0], ny = L.nc[1], nz = L.nc[2], per = L.per;
     const int sy = nx, sz = nx * ny;
     const int c = I + nx * (J + ny * K);
+    if (sizeof(T) == 8 && L.dinvc != nullptr) {
+        // FP64 cycles: the coarse level's inverse diagonal (see relax_cell_inv)
+        const T di = ((const T *)L.dinvc)[c];
+        return di > T(0) ? omega * ((-bc) * di) : T(0);
+    }
     const T *wx = (const T *)L.wc[0], *wy = (const T *)L.wc[1], *wz = (const T *)L.wc[2];
     T d = wx[c];
     if (I + 1 < nx) d += wx[c + 1];

@@ -29,7 +29,7 @@ __device__ __forceinline__ void half_flat_body(const LevelView &L, int lb, int c
         const int k = fdiv(row, L.dy);
         half_quad<T, OUT>((T *)L.x, (const T *)L.b, (const T *)L.w[0], (const T *)L.w[1],
                           (const T *)L.w[2], nx, ny, nz, L.per, row, row - k * ny, k, g - row * nq, colour,
-                          omega, zero, po, go);
+                          omega, zero, po, go, (const T *)L.dinv);
     }
 }
 

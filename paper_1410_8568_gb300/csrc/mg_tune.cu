@@ -146,6 +146,8 @@ int time_shape(mg_handle *h, int kind, int l, int v, float *ms)
     lv.xc = C.x;
     lv.bc = C.b;
     lv.st = h->dstate;
+    lv.dinv = h->mixed ? nullptr : F.dinv;
+    lv.dinvc = h->mixed ? nullptr : C.dinv;
     fill_fastdiv(lv);
     const int blocks = kernel_blocks(kind, lv.n, lv.nc, v);
     const int starts[2] = {0, blocks};
@@ -208,6 +210,8 @@ int time_sweep(mg_handle *h, int v, float *ms)
     lv.xc = C.x;
     lv.bc = C.b;
     lv.st = h->dstate;
+    lv.dinv = h->mixed ? nullptr : F.dinv;
+    lv.dinvc = h->mixed ? nullptr : C.dinv;
     fill_fastdiv(lv);
     const int hv = h->tile[MG_TILE_HALF][0];
     const int blocks = v > 0 ? sweep_layout(lv, v) : half_sweep_blocks_v(lv.n, hv);
