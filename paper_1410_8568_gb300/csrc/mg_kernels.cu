@@ -172,7 +172,7 @@ __device__ __forceinline__ void half_body(const LevelView &L, int lb, int colour
                 const T xc = x[c];
                 T d, f;
                 stencil(wx, wy, wz, LoadPlain<T>{x}, nx, ny, nz, per, i, t.j, t.k, c, xc, d, f);
-                if (di) v = di[c] > T(0) ? xc + omega * ((f - b[c]) * di[c]) : xc;
+                if (di) v = di[c] > T(0) ? xc + omega * ((f - b[c]) * di[c]) : xc;  // (rows of other than whole quads)
                 else v = d > T(0) ? xc + omega * relax_div(f - b[c], d) : xc;
             }
             x[c] = v;

@@ -103,23 +103,27 @@ __device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn
     return d > T(0) ? xc + omega * relax_div(f - bc, d) : xc;
 }
 
-// The same relaxation for FP64 cycles, with the cell's diagonal given by its
-// inverse di = 1 / d (d summed as relax_cell sums it; 0 for a cell without
-// faces), computed once per coefficient set: a multiply in place of the FP64
-// division, which this GPU issues as a long sequence on its narrow FP64 pipe.
-// f is accumulated in relax_cell's order.
+// The relaxation of FP64 cycles, with the cell's diagonal given by its inverse
+// di = 1 / d (d summed as relax_cell sums it; 0 for a cell without faces),
+// computed once per coefficient set: the Gauss-Seidel value
+// g = (sum of w_f x_nb - b) di, then x = g (omega = 1) or xc + omega (g - xc).
+// Eight FP64 operations per cell at omega = 1 (six fused multiply-adds, a
+// subtraction, a multiply) where the difference form with a division takes
+// about thirty; this GPU issues FP64 on a narrow pipe, which bounds the FP64
+// half-sweep.  The neighbours are summed in relax_cell's order.
 template <class T>
 __device__ __forceinline__ T relax_cell_inv(T xc, T xl, T xr, T fl, T fr, T fs, T fn, T fb, T ft, T xs,
                                             T xn, T xb, T xt, T bc, T omega, T di)
 {
-    T f;
-    f = fl * (xl - xc);
-    f += fr * (xr - xc);
-    f += fs * (xs - xc);
-    f += fn * (xn - xc);
-    f += fb * (xb - xc);
-    f += ft * (xt - xc);
-    return di > T(0) ? xc + omega * ((f - bc) * di) : xc;
+    T s = fl * xl;
+    s = fma(fr, xr, s);
+    s = fma(fs, xs, s);
+    s = fma(fn, xn, s);
+    s = fma(fb, xb, s);
+    s = fma(ft, xt, s);
+    const T g = (s - bc) * di;
+    if (!(di > T(0))) return xc;
+    return omega == T(1) ? g : fma(omega, g - xc, xc);
 }
 
 // Add the final correction v of cell c of a refinement step to the outer
