@@ -114,11 +114,12 @@ def read_peaks():
 
 def kernel_source_hash():
     """Hash of the sources that define the profiled smoother kernels: the flat
-    half-sweep (mg_tiles.cu), the one-pass sweep (mg_fused.cu), the per-quad
+    half-sweep (mg_tiles.cu), the one-pass sweeps (mg_fused.cu, mg_staged.cu), the per-quad
     relaxation they share (mg_stencil.cuh, mg_xprec.cuh) and the views and
     launch helpers (mg_device.cuh, mg_launch.cuh)."""
     h = hashlib.sha256()
-    for f in ("mg_tiles.cu", "mg_fused.cu", "mg_stencil.cuh", "mg_xprec.cuh", "mg_device.cuh", "mg_launch.cuh"):
+    for f in ("mg_tiles.cu", "mg_fused.cu", "mg_staged.cu", "mg_stencil.cuh", "mg_xprec.cuh", "mg_device.cuh",
+              "mg_launch.cuh"):
         with open(os.path.join(ROOT, "paper_1410_8568_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -837,7 +838,8 @@ def run_single(args, rank, world, local_rank, dist):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": ("FP32 one-pass red-black sweep of level 0 (both colours in one launch), "
-                                    "shape %d (%d threads, %d planes per block)" % ((sv,) + gbmg.sweep_shape(sv)))
+                                    "shape %d (%d threads, %d planes per block, tile of %d cells along x; "
+                                    "0: whole rows)" % ((sv,) + gbmg.sweep_shape(sv)))
                                    if sv > 0 else
                                    ("FP32 half-sweep of level 0 (one red or black colour), launch shape %d "
                                     "(%d threads x %d quads)" % ((v0,) + gbmg.tile_shape(v0))),

@@ -118,7 +118,7 @@ extern "C" {
 #define MG_TILE_SWEEP 3      /* finest-level full red-black sweep (0 = two half-sweep launches) */
 #define MG_SWEEP_AUTO (-1)   /* mg_params.sweep: timed at create */
 #define MG_SWEEP_HALF 0      /* mg_params.sweep: two half-sweep launches per sweep */
-#define MG_SWEEP_VARIANTS 7  /* one-pass sweep shapes 1 .. 6 (see mg_sweep_shape) */
+#define MG_SWEEP_VARIANTS 11 /* one-pass sweep shapes 1 .. 10 (see mg_sweep_shape) */
 
 typedef struct {
     int nx, ny, nz;     /* cells per axis */
@@ -159,8 +159,9 @@ typedef struct {
                               fit, timed at create), MG_SWEEP_HALF, or a one-pass shape
                               1 .. MG_SWEEP_VARIANTS - 1 (used where it fits, else MG_SWEEP_HALF).
                               The one-pass sweep needs even nu1 and nu2 and a second iterate buffer
-                              on the finest level (4 B per cell mixed, 8 B FP64); every choice gives
-                              bitwise the same result */
+                              on the finest level (4 B per cell mixed, 8 B FP64); the staged shapes
+                              (tile_x of mg_sweep_shape nonzero) run in FP32 cycles only.  Every
+                              choice gives bitwise the same result */
 } mg_params;
 
 typedef struct {
@@ -361,9 +362,11 @@ int mg_restrict_residual(mg_handle *h, int level, int prec, const void *b, const
  * 2 reads work and writes x, and so on (after an even number the result is in
  * x, after an odd number in work).  Bitwise the result of mg_smooth.  variant:
  * a one-pass shape 1 .. MG_SWEEP_VARIANTS - 1, or 0 for the handle's tuned
- * choice on that level.  MG_EINVAL if the shape does not fit the level (rows
- * of a multiple of 4 cells, at most a third of the shape's threads quads per
- * row, an even number of cells along a periodic y or z axis). */
+ * choice on that level.  MG_EINVAL if the shape does not fit the level: an
+ * even number of cells along a periodic y or z axis, and for a whole-row shape
+ * rows of a multiple of 4 cells, at most a third of the shape's threads quads
+ * per row; for a staged shape rows of a multiple of its tile_x cells and
+ * prec = MG_PREC_MIXED. */
 int mg_smooth_onepass(mg_handle *h, int level, int prec, const void *b, void *x, void *work, int sweeps,
                       int variant);
 
@@ -480,11 +483,16 @@ int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant);
  * reports 256 threads, 1 item). */
 int mg_tile_shape(int variant, int *threads, int *items_per_thread);
 
-/* Threads per block and planes per block of one-pass sweep shape `variant`
- * (1 .. MG_SWEEP_VARIANTS - 1; 0 reports 0, 0).  A block owns a strip of full
- * rows (as many as the threads allow at one thread per 4-cell quad, less the
- * two halo rows whose red cells it recomputes) of a chunk of planes. */
-int mg_sweep_shape(int variant, int *threads, int *planes);
+/* Threads per block, planes per block and tile width of one-pass sweep shape
+ * `variant` (1 .. MG_SWEEP_VARIANTS - 1; 0 reports 0, 0, 0).  tile_x = 0: a
+ * block owns a strip of full rows (as many as the threads allow at one thread
+ * per 4-cell quad, less the two halo rows whose red cells it recomputes) of a
+ * chunk of planes, and reads its operands from global memory.  tile_x > 0
+ * (staged shapes, FP32 cycles): a block owns a tile of tile_x cells along x
+ * and up to 14 rows of a chunk of planes, and copies each plane of its
+ * operands (with the halo cells it recomputes) into shared memory two planes
+ * ahead of the relaxation. */
+int mg_sweep_shape(int variant, int *threads, int *planes, int *tile_x);
 
 /* Forget every cached choice (the next mg_create times again). */
 int mg_tune_cache_clear(void);

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgbmg.so")
 SOURCES = ["mg_kernels.cu", "mg_tiles.cu", "mg_pcg.cu", "mg_gmres.cu", "mg_api.cu", "mg_tune.cu", "mg_server.cu",
-           "mg_static.cu", "mg_probe.cu", "mg_fused.cu"]
+           "mg_static.cu", "mg_probe.cu", "mg_fused.cu", "mg_staged.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

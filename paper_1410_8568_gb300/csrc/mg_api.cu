@@ -123,7 +123,7 @@ static bool onepass_possible(const mg_grid &g, const mg_params &p, const int n[3
     const int per = (g.bc[0] == MG_BC_PERIODIC ? 1 : 0) | (g.bc[1] == MG_BC_PERIODIC ? 2 : 0) |
                     (g.bc[2] == MG_BC_PERIODIC ? 4 : 0);
     for (int v = 1; v < kSweepVariants; v++)
-        if (sweep_fits(n, per, v)) return true;
+        if (sweep_fits(n, per, v, p.precision == MG_PREC_MIXED)) return true;
     return false;
 }
 
@@ -315,7 +315,7 @@ int Plan::fill(mg_handle *const *handles, int count)
             for (int g = 0; g < G && sv > 0; g++) {
                 mg_handle *h = hs[g];
                 if (l + 1 >= h->L || l >= lt[g]) continue;
-                if (!h->lev[0].x2 || !sweep_fits(h->lev[0].n, h->per, sv)) sv = 0;
+                if (!h->lev[0].x2 || !sweep_fits(h->lev[0].n, h->per, sv, h->mixed)) sv = 0;
             }
         }
         // three prefix arrays (four on the finest level), each count + 1 long,
@@ -1658,7 +1658,7 @@ int mg_smooth_onepass(mg_handle *h, int level, int prec, const void *b, void *x,
     if (prec == MG_PREC_MIXED && !h->mixed) return MG_EINVAL;
     if (variant == 0) variant = level == 0 ? h->tile[MG_TILE_SWEEP][0] : 0;
     const HLevel &L = h->lev[level];
-    if (!sweep_fits(L.n, h->per, variant)) return MG_EINVAL;
+    if (!sweep_fits(L.n, h->per, variant, prec == MG_PREC_MIXED)) return MG_EINVAL;
     LevelView v;
     memset(&v, 0, sizeof(v));
     for (int d = 0; d < 3; d++) {

@@ -124,23 +124,30 @@ __host__ __device__ constexpr TileShape tile_shape(int v)
                   : TileShape{kThreads, 1};
 }
 
-// Launch shapes of the one-pass red-black sweep (mg_fused.cu): B threads per
-// block (a thread per quad of each row of a strip of rows, 2 halo rows
-// included) and Kc planes per block (a chunk of the z march).  Variant 0 is
-// no one-pass sweep (two half-sweep launches per sweep).
-constexpr int kSweepVariants = 7;
+// Launch shapes of the one-pass red-black sweep: B threads per block and Kc
+// planes per block (a chunk of the z march).  Variants 1 .. 6 (mg_fused.cu):
+// a block owns a strip of full rows, a thread per quad of each row of the
+// strip (2 halo rows included).  Variants 7 .. 10 (mg_staged.cu, FP32 cycles):
+// a block owns a tile of tile_x = 128 cells of up to 14 rows and stages its
+// operands in shared memory.  Variant 0 is no one-pass sweep (two half-sweep
+// launches per sweep).
+constexpr int kSweepVariants = 11;
 struct SweepShape {
-    int B, Kc;
+    int B, Kc, tile_x;  // tile_x: cells of a block's tile along x, 0 for whole rows
 };
 __host__ __device__ constexpr SweepShape sweep_shape(int v)
 {
-    return v == 1 ? SweepShape{1024, 16}
-         : v == 2 ? SweepShape{1024, 32}
-         : v == 3 ? SweepShape{1024, 64}
-         : v == 4 ? SweepShape{512, 16}
-         : v == 5 ? SweepShape{512, 32}
-         : v == 6 ? SweepShape{512, 64}
-                  : SweepShape{0, 0};
+    return v == 1  ? SweepShape{1024, 16, 0}
+         : v == 2  ? SweepShape{1024, 32, 0}
+         : v == 3  ? SweepShape{1024, 64, 0}
+         : v == 4  ? SweepShape{512, 16, 0}
+         : v == 5  ? SweepShape{512, 32, 0}
+         : v == 6  ? SweepShape{512, 64, 0}
+         : v == 7  ? SweepShape{544, 64, 128}
+         : v == 8  ? SweepShape{544, 128, 128}
+         : v == 9  ? SweepShape{544, 512, 128}
+         : v == 10 ? SweepShape{544, 1024, 128}
+                   : SweepShape{0, 0, 0};
 }
 
 // One level of one grid as seen by the V-cycle kernels (precision T is fixed

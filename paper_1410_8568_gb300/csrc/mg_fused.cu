@@ -281,10 +281,11 @@ void launch_sweep_b(const Table &tb, int dir, double omega, int flags, const Out
 
 }  // namespace
 
-bool sweep_fits(const int n[3], int per, int v)
+bool sweep_fits(const int n[3], int per, int v, bool fp32)
 {
     if (v < 1 || v >= kSweepVariants) return false;
     const SweepShape sh = sweep_shape(v);
+    if (sh.tile_x) return fp32 && staged_fits(n, per);
     // rows of whole quads, at least one own row per strip, and an even number
     // of cells along every periodic axis (else the colours do not alternate
     // across the wrap)
@@ -295,6 +296,7 @@ bool sweep_fits(const int n[3], int per, int v)
 int sweep_layout(LevelView &v, int variant)
 {
     const SweepShape sh = sweep_shape(variant);
+    if (sh.tile_x) return staged_layout(v, sh.Kc);
     const int nq = v.n[0] >> 2, ny = v.n[1], nz = v.n[2];
     const int rmax = sh.B / nq - 2;
     const int strips = (ny + rmax - 1) / rmax;
@@ -318,9 +320,14 @@ template <class T>
 void launch_sweep(const Table &tb, int dir, double omega, int flags, const OuterView *ov, cudaStream_t s)
 {
     if (tb.blocks == 0) return;
+    const SweepShape sh = sweep_shape(tb.variant);
+    if (sh.tile_x) {
+        // FP32 only: sweep_fits() offers the staged shapes to FP32 cycles alone
+        if constexpr (sizeof(T) == 4) launch_sweep_staged(tb, dir, omega, flags, ov, s);
+        return;
+    }
     const bool mo = (flags & kOuter) != 0;
-    const int B = sweep_shape(tb.variant).B;
-    if (B == 1024) {
+    if (sh.B == 1024) {
         if (mo) launch_sweep_b<T, 1024, true>(tb, dir, omega, flags, ov, s);
         else launch_sweep_b<T, 1024, false>(tb, dir, omega, flags, nullptr, s);
     } else {

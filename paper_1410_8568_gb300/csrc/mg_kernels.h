@@ -111,12 +111,16 @@ template <class T> void launch_half_rows(const Table &, int colour, double omega
                                          const OuterView *ov, cudaStream_t);
 template <class T> void launch_restrict_rows(const Table &, double omega, cudaStream_t);
 template <class T> void launch_prolong_rows(const Table &, const OuterView *ov, cudaStream_t);
-// one-pass red-black sweep (mg_fused.cu): shape v fits a level with n cells
-// per axis and periodic bits per; sweep_layout fills the view's strip and chunk
+// one-pass red-black sweep (mg_fused.cu, and mg_staged.cu for the staged
+// shapes): shape v fits a level with n cells per axis and periodic bits per in
+// FP32 (fp32) or FP64 cycles; sweep_layout fills the view's strip and chunk
 // fields for shape v and returns the blocks of the grid; a launch reads the
 // iterate from x (dir 0) or x2 (dir 1) and writes the other buffer; flags as
 // for the half-sweep (kHalfZero, kHalfOuter)
-bool sweep_fits(const int n[3], int per, int v);
+bool sweep_fits(const int n[3], int per, int v, bool fp32);
+bool staged_fits(const int n[3], int per);
+int staged_layout(LevelView &v, int kc);
+void launch_sweep_staged(const Table &, int dir, double omega, int flags, const OuterView *ov, cudaStream_t);
 int sweep_layout(LevelView &v, int variant);
 int sweep_blocks(const int n[3], int variant);
 template <class T> void launch_sweep(const Table &, int dir, double omega, int flags, const OuterView *ov,

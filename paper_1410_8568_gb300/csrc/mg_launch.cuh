@@ -3,7 +3,8 @@
 //
 // A kernel launched with the attribute may be scheduled onto the SMs while the
 // kernel before it in the stream (or the graph node before it, when captured)
-// is still running.  Every kernel of this library begins with dep_entry():
+// is still running.  Every kernel of this library begins with dep_entry() (the
+// staged one-pass sweep with dep_wait(), and dep_release() at its end):
 //   griddepcontrol.wait              holds the block until the preceding grid
 //                                    has completed and its memory operations
 //                                    are visible (returns at once when the
@@ -30,6 +31,12 @@ __device__ __forceinline__ void dep_entry()
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+
+// The two halves of dep_entry for a kernel whose SMs should not host the next
+// grid's waiting blocks while it runs (an issue-bound kernel that leaves room
+// for them): wait at entry, allow the next grid only when the block is done.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Launches made by this host thread carry the attribute while a DepScope with
 // on = 1 is alive (plan execution and graph capture); elsewhere (autotuner

@@ -82,25 +82,31 @@ constexpr int kZeroGuess = 1, kOuter = 4;
 // the other colour); b and the y/z neighbours and faces only at the two colour
 // cells.  The quad is written back whole, the other colour unchanged.  Per
 // cell, the terms are summed in the order x-, x+, y-, y+, z-, z+ as in every
-// other kernel.
+// other kernel.  The rounding steps are written out (a product rounded on its
+// own, then fused multiply-adds, and a fused multiply-add for the update):
+// left to the compiler, the first two products of the sum could be contracted
+// either way, differently in different kernels, and the kernels that relax the
+// same cell (half-sweep tilings, one-pass sweeps, the tail) would then differ in
+// the last bits.
+template <class T>
+__device__ __forceinline__ T mul_rn(T a, T b)
+{
+    if constexpr (sizeof(T) == 4) return __fmul_rn(a, b);
+    else return __dmul_rn(a, b);
+}
+
 template <class T>
 __device__ __forceinline__ T relax_cell(T xc, T xl, T xr, T fl, T fr, T fs, T fn, T fb, T ft, T xs,
                                         T xn, T xb, T xt, T bc, T omega)
 {
-    T d, f;
-    d = fl;
-    f = fl * (xl - xc);
-    d += fr;
-    f += fr * (xr - xc);
-    d += fs;
-    f += fs * (xs - xc);
-    d += fn;
-    f += fn * (xn - xc);
-    d += fb;
-    f += fb * (xb - xc);
-    d += ft;
-    f += ft * (xt - xc);
-    return d > T(0) ? xc + omega * relax_div(f - bc, d) : xc;
+    const T d = ((((fl + fr) + fs) + fn) + fb) + ft;
+    T f = mul_rn(fl, xl - xc);
+    f = fma(fr, xr - xc, f);
+    f = fma(fs, xs - xc, f);
+    f = fma(fn, xn - xc, f);
+    f = fma(fb, xb - xc, f);
+    f = fma(ft, xt - xc, f);
+    return d > T(0) ? fma(omega, relax_div(f - bc, d), xc) : xc;
 }
 
 // The relaxation of FP64 cycles, with the cell's diagonal given by its inverse

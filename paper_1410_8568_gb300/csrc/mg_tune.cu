@@ -101,7 +101,7 @@ int load_locked(const char *path, int *loaded)
         if (k.kind < 0 || k.kind > MG_TILE_SWEEP || (k.mixed != 0 && k.mixed != 1) || k.per < 0 || k.per > 7 ||
             v < 0)
             continue;
-        if (k.kind == MG_TILE_SWEEP ? (v >= kSweepVariants || (v > 0 && !sweep_fits(k.n, k.per, v)))
+        if (k.kind == MG_TILE_SWEEP ? (v >= kSweepVariants || (v > 0 && !sweep_fits(k.n, k.per, v, k.mixed == 1)))
                                     : (v >= kTileVariants || !tile_fits(k.n, v)))
             continue;
         g_tune[k] = v;
@@ -267,7 +267,7 @@ int tune_sweep(mg_handle *h)
     const int *n = h->lev[0].n;
     const int forced = h->prm.sweep;
     if (forced >= 0) {
-        h->tile[MG_TILE_SWEEP][0] = (signed char)((forced > 0 && sweep_fits(n, h->per, forced)) ? forced : 0);
+        h->tile[MG_TILE_SWEEP][0] = (signed char)((forced > 0 && sweep_fits(n, h->per, forced, h->mixed)) ? forced : 0);
         return MG_OK;
     }
     TuneKey key;
@@ -289,7 +289,7 @@ int tune_sweep(mg_handle *h)
     for (int v = 0; v < kSweepVariants; v++) t[v] = -1.f;
     for (int round = 0; round < 3; round++)
         for (int v = 0; v < kSweepVariants; v++) {
-            if (v > 0 && !sweep_fits(n, h->per, v)) continue;
+            if (v > 0 && !sweep_fits(n, h->per, v, h->mixed)) continue;
             float ms = 0.f;
             const int rc = h->mixed ? time_sweep<float>(h, v, &ms) : time_sweep<double>(h, v, &ms);
             if (rc) return rc;
@@ -386,12 +386,13 @@ int mg_tile_choice(const mg_handle *h, int kind, int level, int *variant)
     return MG_OK;
 }
 
-int mg_sweep_shape(int variant, int *threads, int *planes)
+int mg_sweep_shape(int variant, int *threads, int *planes, int *tile_x)
 {
-    if (variant < 0 || variant >= gbmg::kSweepVariants || !threads || !planes) return MG_EINVAL;
+    if (variant < 0 || variant >= gbmg::kSweepVariants || !threads || !planes || !tile_x) return MG_EINVAL;
     const gbmg::SweepShape sh = gbmg::sweep_shape(variant);
     *threads = sh.B;
     *planes = sh.Kc;
+    *tile_x = sh.tile_x;
     return MG_OK;
 }
 

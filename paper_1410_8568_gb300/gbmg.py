@@ -32,7 +32,7 @@ COARSE_AUTO, COARSE_GMRES = 0, 1
 OUTER_FP64, OUTER_XP = 0, 1
 MAX_COARSE, MAX_COARSE_GMRES = 512, 32768
 TILE_HALF, TILE_RESTRICT, TILE_PROLONG, TILE_SWEEP = 0, 1, 2, 3
-SWEEP_AUTO, SWEEP_HALF, SWEEP_VARIANTS = -1, 0, 7
+SWEEP_AUTO, SWEEP_HALF, SWEEP_VARIANTS = -1, 0, 11
 
 
 class MGError(RuntimeError):
@@ -129,7 +129,7 @@ def lib():
             "mg_handle_params": (_I, [_V, _P(Params)]),
             "mg_probe_fp64_rate": (_I, [_I, _I, _P(_D), _V]),
             "mg_set_wait_limit": (_I, [_V, ctypes.c_longlong]),
-            "mg_sweep_shape": (_I, [_I, _P(_I), _P(_I)]),
+            "mg_sweep_shape": (_I, [_I, _P(_I), _P(_I), _P(_I)]),
             "mg_smooth_onepass": (_I, [_V, _I, _I, _V, _V, _V, _I, _I]),
         }
         for name, (res, args) in sig.items():
@@ -197,10 +197,13 @@ def make_params(precision=MIXED, nu1=2, nu2=2, omega=1.0, max_iters=100, use_gra
 
 
 def sweep_shape(variant):
-    """(threads per block, planes per block) of one-pass sweep shape `variant`."""
-    a, b = ctypes.c_int(), ctypes.c_int()
-    check(lib().mg_sweep_shape(int(variant), ctypes.byref(a), ctypes.byref(b)), "mg_sweep_shape")
-    return (a.value, b.value)
+    """(threads per block, planes per block, tile_x) of one-pass sweep shape
+    `variant`; tile_x = 0 for the whole-row shapes, else the cells along x of a
+    staged shape's tile (FP32 cycles only)."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().mg_sweep_shape(int(variant), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+          "mg_sweep_shape")
+    return (a.value, b.value, c.value)
 
 
 def tile_shape(variant):

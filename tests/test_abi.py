@@ -104,11 +104,14 @@ def test_sweep_shapes_and_param():
     p = gbmg.Params()
     assert L.mg_params_default(ctypes.byref(p)) == 0
     assert p.sweep == gbmg.SWEEP_AUTO
-    assert gbmg.sweep_shape(0) == (0, 0)
+    assert gbmg.sweep_shape(0) == (0, 0, 0)
     shapes = [gbmg.sweep_shape(v) for v in range(1, gbmg.SWEEP_VARIANTS)]
     assert len(set(shapes)) == gbmg.SWEEP_VARIANTS - 1
-    for threads, planes in shapes:
-        assert threads in (512, 1024) and planes >= 8
+    for threads, planes, tile_x in shapes:
+        # whole-row shapes, or staged tiles of 128 cells (16 row warps, a halo-quad warp)
+        assert (threads in (512, 1024) and tile_x == 0) or (threads == 544 and tile_x == 128)
+        assert planes >= 8
+    assert any(s[2] for s in shapes) and any(not s[2] for s in shapes)
     with pytest.raises(gbmg.MGError):
         gbmg.sweep_shape(gbmg.SWEEP_VARIANTS)
     g = gbmg.make_grid((64, 64, 64), (1, 1, 0))
@@ -138,15 +141,18 @@ def test_tune_cache_file_roundtrip(tmp_path):
                    "0 1 0 30 16 16 2\n"         # rows of 30 cells: flat shapes do not fit
                    "2 1 0 64 64 64 9\n"         # no such shape
                    "3 1 3 128 128 128 2\n"      # one-pass sweep, FP32, periodic x y
-                   "3 1 3 128 127 128 2\n")     # odd periodic y: the one-pass sweep does not fit
+                   "3 1 3 128 127 128 2\n"      # odd periodic y: the one-pass sweep does not fit
+                   "3 1 3 256 256 256 8\n"      # staged one-pass sweep, FP32
+                   "3 0 3 256 256 128 8\n"      # staged shapes are FP32 only
+                   "3 1 0 96 64 64 7\n")        # rows of 96 cells: no whole 128-cell tiles
     gbmg.tune_cache_clear()
     assert gbmg.tune_cache_size() == 0
-    assert gbmg.tune_cache_load(str(src)) == 3
-    assert gbmg.tune_cache_size() == 3
+    assert gbmg.tune_cache_load(str(src)) == 4
+    assert gbmg.tune_cache_size() == 4
     out = tmp_path / "out.txt"
     gbmg.tune_cache_save(str(out))
     assert sorted(out.read_text().split("\n")[:-1]) == ["0 1 3 128 128 128 1", "1 0 0 64 48 32 5",
-                                                        "3 1 3 128 128 128 2"]
+                                                        "3 1 3 128 128 128 2", "3 1 3 256 256 256 8"]
     with pytest.raises(gbmg.MGError) as e:
         gbmg.tune_cache_load(str(tmp_path / "missing.txt"))
     assert e.value.code == gbmg.ENOTFOUND
@@ -172,8 +178,10 @@ def test_every_launched_kernel_waits_for_its_predecessor_first():
     """A launch with programmatic stream serialization (launch_k inside a
     dependent-launch scope) may be scheduled while the previous kernel runs, so
     every kernel defined anywhere in csrc (.cu and .cuh) must begin with
-    dep_entry() (griddepcontrol.wait) before any other statement, except the
-    plain-launched ones, which must never be launched through launch_k."""
+    dep_entry() (griddepcontrol.wait, then the release of the next grid) or
+    dep_wait() (the wait alone, with dep_release() later in the kernel) before
+    any other statement, except the plain-launched ones, which must never be
+    launched through launch_k."""
     import glob
 
     csrc = os.path.join(os.path.dirname(gbmg.__file__), "csrc")
@@ -184,12 +192,20 @@ def test_every_launched_kernel_waits_for_its_predecessor_first():
         for m in re.finditer(r"__global__[^;{]*\{", src):
             head = src[m.start():m.end()]
             kernel = re.search(r"\b(k_\w+)\s*\(", head).group(1)
-            first = src[m.end():].lstrip().split("\n", 1)[0].strip()
+            lines = [ln.strip() for ln in src[m.end():].split("\n")]
+            body = [ln for ln in lines if ln and not ln.startswith("//")]
+            first = body[0]
             if kernel in PLAIN_LAUNCH:
                 plain.add(kernel)
                 assert "<<<" in src, (name, kernel)
                 continue
-            assert first == "dep_entry();", (name, head[:90])
+            assert first in ("dep_entry();", "dep_wait();"), (name, head[:90])
+            if first == "dep_wait();":
+                depth, i = 1, m.end()
+                while depth:
+                    depth += {"{": 1, "}": -1}.get(src[i], 0)
+                    i += 1
+                assert "dep_release();" in src[m.end():i], (name, kernel)
             checked += 1
     assert checked >= 30
     assert plain == PLAIN_LAUNCH

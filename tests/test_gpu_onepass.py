@@ -1,9 +1,11 @@
 """The one-pass red-black sweep (both colours of a sweep in one launch, Sec. 2.3
 item 5) through the C ABI: bitwise equal to the red and black half-sweep
 launches and to the oracle's red-black sweep within rounding, for every launch
-shape that fits, on grids whose strips and plane chunks are ragged; whole
-solves with it are bitwise equal to whole solves with half-sweeps, alone,
-batched and in the host-driven loop, and reach the oracle's p*."""
+shape that fits (whole-row shapes, and the staged shapes whose tiles of 128
+cells are copied into shared memory), on grids whose strips, tiles and plane
+chunks are ragged; whole solves with it are bitwise equal to whole solves with
+half-sweeps, alone, batched and in the host-driven loop, and reach the
+oracle's p*."""
 import numpy as np
 import pytest
 
@@ -26,10 +28,13 @@ def dev(a, dtype=torch.float64):
     return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
-def fits(shape, bc, v):
-    threads, _ = gbmg.sweep_shape(v)
-    return (shape[0] % 4 == 0 and 3 * (shape[0] // 4) <= threads and not (bc[1] and shape[1] % 2)
-            and not (bc[2] and shape[2] % 2))
+def fits(shape, bc, v, fp32=True):
+    threads, _, tile_x = gbmg.sweep_shape(v)
+    if (bc[1] and shape[1] % 2) or (bc[2] and shape[2] % 2):
+        return False
+    if tile_x:
+        return fp32 and shape[0] % tile_x == 0
+    return shape[0] % 4 == 0 and 3 * (shape[0] // 4) <= threads
 
 
 def random_faces(shape, bc, seed):
@@ -43,7 +48,11 @@ def random_faces(shape, bc, seed):
 # 2 strips of 24; 40 planes are 3 chunks of 14 / 14 / 12 planes of 16 (or 2 of
 # 20 of 32); rows of 160 cells: 40 quads, 12 rows per 512-thread strip
 SHAPES = [((64, 48, 40), (1, 1, 0)), ((64, 48, 40), (0, 0, 0)), ((160, 30, 18), (1, 0, 1)),
-          ((32, 66, 34), (0, 1, 1))]
+          ((32, 66, 34), (0, 1, 1)),
+          # staged shapes: tiles of 128 cells; 30 rows = 3 strips of 10, 15 rows =
+          # strips of 8 / 7; 130 planes in chunks of at most 64: 44 / 44 / 42
+          ((128, 30, 18), (1, 1, 0)), ((256, 30, 22), (0, 0, 1)), ((128, 15, 9), (1, 0, 0)),
+          ((384, 16, 6), (0, 1, 0)), ((128, 12, 130), (0, 1, 1))]
 
 
 @pytest.mark.parametrize("shape,bc", SHAPES)
@@ -66,7 +75,7 @@ def test_onepass_equals_half_sweeps_and_oracle(shape, bc, prec, omega):
         S.smooth(0, dev(b, dt), ref1, 1, prec=prec)
         tried = 0
         for v in range(1, gbmg.SWEEP_VARIANTS):
-            if not fits(shape, bc, v):
+            if not fits(shape, bc, v, prec == gbmg.MIXED):
                 continue
             x = dev(x0, dt)
             work = torch.full_like(x, float("nan"))
@@ -100,6 +109,23 @@ def test_onepass_refuses_shapes_that_do_not_fit():
         with pytest.raises(gbmg.MGError):
             S.smooth_onepass(0, x, x.clone(), x.clone(), 1, prec=gbmg.MIXED, variant=1)
         assert S.tile_choice(gbmg.TILE_SWEEP, 0) == 0
+    # staged shapes: FP32 only, and rows of whole 128-cell tiles
+    shape, bc = (128, 16, 8), (1, 1, 0)
+    f = random_faces(shape, bc, 3)
+    staged = [v for v in range(1, gbmg.SWEEP_VARIANTS) if gbmg.sweep_shape(v)[2]]
+    assert staged
+    with gbmg.Solver(shape, bc, faces=[dev(a) for a in f], precision=gbmg.FP64) as S:
+        x = torch.zeros(cells(shape), dtype=torch.float64, device="cuda")
+        for v in staged:
+            with pytest.raises(gbmg.MGError):
+                S.smooth_onepass(0, x, x.clone(), x.clone(), 1, prec=gbmg.FP64, variant=v)
+    shape = (64, 16, 8)
+    f = random_faces(shape, bc, 4)
+    with gbmg.Solver(shape, bc, faces=[dev(a) for a in f]) as S:
+        x = torch.zeros(cells(shape), dtype=torch.float32, device="cuda")
+        for v in staged:
+            with pytest.raises(gbmg.MGError):
+                S.smooth_onepass(0, x, x.clone(), x.clone(), 1, prec=gbmg.MIXED, variant=v)
 
 
 def solve_with(P, f, sweep, precision, outer=gbmg.OUTER_FP64, use_graph=True):
@@ -129,6 +155,22 @@ def test_solve_with_onepass_sweeps_is_bitwise_the_half_sweep_solve(precision, ou
     assert err <= ERR
 
 
+@pytest.mark.parametrize("outer", [gbmg.OUTER_FP64, gbmg.OUTER_XP], ids=["mixed", "mixed_xp"])
+def test_staged_solve_is_bitwise_the_half_sweep_solve(outer):
+    """FP32 cycles with the staged one-pass sweep on a 128^3 drop/film grid (one
+    128-cell tile per row, 10 strips of up to 13 rows): every staged shape, in the
+    graph and in the host-driven loop, bitwise the half-sweep solve."""
+    P = I.config2(128)
+    f = oracle.faces_from_density(P.shape, P.bc, P.rho)
+    p_half, it_half, _ = solve_with(P, f, gbmg.SWEEP_HALF, gbmg.MIXED, outer)
+    staged = [v for v in range(1, gbmg.SWEEP_VARIANTS) if gbmg.sweep_shape(v)[2]]
+    for v in staged:
+        for use_graph in (True, False):
+            p, it, chosen = solve_with(P, f, v, gbmg.MIXED, outer, use_graph)
+            assert chosen == v
+            assert it == it_half and torch.equal(p, p_half), (v, use_graph)
+
+
 def test_batch_with_onepass_sweeps_matches_alone():
     """A batch of grids of different sizes runs its finest-level sweeps as one
     one-pass launch over all grids (the shape of the largest): each grid's
@@ -137,6 +179,28 @@ def test_batch_with_onepass_sweeps_matches_alone():
     faces = [oracle.faces_from_density(P.shape, P.bc, P.rho) for P in probs]
     alone = [solve_with(P, f, gbmg.SWEEP_HALF, gbmg.MIXED)[:2] for P, f in zip(probs, faces)]
     solvers = [gbmg.Solver(P.shape, P.bc, faces=[dev(a) for a in f], sweep=1) for P, f in zip(probs, faces)]
+    B = gbmg.Batch(solvers)
+    rhs = [dev(P.rhs) for P in probs]
+    ps = [torch.zeros_like(r) for r in rhs]
+    sts = B.solve(rhs, ps, tol=TOL)
+    for (pa, ia), pb, st in zip(alone, ps, sts):
+        assert st.status == gbmg.OK and st.iters == ia
+        assert torch.equal(pa, pb)
+    B.close()
+    for S in solvers:
+        S.close()
+
+
+def test_batch_with_staged_sweeps_matches_alone():
+    """A batch of grids with rows of whole 128-cell tiles runs its finest-level
+    sweeps as one staged launch over all grids (each grid with its own tiles):
+    each grid's result is bitwise its solo result with half-sweeps."""
+    probs = [I.config2(128), I.config1(128, ratio=10.0), I.config2(256)]
+    faces = [oracle.faces_from_density(P.shape, P.bc, P.rho) for P in probs]
+    alone = [solve_with(P, f, gbmg.SWEEP_HALF, gbmg.MIXED)[:2] for P, f in zip(probs, faces)]
+    staged = [v for v in range(1, gbmg.SWEEP_VARIANTS) if gbmg.sweep_shape(v)[2]]
+    solvers = [gbmg.Solver(P.shape, P.bc, faces=[dev(a) for a in f], sweep=staged[1]) for P, f in zip(probs, faces)]
+    assert all(S.tile_choice(gbmg.TILE_SWEEP, 0) == staged[1] for S in solvers)
     B = gbmg.Batch(solvers)
     rhs = [dev(P.rhs) for P in probs]
     ps = [torch.zeros_like(r) for r in rhs]
