@@ -601,7 +601,11 @@ static void vcycle(Plan &P, Prof &pf, int cyc, bool outer)
         pf.begin(s, MG_K_PROLONG, l);
         launch_prolong<T>(at(P.down[l]), (top && q.nu2 == 0) ? P.ov : nullptr, s);
         pf.end(s);
-        if (l == 0 && P.sweep0.count > 0) {
+        // the post-sweeps that end a refinement step also add the final values
+        // to the outer iterate: as half-sweep launches where the one-pass shape
+        // is a staged one (bitwise the same; the staged kernel's instance with
+        // that update runs out of registers and takes twice as long)
+        if (l == 0 && P.sweep0.count > 0 && !(top && sweep_shape(P.sweep0.variant).tile_x)) {
             const Table W = at(P.sweep0);
             for (int it = 0; it < q.nu2; it++) {
                 // the last sweep adds both colours' final values
