@@ -218,10 +218,12 @@ def level_shapes(shape):
 
 
 def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, mixed=True, pcg=False,
-                   xp=False):
+                   xp=False, onepass=False, staged=False):
     """Kernels of one solve step: coefficient set-up, prologue, refinement (or CG) steps, epilogue.
     In FP32 cycles the levels of at most tail_cells cells (below the finest) run in one launch;
-    with more than one V-cycle per refinement step each step starts with a step-control kernel."""
+    with more than one V-cycle per refinement step each step starts with a step-control kernel.
+    onepass: the finest level runs one launch per red-black sweep instead of two; staged: with a
+    staged shape, the post-sweeps of a step's last cycle still run as half-sweep pairs."""
     lv = level_shapes(shape)
     L = len(lv)
     lt = next((l for l in range(1, L - 1) if math.prod(lv[l]) <= tail_cells), L) if mixed else L
@@ -239,6 +241,9 @@ def count_launches(shape, iters, steps, nu1=2, nu2=2, inner=3, tail_cells=4096, 
     else:
         per_step = 3 + (1 if inner > 1 else 0)  # residual, finalize, loop control (+ step control)
     epilogue = 3                       # sum p, mean, p - mean
+    if onepass and not pcg:
+        cycle -= nu1 + nu2
+        per_step += nu2 if staged else 0
     return setup + prologue + iters * cycle + steps * per_step + epilogue
 
 
@@ -805,7 +810,8 @@ def run_single(args, rank, world, local_rank, dist):
     if rank == 0:
         m, f = results["mixed"], results["fp64"]
         launches = args.steps * count_launches(P.shape, m["iters"], m["refine_steps"], inner=m["inner"],
-                                               pcg=args.solver == "pcg")
+                                               pcg=args.solver == "pcg", onepass=sv > 0,
+                                               staged=sv > 0 and gbmg.sweep_shape(sv)[2] > 0)
         xp = results.get("mixed_xp")
         line = {
             "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
