@@ -634,6 +634,29 @@ def oracle_reference_run(P, tol=TOL):
     return r.x, dt, r.cycles, reach
 
 
+def oracle_single_thread(P, cycles):
+    """The oracle on one host thread, a bounded sample: its set-up (a call that
+    stops before the first cycle) and one V(2,2) cycle, each timed; a solve =
+    set-up + `cycles` cycles."""
+    import oracle
+    faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
+    threads = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        t = time.perf_counter()
+        oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=0)
+        s0 = time.perf_counter() - t
+        t = time.perf_counter()
+        oracle.solve(P.shape, P.bc, faces, P.rhs, tol=0.0, max_cycles=1)
+        s1 = time.perf_counter() - t
+    finally:
+        oracle.set_threads(threads)
+    cyc = max(s1 - s0, 1e-9)
+    return {"value": 1.0 / (s0 + cycles * cyc), "unit": "solves/s", "cores": 1,
+            "sample": "one thread: set-up %.2f s and one V(2,2) cycle %.2f s, timed; a solve = set-up + %d "
+                      "cycles" % (s0, cyc, cycles)}
+
+
 def run_single(args, rank, world, local_rank, dist):
     """One grid per step: new density in, cold-start solve to 1e-10 (mixed,
     FP64, extended-precision outer iteration), end to end through the host
@@ -796,7 +819,8 @@ def run_single(args, rank, world, local_rank, dist):
             cpu = {"value": 1.0 / t_solve, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
                    "sample": "the oracle's p* run on this workload (%d V(2,2) cycles to rounding level, %.1f s), "
                              "timed; solves/s = 1 / (mean cycle time x the %d cycles that reached 1e-10)" %
-                             (ncyc, dt, reach)}
+                             (ncyc, dt, reach),
+                   "single_thread": oracle_single_thread(P, reach)}
     elif rank == 0 and not args.no_cpu_baseline:
         import oracle
         faces = oracle.faces_from_density(P.shape, P.bc, P.rho)
